@@ -1,0 +1,134 @@
+/*
+ * dm.h -- C ABI of the GB300 (sm_103a) decomposition-method solver for
+ * block-tridiagonal linear systems.
+ *
+ * Method: P. A. Belov, E. R. Nugumanov, S. L. Yakovlev, "Decomposition
+ * method for block-tridiagonal matrix systems", arXiv:1505.06864.
+ *
+ * The system (the paper's Eq. 1, with this library's letters) is
+ *
+ *     A_i X_{i-1} + B_i X_i + C_i X_{i+1} = b_i,   i = 1..N,   A_1 = C_N = 0,
+ *
+ * B_i the m x m diagonal block (the paper's C_i), C_i the super-diagonal
+ * block (the paper's B_i), m the block size (the paper's n), nrhs the number
+ * of right-hand-side columns (the paper's l), P the number of subsystems
+ * (the paper's M).
+ *
+ * Memory layout of every array argument: float64, row-major blocks stored one
+ * after another.  A, B, C: [N][m][m] (element (i, r, c) at i*m*m + r*m + c);
+ * b, x: [N][m][nrhs] (element (i, r, c) at i*m*nrhs + r*nrhs + c).  The
+ * entries of A_1 (index 0) and C_N (index N-1) are ignored.  Each pointer may
+ * be host memory (pageable or pinned) or device memory of the current CUDA
+ * device; the library detects which.  The caller keeps ownership of every
+ * array; the library copies what it needs before the call returns (dm_submit
+ * excepted, see there).
+ *
+ * Return values: DM_OK (0) on success, a negative DM_E* code on failure.
+ * Nothing is thrown across the ABI.  dm_last_error() gives a text for the
+ * calling thread's last failure.  A plan handle may be used by one thread at
+ * a time; different plans may be used concurrently from different threads.
+ */
+#ifndef DM_GB300_H
+#define DM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DM_OK 0
+#define DM_PENDING 1      /* dm_poll: the request has not finished */
+#define DM_EINVAL (-1)    /* invalid argument (sizes, P, levels, precision, NULL pointer) */
+#define DM_ENOMEM (-2)    /* device memory could not be allocated / admission refused */
+#define DM_ESINGULAR (-3) /* a pivot of some block LU was zero or not finite */
+#define DM_ENOTCONV (-4)  /* iterative refinement did not reach its tolerance */
+#define DM_EAGAIN (-5)    /* no serving slot free right now; try again */
+#define DM_ECUDA (-6)     /* a CUDA runtime call failed */
+#define DM_ESTATE (-7)    /* call out of order (e.g. dm_solve before dm_factor) */
+#define DM_ETIMEOUT (-8)  /* a bounded device-side wait gave up */
+
+/* precision of the block factorisation at the top level.  The supplementary
+ * (interface) system is always factored and solved in float64, and the
+ * residual of iterative refinement is always evaluated in float64. */
+#define DM_FP64 0    /* plain float64 throughout; no refinement */
+#define DM_FP32 1    /* float32 factors on CUDA cores + float64 refinement */
+#define DM_TF32 2    /* tcgen05 kind::tf32 block products, float32 accumulate + refinement */
+#define DM_BF16X3 3  /* tcgen05 kind::f16 split-bf16 (hi*hi + hi*lo + lo*hi) + refinement */
+
+typedef struct dm_plan_s* dm_plan_t;
+
+/* Facts about a plan, filled by dm_plan_query. */
+typedef struct dm_plan_info {
+  int N, m, nrhs;        /* sizes (first system of a batch plan) */
+  int P;                 /* subsystems at the top level (the paper's M) */
+  int levels;            /* 1: supplementary system by block Thomas; L > 1: by DM with L-1 levels */
+  int P2;                /* subsystems of the supplementary system when levels > 1, else 1 */
+  int precision;         /* DM_FP64 / DM_FP32 / DM_TF32 / DM_BF16X3 */
+  int count;             /* systems in the plan (1 unless made by dm_plan_batch) */
+  int last_iters;        /* refinement iterations taken by the last dm_solve */
+  int max_rows;          /* longest subsystem (block rows swept sequentially) */
+  size_t device_bytes;   /* device memory held by the plan */
+  double last_relres;    /* max_k ||b - T x||_2 / ||b||_2 over columns of the last solve */
+  double last_correction;/* last refinement step ||dx||_2 / ||x||_2 (0 for DM_FP64) */
+  double factor_flops;   /* algorithmic flops of one dm_factor (2 per multiply-add) */
+  double solve_flops;    /* algorithmic flops of one solve sweep (without refinement) */
+} dm_plan_info;
+
+/* Plan the solution of one system of N block rows, blocks m x m, nrhs
+ * right-hand-side columns, split into P subsystems (Section 2 of the paper;
+ * 1 <= P <= (N+1)/2, every subsystem keeps >= 1 row; P = 1 is the block Thomas
+ * algorithm of Section 3).  levels >= 1: the supplementary system of Eq. (e232)
+ * is solved by block Thomas (levels = 1) or by DM recursively (levels > 1,
+ * Section 4.2.1, its subsystem count from Eq. (SuppMatrM)).  P = 0 or
+ * levels = 0 asks the built-in tuner to choose (seeded by Eqs. (MAXSpeedP) and
+ * (SuppMatrM)).  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
+ * device workspace; returns DM_EINVAL or DM_ENOMEM on failure.  *out is set
+ * only on success. */
+int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision);
+
+/* Plan `count` independent systems (sizes N[s], m[s], nrhs[s]) that are
+ * factored and solved together, every stage of all systems in the same
+ * launches.  Partition counts and recursion depth are chosen per system by
+ * the tuner.  Arrays of a batch are the systems' arrays concatenated in order
+ * (system s starts at sum_{s'<s} N[s'] m[s']^2 for A, B, C and at
+ * sum_{s'<s} N[s'] m[s'] nrhs[s'] for b, x).  relres_out of dm_solve then points to
+ * `count` doubles. */
+int dm_plan_batch(dm_plan_t* out, int count, const int* N, const int* m, const int* nrhs, int precision);
+
+/* Factor: forward and backward sweeps of every subsystem for its spikes
+ * (Eq. e231, the W_R right-hand sides), assembly of the supplementary matrix
+ * (Eq. e2311) and its float64 factorisation (Eq. e232).  The factors stay on
+ * the device until dm_destroy; dm_factor may be called again with new blocks.
+ * Returns DM_ESINGULAR if a pivot vanished (dm_last_error names the block row). */
+int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C);
+
+/* Solve T x = b with the resident factors: subsystem sweeps for z^k
+ * (Eq. e231), supplementary right-hand side (Eq. e2311), supplementary solve
+ * for h (Eq. e232), back-substitution (Eq. endSolution), float64 residual.
+ * For precision != DM_FP64 the solve is repeated on float64 residuals
+ * (iterative refinement) until ||dx||/||x|| <= tol (dm_set_refinement) or the
+ * iteration cap; DM_ENOTCONV then, with the best x written.  x may alias b.
+ * relres_out (may be NULL) receives max over columns of ||b - T x||/||b||. */
+int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out);
+
+/* The decomposition dm_plan would choose for P = 0 / levels = 0 (the tuner's
+ * seed: P from Eq. (MAXSpeedP), recursion from the P >= 21 condition after
+ * Eq. (SuppMatrM), P2 from Eq. (SuppMatrM)).  Host only: allocates nothing and
+ * needs no GPU.  Inputs P, levels as for dm_plan (0 = choose); outputs the
+ * effective P, levels and P2.  DM_EINVAL for invalid sizes. */
+int dm_plan_tune(int N, int m, int nrhs, int* P, int* levels, int* P2);
+
+/* Optional settings and queries. */
+int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */
+int dm_set_refinement(dm_plan_t plan, double tol, int max_iters); /* default 1e-12, 30 */
+int dm_plan_query(dm_plan_t plan, dm_plan_info* info);
+void dm_destroy(dm_plan_t plan);
+const char* dm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DM_GB300_H */

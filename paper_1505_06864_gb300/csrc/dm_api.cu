@@ -1,0 +1,641 @@
+// C ABI of the decomposition-method solver: plans, factor, solve, refinement.
+//
+// A plan is a stack of levels.  Level 0 holds the user's systems split into
+// subsystems (Section 2 of the paper).  Level 1 holds every system's
+// supplementary system (Eq. e232: P-1 block rows assembled from the spikes),
+// split again into subsystems when the recursion depth asks for DM there
+// (Section 4.2.1), and so on; the last level is solved by the block Thomas
+// algorithm (one subsystem per system, Section 3).  Every level runs the same
+// level-synchronous kernels (dm_kernels.cu); level 0 may hold float32 factors
+// (mixed precision), every deeper level is float64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dm.h"
+#include "dm_internal.cuh"
+#include "dm_plan.h"
+
+namespace dm {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define DM_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return set_error(DM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                       __FILE__, __LINE__);                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Level construction
+int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors) {
+  f32 = fp32_factors;
+  nsys = (int)specs.size();
+  spec = specs;
+  blk0.assign(nsys, 0);
+  vec0.assign(nsys, 0);
+  long long b = 0, v = 0;
+  max_m = 1;
+  max_r = 1;
+  Nmax = 0;
+  for (int s = 0; s < nsys; ++s) {
+    blk0[s] = b;
+    vec0[s] = v;
+    b += (long long)specs[s].N * specs[s].m * specs[s].m;
+    v += (long long)specs[s].N * specs[s].m * specs[s].r;
+    max_m = std::max(max_m, specs[s].m);
+    max_r = std::max(max_r, specs[s].r);
+    Nmax = std::max(Nmax, specs[s].N);
+  }
+  nblk = b;
+  nvec = v;
+  // supplementary systems: one per system with P > 1
+  std::vector<SysSpec> sub;
+  std::vector<int> sub_of(nsys, -1);
+  for (int s = 0; s < nsys; ++s) {
+    if (specs[s].P > 1) {
+      SysSpec t;
+      t.N = specs[s].P - 1;
+      t.m = specs[s].m;
+      t.r = specs[s].r;
+      t.levels = specs[s].levels - 1;
+      t.P = (t.levels >= 1 && specs[s].P2 > 1) ? specs[s].P2 : 1;
+      t.P2 = (t.levels >= 2) ? supp_partitions(t.P - 1, t.P, t.r, t.m) : 1;
+      if (t.P <= 1) { t.levels = 1; t.P = 1; }
+      sub_of[s] = (int)sub.size();
+      sub.push_back(t);
+    }
+  }
+  if (!sub.empty()) {
+    supp.reset(new Level());
+    int rc = supp->build(sub, false);
+    if (rc) return rc;
+  }
+  // subsystem and separator tables
+  parts.clear();
+  seps.clear();
+  sysd.clear();
+  for (int s = 0; s < nsys; ++s) {
+    const SysSpec& sp = specs[s];
+    SysDesc sd;
+    sd.blk = blk0[s];
+    sd.vec = vec0[s];
+    sd.N = sp.N;
+    sd.m = sp.m;
+    sd.r = sp.r;
+    sd.pad = 0;
+    sysd.push_back(sd);
+    std::vector<int> starts, lens, sepr;
+    partition_plan(sp.N, sp.P, starts, lens, sepr);
+    const long long mm = (long long)sp.m * sp.m, mr = (long long)sp.m * sp.r;
+    for (int k = 0; k < sp.P; ++k) {
+      PartDesc pd;
+      pd.blk = blk0[s] + starts[k] * mm;
+      pd.vec = vec0[s] + starts[k] * mr;
+      pd.m = sp.m;
+      pd.r = sp.r;
+      pd.L = lens[k];
+      pd.flags = (k > 0 ? HAS_LEFT : 0) | (k < sp.P - 1 ? HAS_RIGHT : 0);
+      pd.sys = s;
+      pd.row0 = starts[k];
+      pd.hprev = pd.hnext = 0;
+      if (sp.P > 1) {
+        const int ss = sub_of[s];
+        if (k > 0) pd.hprev = supp->vec0[ss] + (long long)(k - 1) * mr;
+        if (k < sp.P - 1) pd.hnext = supp->vec0[ss] + (long long)k * mr;
+      }
+      parts.push_back(pd);
+    }
+    for (int j = 0; j + 1 < sp.P; ++j) {
+      const int q = sepr[j];
+      SepDesc d;
+      d.blk_q = blk0[s] + q * mm;
+      d.vec_q = vec0[s] + q * mr;
+      d.blk_prev = d.blk_q - mm;
+      d.vec_prev = d.vec_q - mr;
+      d.blk_next = d.blk_q + mm;
+      d.vec_next = d.vec_q + mr;
+      const int ss = sub_of[s];
+      d.hblk = supp->blk0[ss] + (long long)j * mm;
+      d.hvec = supp->vec0[ss] + (long long)j * mr;
+      d.m = sp.m;
+      d.r = sp.r;
+      d.flags = (j > 0 ? HAS_HA : 0) | (j < sp.P - 2 ? HAS_HC : 0);
+      d.sys = s;
+      seps.push_back(d);
+    }
+  }
+  // longest subsystems first: the subsystems still active at a step form a prefix
+  std::stable_sort(parts.begin(), parts.end(),
+                   [](const PartDesc& a, const PartDesc& b) { return a.L > b.L; });
+  nparts = (int)parts.size();
+  nseps = (int)seps.size();
+  Lmax = nparts ? parts[0].L : 0;
+  active_fwd.assign(std::max(Lmax, 1), 0);
+  for (int t = 0; t < Lmax; ++t) {
+    int c = 0;
+    while (c < nparts && parts[c].L > t) ++c;
+    active_fwd[t] = c;
+  }
+  active_back.assign(std::max(Lmax, 1), 0);
+  for (int s = 0; s + 1 < Lmax; ++s) {
+    int c = 0;
+    while (c < nparts && parts[c].L >= s + 2) ++c;
+    active_back[s] = c;
+  }
+  return DM_OK;
+}
+
+size_t Level::bytes_needed() const {
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  size_t b = 3 * nblk * sizeof(double);     // A, B, C
+  b += 4 * nblk * es;                       // G, Acal, ZL, ZR
+  b += nvec * es;                           // z
+  b += 2 * nvec * sizeof(double);           // F, X
+  b += parts.size() * sizeof(PartDesc) + seps.size() * sizeof(SepDesc) + sysd.size() * sizeof(SysDesc);
+  b += nsys * sizeof(int);
+  if (supp) b += supp->bytes_needed();
+  return b;
+}
+
+int Level::allocate() {
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(DM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    owned.push_back(*p);
+    return DM_OK;
+  };
+  int rc;
+#define DM_ALLOC(ptr, bytes)                                    \
+  if ((rc = alloc(reinterpret_cast<void**>(&(ptr)), (bytes)))) \
+    return rc;
+  DM_ALLOC(A, nblk * sizeof(double));
+  DM_ALLOC(B, nblk * sizeof(double));
+  DM_ALLOC(C, nblk * sizeof(double));
+  DM_ALLOC(G, nblk * es);
+  DM_ALLOC(Acal, nblk * es);
+  DM_ALLOC(ZL, nblk * es);
+  DM_ALLOC(ZR, nblk * es);
+  DM_ALLOC(z, nvec * es);
+  DM_ALLOC(F, nvec * sizeof(double));
+  DM_ALLOC(X, nvec * sizeof(double));
+  DM_ALLOC(d_parts, std::max<size_t>(1, parts.size()) * sizeof(PartDesc));
+  DM_ALLOC(d_seps, std::max<size_t>(1, seps.size()) * sizeof(SepDesc));
+  DM_ALLOC(d_sys, std::max<size_t>(1, sysd.size()) * sizeof(SysDesc));
+  DM_ALLOC(status, std::max(1, nsys) * sizeof(int));
+#undef DM_ALLOC
+  if (!parts.empty()) DM_CUDA(cudaMemcpy(d_parts, parts.data(), parts.size() * sizeof(PartDesc), cudaMemcpyHostToDevice));
+  if (!seps.empty()) DM_CUDA(cudaMemcpy(d_seps, seps.data(), seps.size() * sizeof(SepDesc), cudaMemcpyHostToDevice));
+  DM_CUDA(cudaMemcpy(d_sys, sysd.data(), sysd.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+  if (supp) {
+    rc = supp->allocate();
+    if (rc) return rc;
+    // corner blocks of the supplementary systems that no assembly writes
+    DM_CUDA(cudaMemset(supp->A, 0, supp->nblk * sizeof(double)));
+    DM_CUDA(cudaMemset(supp->C, 0, supp->nblk * sizeof(double)));
+  }
+  return DM_OK;
+}
+
+Level::~Level() {
+  for (void* p : owned) cudaFree(p);
+}
+
+// Forward and backward spike sweeps, assembly, and the factorisation of the
+// supplementary level (recursively).  A, B, C must hold the level's blocks.
+template <typename T>
+static void factor_level_t(Level& L, cudaStream_t st) {
+  T* G = static_cast<T*>(L.G);
+  T* Ac = static_cast<T*>(L.Acal);
+  T* ZL = static_cast<T*>(L.ZL);
+  T* ZR = static_cast<T*>(L.ZR);
+  for (int t = 0; t < L.Lmax; ++t) {
+    const int np = L.active_fwd[t];
+    launch_inv<T>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st);
+    launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st);
+  }
+  for (int s = 0; s + 1 < L.Lmax; ++s)
+    launch_back_factor<T>(L.d_parts, L.active_back[s], s, L.max_m, Ac, ZL, ZR, st);
+  if (L.supp) launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C, st);
+}
+
+void factor_level(Level& L, cudaStream_t st) {
+  cudaMemsetAsync(L.status, 0x7f, std::max(1, L.nsys) * sizeof(int), st);
+  if (L.f32)
+    factor_level_t<float>(L, st);
+  else
+    factor_level_t<double>(L, st);
+  if (L.supp) factor_level(*L.supp, st);
+}
+
+// Solve with resident factors: F -> X for every system of the level.
+template <typename T>
+static void solve_level_t(Level& L, const double* F, double* X, cudaStream_t st) {
+  T* z = static_cast<T*>(L.z);
+  const T* G = static_cast<const T*>(L.G);
+  const T* Ac = static_cast<const T*>(L.Acal);
+  for (int t = 0; t < L.Lmax; ++t)
+    launch_fwd_solve<T>(L.d_parts, L.active_fwd[t], t, L.max_m, L.max_r, L.A, G, F, z, st);
+  for (int s = 0; s + 1 < L.Lmax; ++s)
+    launch_back_solve<T>(L.d_parts, L.active_back[s], s, L.max_m, L.max_r, Ac, z, st);
+  if (L.supp) {
+    launch_assemble_f<T>(L.d_seps, L.nseps, L.max_m, L.max_r, L.A, L.C, F, z, L.supp->F, st);
+    solve_level(*L.supp, L.supp->F, L.supp->X, st);
+  }
+  launch_backsub<T>(L.d_parts, L.nparts, L.Lmax, L.max_m, L.max_r, static_cast<const T*>(L.ZL),
+                    static_cast<const T*>(L.ZR), z, L.supp ? L.supp->X : nullptr, X, st);
+  if (L.supp) launch_sep_copy(L.d_seps, L.nseps, L.max_m, L.max_r, L.supp->X, X, st);
+}
+
+void solve_level(Level& L, const double* F, double* X, cudaStream_t st) {
+  if (L.f32)
+    solve_level_t<float>(L, F, X, st);
+  else
+    solve_level_t<double>(L, F, X, st);
+}
+
+// first failing block row per system (host check after a factorisation)
+static int check_status(Level& L, cudaStream_t st, int depth) {
+  std::vector<int> h(std::max(1, L.nsys));
+  DM_CUDA(cudaMemcpyAsync(h.data(), L.status, h.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DM_CUDA(cudaStreamSynchronize(st));
+  for (int s = 0; s < L.nsys; ++s)
+    if (h[s] != 0x7f7f7f7f)
+      return set_error(DM_ESINGULAR, "singular pivot: level %d, system %d, block row %d (0-based)", depth, s,
+                       h[s] - 1);
+  if (L.supp) return check_status(*L.supp, st, depth + 1);
+  return DM_OK;
+}
+
+// algorithmic flops (2 per multiply-add) of the level's factor and solve kernels
+void level_flops(const Level& L, double* ffac, double* fsol) {
+  double f = 0, g = 0;
+  for (const PartDesc& p : L.parts) {
+    const double m3 = 2.0 * p.m * (double)p.m * p.m, m2r = 2.0 * p.m * (double)p.m * p.r;
+    const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
+    f += p.L * m3;                                   // inversions
+    f += (p.L - 1) * m3 * 2 + (hr ? m3 : 0);         // Acal and D, right-spike bottom block
+    if (hl) f += p.L * m3 + (p.L - 1) * m3;          // left spike forward
+    if (hl) f += (p.L - 1) * m3;                     // left spike backward
+    if (hr) f += (p.L - 1) * m3;                     // right spike backward
+    g += p.L * m2r + (p.L - 1) * m2r + (p.L - 1) * m2r;  // z forward and backward
+    g += ((hl ? 1 : 0) + (hr ? 1 : 0)) * p.L * m2r;       // back-substitution
+  }
+  for (const SepDesc& s : L.seps) {
+    const double m3 = 2.0 * s.m * (double)s.m * s.m, m2r = 2.0 * s.m * (double)s.m * s.r;
+    f += 2 * m3 + ((s.flags & HAS_HA) ? m3 : 0) + ((s.flags & HAS_HC) ? m3 : 0);
+    g += 2 * m2r;
+  }
+  if (L.supp) {
+    double a, b;
+    level_flops(*L.supp, &a, &b);
+    f += a;
+    g += b;
+  }
+  *ffac = f;
+  *fsol = g;
+}
+
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return DM_OK;
+  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  return DM_OK;
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return DM_OK;
+  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  return DM_OK;
+}
+
+int Plan::init(const std::vector<SysSpec>& specs, int prec) {
+  precision = prec;
+  int rc = top.build(specs, prec != DM_FP64);
+  if (rc) return rc;
+  DM_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
+  stream = own_stream;
+  rc = top.allocate();
+  if (rc) return rc;
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(DM_ENOMEM, "cudaMalloc(%zu bytes) failed", bytes);
+    }
+    return DM_OK;
+  };
+  if ((rc = alloc((void**)&R, top.nvec * sizeof(double)))) return rc;
+  if ((rc = alloc((void**)&Dx, top.nvec * sizeof(double)))) return rc;
+  if ((rc = alloc((void**)&nrm, (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double)))) return rc;
+  h_nrm.assign((size_t)std::max(1, top.nsys) * 4 * kMaxR, 0.0);
+  relres.assign(std::max(1, top.nsys), 0.0);
+  level_flops(top, &factor_flops, &solve_flops);
+  device_bytes = top.bytes_needed() + 2 * top.nvec * sizeof(double);
+  return DM_OK;
+}
+
+Plan::~Plan() {
+  if (R) cudaFree(R);
+  if (Dx) cudaFree(Dx);
+  if (nrm) cudaFree(nrm);
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+int Plan::factor(const double* A, const double* B, const double* C) {
+  cudaStream_t st = stream;
+  int rc;
+  if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
+  if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
+  if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
+  factor_level(top, st);
+  DM_CUDA(cudaGetLastError());
+  rc = check_status(top, st, 0);
+  factored = (rc == DM_OK);
+  return rc;
+}
+
+// per-system max over columns of sqrt(num/den) from the device norm array
+static double col_ratio(const std::vector<double>& h, int s, int r, int num, int den) {
+  double worst = 0.0;
+  for (int c = 0; c < r; ++c) {
+    const double a = h[(size_t)s * 4 * kMaxR + num * kMaxR + c];
+    const double b = h[(size_t)s * 4 * kMaxR + den * kMaxR + c];
+    const double q = b > 0 ? std::sqrt(a / b) : std::sqrt(a);
+    worst = std::max(worst, q);
+  }
+  return worst;
+}
+
+int Plan::solve_device(const double* b_dev, double* x_dev) {
+  cudaStream_t st = stream;
+  const size_t nb = (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double);
+  if (precision == DM_FP64) {
+    solve_level(top, b_dev, x_dev, st);
+    DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
+    launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev, b_dev, R, nrm, st);
+    DM_CUDA(cudaGetLastError());
+    DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
+    DM_CUDA(cudaStreamSynchronize(st));
+    last_iters = 1;
+    last_corr = 0.0;
+    for (int s = 0; s < top.nsys; ++s) relres[s] = col_ratio(h_nrm, s, top.spec[s].r, 0, 1);
+    return DM_OK;
+  }
+  // iterative refinement: x_0 = 0, r_0 = b; x_{i+1} = x_i + M^{-1} r_i with
+  // M^{-1} the float32-factor DM solve; r in float64.
+  DM_CUDA(cudaMemsetAsync(x_dev, 0, top.nvec * sizeof(double), st));
+  const double* rhs = b_dev;
+  int rc = DM_ENOTCONV;
+  int it = 0;
+  double corr = 0.0;
+  for (it = 1; it <= max_iters; ++it) {
+    solve_level(top, rhs, Dx, st);
+    DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
+    launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, st);
+    launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev, b_dev, R, nrm, st);
+    DM_CUDA(cudaGetLastError());
+    DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
+    DM_CUDA(cudaStreamSynchronize(st));
+    rhs = R;
+    corr = 0.0;
+    bool bad = false;
+    for (int s = 0; s < top.nsys; ++s) {
+      const double c = col_ratio(h_nrm, s, top.spec[s].r, 2, 3);
+      corr = std::max(corr, c);
+      relres[s] = col_ratio(h_nrm, s, top.spec[s].r, 0, 1);
+      if (!std::isfinite(c) || !std::isfinite(relres[s])) bad = true;
+    }
+    if (bad) {
+      rc = set_error(DM_ENOTCONV, "refinement diverged (non-finite correction) at iteration %d", it);
+      break;
+    }
+    if (corr <= tol) {
+      rc = DM_OK;
+      break;
+    }
+  }
+  last_iters = std::min(it, max_iters);
+  last_corr = corr;
+  if (rc == DM_ENOTCONV && g_last_error.find("refinement") == std::string::npos)
+    set_error(DM_ENOTCONV, "refinement stopped after %d iterations: ||dx||/||x|| = %.3e > tol %.1e",
+              last_iters, corr, tol);
+  return rc;
+}
+
+int Plan::solve(const double* b, double* x, double* relres_out) {
+  if (!factored) return set_error(DM_ESTATE, "dm_solve before a successful dm_factor");
+  cudaStream_t st = stream;
+  int rc;
+  const size_t vb = top.nvec * sizeof(double);
+  if ((rc = copy_in(top.F, b, vb, st))) return rc;
+  rc = solve_device(top.F, top.X);
+  if (rc != DM_OK && rc != DM_ENOTCONV) return rc;
+  int rc2 = copy_out(x, top.X, vb, st);
+  if (rc2) return rc2;
+  DM_CUDA(cudaStreamSynchronize(st));
+  if (relres_out)
+    for (int s = 0; s < top.nsys; ++s) relres_out[s] = relres[s];
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// partition plan and tuner seeds (Section 2, Section 5)
+void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps) {
+  starts.clear();
+  lens.clear();
+  seps.clear();
+  const int rows = N - (P - 1);
+  const int base = rows / P, extra = rows % P;
+  int r = 0;
+  for (int k = 0; k < P; ++k) {
+    const int L = base + (k < extra ? 1 : 0);
+    starts.push_back(r);
+    lens.push_back(L);
+    r += L;
+    if (k < P - 1) seps.push_back(r++);
+  }
+}
+
+// Eq. (MAXSpeedP): P* = sqrt((N+1)/3 (5 + 2/(1 + l/n))), clamped to 1..(N+1)/2.
+int tuner_seed_p(int N, int m, int r) {
+  const double c = 5.0 + 2.0 / (1.0 + (double)r / m);
+  int P = (int)std::lround(std::sqrt((N + 1) / 3.0 * c));
+  P = std::max(1, std::min(P, (N + 1) / 2));
+  return P;
+}
+
+// Eq. (SuppMatrM) with its boundary case m = P/3 when (P - m)/m < 2, clamped so
+// that each of the Ms supplementary rows' subsystems keeps at least one row.
+int supp_partitions(int Ms, int P, int r, int m) {
+  const double c = 5.0 + 2.0 / (1.0 + (double)r / m);
+  double p2 = std::sqrt(P / 3.0 * c);
+  if ((P - p2) / p2 < 2.0) p2 = P / 3.0;
+  int q = (int)std::lround(p2);
+  q = std::min(q, (Ms + 1) / 2);
+  return std::max(q, 1);
+}
+
+int make_spec(int N, int m, int r, int P, int levels, SysSpec* out) {
+  if (N < 1 || m < 1 || r < 1) return set_error(DM_EINVAL, "N, m, nrhs must be >= 1 (got %d, %d, %d)", N, m, r);
+  if (m > kMaxM) return set_error(DM_EINVAL, "block size m = %d exceeds the limit %d", m, kMaxM);
+  if (r > kMaxR) return set_error(DM_EINVAL, "nrhs = %d exceeds the limit %d", r, kMaxR);
+  if (P < 0 || levels < 0) return set_error(DM_EINVAL, "P and levels must be >= 0");
+  if (P == 0) P = tuner_seed_p(N, m, r);
+  if (P > 1 && 2 * P - 1 > N)
+    return set_error(DM_EINVAL, "P = %d too large for N = %d: every subsystem needs >= 1 row (P <= (N+1)/2)", P, N);
+  if (levels == 0) levels = (P >= 21) ? 2 : 1;   // Section 5.2.1: DM on the supplementary system pays from P >= 21
+  SysSpec s;
+  s.N = N;
+  s.m = m;
+  s.r = r;
+  s.P = P;
+  s.levels = levels;
+  s.P2 = 1;
+  if (P > 1 && levels > 1) s.P2 = supp_partitions(P - 1, P, r, m);
+  if (s.P2 <= 1) s.levels = (P > 1 ? std::min(levels, 1) : levels), s.P2 = 1;
+  if (P == 1) s.levels = 1;
+  *out = s;
+  return DM_OK;
+}
+
+}  // namespace dm
+
+// ===========================================================================
+// extern "C" entry points
+using namespace dm;
+
+struct dm_plan_s {
+  Plan plan;
+};
+
+extern "C" {
+
+const char* dm_last_error(void) { return g_last_error.c_str(); }
+
+int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision) {
+  if (!out) return set_error(DM_EINVAL, "out is NULL");
+  if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
+    return set_error(DM_EINVAL, "unknown precision %d", precision);
+  if (precision == DM_TF32 || precision == DM_BF16X3)
+    return set_error(DM_EINVAL, "precision %d needs the tcgen05 kernels, not in this build", precision);
+  SysSpec s;
+  int rc = make_spec(N, m, nrhs, P, levels, &s);
+  if (rc) return rc;
+  std::unique_ptr<dm_plan_s> p(new dm_plan_s());
+  rc = p->plan.init(std::vector<SysSpec>{s}, precision);
+  if (rc) return rc;
+  *out = p.release();
+  return DM_OK;
+}
+
+int dm_plan_batch(dm_plan_t* out, int count, const int* N, const int* m, const int* nrhs, int precision) {
+  if (!out || count < 1 || !N || !m || !nrhs) return set_error(DM_EINVAL, "invalid batch arguments");
+  if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
+    return set_error(DM_EINVAL, "unknown precision %d", precision);
+  std::vector<SysSpec> specs(count);
+  for (int s = 0; s < count; ++s) {
+    int rc = make_spec(N[s], m[s], nrhs[s], 0, 0, &specs[s]);
+    if (rc) return rc;
+  }
+  std::unique_ptr<dm_plan_s> p(new dm_plan_s());
+  int rc = p->plan.init(specs, precision);
+  if (rc) return rc;
+  *out = p.release();
+  return DM_OK;
+}
+
+int dm_plan_tune(int N, int m, int nrhs, int* P, int* levels, int* P2) {
+  if (!P || !levels || !P2) return set_error(DM_EINVAL, "NULL argument to dm_plan_tune");
+  SysSpec s;
+  int rc = make_spec(N, m, nrhs, *P, *levels, &s);
+  if (rc) return rc;
+  *P = s.P;
+  *levels = s.levels;
+  *P2 = s.P2;
+  return DM_OK;
+}
+
+int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C) {
+  if (!plan || !A || !B || !C) return set_error(DM_EINVAL, "NULL argument to dm_factor");
+  return plan->plan.factor(A, B, C);
+}
+
+int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out) {
+  if (!plan || !b || !x) return set_error(DM_EINVAL, "NULL argument to dm_solve");
+  return plan->plan.solve(b, x, relres_out);
+}
+
+int dm_set_stream(dm_plan_t plan, void* cuda_stream) {
+  if (!plan) return set_error(DM_EINVAL, "NULL plan");
+  plan->plan.stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : plan->plan.own_stream;
+  return DM_OK;
+}
+
+int dm_set_refinement(dm_plan_t plan, double tol, int max_iters) {
+  if (!plan || !(tol > 0) || max_iters < 1) return set_error(DM_EINVAL, "invalid refinement settings");
+  plan->plan.tol = tol;
+  plan->plan.max_iters = max_iters;
+  return DM_OK;
+}
+
+int dm_plan_query(dm_plan_t plan, dm_plan_info* info) {
+  if (!plan || !info) return set_error(DM_EINVAL, "NULL argument to dm_plan_query");
+  const Plan& p = plan->plan;
+  const SysSpec& s = p.top.spec[0];
+  info->N = s.N;
+  info->m = s.m;
+  info->nrhs = s.r;
+  info->P = s.P;
+  info->levels = s.levels;
+  info->P2 = s.P2;
+  info->precision = p.precision;
+  info->count = p.top.nsys;
+  info->last_iters = p.last_iters;
+  info->max_rows = p.top.Lmax;
+  info->device_bytes = p.device_bytes;
+  info->last_relres = 0;
+  for (int i = 0; i < p.top.nsys; ++i) info->last_relres = std::max(info->last_relres, p.relres[i]);
+  info->last_correction = p.last_corr;
+  info->factor_flops = p.factor_flops;
+  info->solve_flops = p.solve_flops;
+  return DM_OK;
+}
+
+void dm_destroy(dm_plan_t plan) { delete plan; }
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the solver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dm {
+
+// Flags of a subsystem (partition) descriptor.
+enum : int {
+  HAS_LEFT = 1,   // subsystem k > 0: spike for h^{k-1} (top block A of its first row)
+  HAS_RIGHT = 2,  // subsystem k < P-1: spike for h^k (bottom block C of its last row)
+};
+
+// One subsystem S^k of one system (Section 2).  Its rows are contiguous in
+// the system's row space; block offsets are element offsets into the level's
+// [rows][m][m] arrays, vector offsets into its [rows][m][nrhs] arrays.
+struct PartDesc {
+  long long blk;    // offset of the subsystem's first row block
+  long long vec;    // offset of the subsystem's first right-hand-side block
+  long long hprev;  // offset of h^{k-1} in the supplementary level's vectors (HAS_LEFT)
+  long long hnext;  // offset of h^k in the supplementary level's vectors (HAS_RIGHT)
+  int m, r, L;      // block size, right-hand-side columns, rows of the subsystem
+  int flags;
+  int sys;          // system index within the level
+  int row0;         // row index (within its system) of the subsystem's first row
+};
+
+// Separator row j of one system (between subsystems j and j+1).
+enum : int { HAS_HA = 1, HAS_HC = 2 };
+struct SepDesc {
+  long long blk_q, vec_q;        // the separator row q
+  long long blk_prev, vec_prev;  // row q-1 (last row of subsystem j)
+  long long blk_next, vec_next;  // row q+1 (first row of subsystem j+1)
+  long long hblk, hvec;          // row j of the supplementary system (its level's offsets)
+  int m, r, flags, sys;
+};
+
+// One system of a level (for row-parallel kernels such as the residual).
+struct SysDesc {
+  long long blk, vec;  // offsets of row 0
+  int N, m, r, pad;
+};
+
+// ---- launchers (dm_kernels.cu); T = double or float (factor storage type)
+template <typename T>
+void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G, int* status,
+                int max_m, cudaStream_t st);
+template <typename T>
+void launch_fwd_factor(const PartDesc* parts, int nparts, int t, int max_m, const double* A,
+                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st);
+template <typename T>
+void launch_back_factor(const PartDesc* parts, int nparts, int s, int max_m, const T* Acal, T* ZL,
+                        T* ZR, cudaStream_t st);
+template <typename T>
+void launch_fwd_solve(const PartDesc* parts, int nparts, int t, int max_m, int max_r,
+                      const double* A, const T* G, const double* F, T* z, cudaStream_t st);
+template <typename T>
+void launch_back_solve(const PartDesc* parts, int nparts, int s, int max_m, int max_r,
+                       const T* Acal, T* z, cudaStream_t st);
+template <typename T>
+void launch_assemble_h(const SepDesc* seps, int nseps, int max_m, const double* A, const double* B,
+                       const double* C, const T* ZL, const T* ZR, double* HA, double* HB,
+                       double* HC, cudaStream_t st);
+template <typename T>
+void launch_assemble_f(const SepDesc* seps, int nseps, int max_m, int max_r, const double* A,
+                       const double* C, const double* F, const T* z, double* fh, cudaStream_t st);
+template <typename T>
+void launch_backsub(const PartDesc* parts, int nparts, int Lmax, int max_m, int max_r, const T* ZL,
+                    const T* ZR, const T* z, const double* h, double* x, cudaStream_t st);
+void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const double* h,
+                     double* x, cudaStream_t st);
+// r = b - T x (float64), per-system column norms: nrm[s*4*64 + 0*64 + c] = ||r_c||^2,
+// [1] = ||b_c||^2 (both accumulated by atomics; zeroed by the caller).
+void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* A,
+                     const double* B, const double* C, const double* x, const double* b, double* r,
+                     double* nrm, cudaStream_t st);
+// x += d, nrm[2] += ||d_c||^2, nrm[3] += ||x_c||^2 (after the update)
+void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
+                       double* x, double* nrm, cudaStream_t st);
+
+constexpr int kMaxM = 512;
+constexpr int kMaxR = 64;
+
+}  // namespace dm

@@ -1,0 +1,839 @@
+// Level-synchronous block kernels of the decomposition method (SIMT path).
+//
+// Every kernel works on a table of subsystems (PartDesc) or separators
+// (SepDesc) so that one launch advances the same step of every subsystem of
+// every system in a level: step t of the forward sweep processes row t of all
+// subsystems at once (Section 3's recurrences run down each subsystem, the
+// subsystems are independent, Section 2).  Block products are computed in
+// "panels": all m rows of an m x W slab of the result, W = 32 (m <= 256) or
+// 16 (m <= 512) columns, so a CTA can chain two products on the same slab
+// (e.g. Acal_t = G_t C_t followed by D_{t+1} = B_{t+1} - A_{t+1} Acal_t).
+//
+// T is the factor storage/arithmetic type: double for DM_FP64 and for every
+// supplementary level, float for the mixed-precision top level (its block
+// products on CUDA cores; the tcgen05 kernels replace them where enabled).
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "dm_internal.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int kThreads = 256;  // 16 x 16 thread grid of the panel products
+
+// ---------------------------------------------------------------------------
+// Panel product core.  Computes rows r0..r0+63 of L (m x m, row-major, leading
+// dimension m, element type TL) times Rs (m x W in shared memory, row stride
+// W), accumulating into acc.  Thread (ty, tx) owns rows r0 + ty + 16a (a < 4)
+// and columns tx + 16b (b < W/16).  Lc is a 64 x 17 staging tile for L.
+template <typename T, typename TL, int W>
+__device__ __forceinline__ void mm_rowblock(T (&acc)[4][W / 16], const TL* __restrict__ L, int m,
+                                            int r0, const T* __restrict__ Rs, T* __restrict__ Lc) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int k0 = 0; k0 < m; k0 += 16) {
+    for (int e = tid; e < 64 * 16; e += kThreads) {
+      const int rr = e >> 4, kk = e & 15, row = r0 + rr, col = k0 + kk;
+      Lc[rr * 17 + kk] = (row < m && col < m) ? (T)L[(long long)row * m + col] : (T)0;
+    }
+    __syncthreads();
+    const int kmax = min(16, m - k0);
+    for (int kk = 0; kk < kmax; ++kk) {
+      T lv[4], rv[W / 16];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) lv[a] = Lc[(ty + 16 * a) * 17 + kk];
+#pragma unroll
+      for (int b = 0; b < W / 16; ++b) rv[b] = Rs[(k0 + kk) * W + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < W / 16; ++b) acc[a][b] = fma(lv[a], rv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+}
+
+// out = L1 * R1 (+ L2 * R2 when L2 != nullptr), delivered element by element
+// to epi(row, col, value) for row < m and every col < W.
+template <typename T, typename TL1, typename TL2, int W, typename Epi>
+__device__ __forceinline__ void panel_mm(int m, const TL1* L1, const T* R1, const TL2* L2,
+                                         const T* R2, T* Lc, Epi epi) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int r0 = 0; r0 < m; r0 += 64) {
+    T acc[4][W / 16];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < W / 16; ++b) acc[a][b] = (T)0;
+    mm_rowblock<T, TL1, W>(acc, L1, m, r0, R1, Lc);
+    if (L2 != nullptr) mm_rowblock<T, TL2, W>(acc, L2, m, r0, R2, Lc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int row = r0 + ty + 16 * a;
+      if (row < m) {
+#pragma unroll
+        for (int b = 0; b < W / 16; ++b) epi(row, tx + 16 * b, acc[a][b]);
+      }
+    }
+  }
+}
+
+// Rs[k][c] = scale * src[k * ld + c0 + c] for k < rows, c < W; zero past `cols`.
+template <typename T, typename TS, int W>
+__device__ __forceinline__ void load_panel(T* Rs, const TS* __restrict__ src, int rows, int ld,
+                                           int c0, int cols, T scale) {
+  for (int e = threadIdx.x; e < rows * W; e += kThreads) {
+    const int k = e / W, c = e - k * W;
+    Rs[e] = (c0 + c < cols) ? scale * (T)src[(long long)k * ld + c0 + c] : (T)0;
+  }
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t panel_smem(int m, int W, int npanels) {
+  return sizeof(T) * ((size_t)npanels * m * W + 64 * 17);
+}
+
+template <int W>
+__host__ __device__ constexpr int ntiles(int cols) { return (cols + W - 1) / W; }
+
+// ---------------------------------------------------------------------------
+// Block inverse G_t = D_t^{-1} by Gauss-Jordan elimination with partial
+// (row) pivoting, in place (m^3 multiply-adds, the paper's cost for an
+// inversion in Section 4).  One CTA per subsystem.  D_t was written into G's
+// row-t slot by the previous forward step; at t = 0 it is B of the
+// subsystem's first row.  The working matrix lives in shared memory when it
+// fits, else in the G slot itself (global memory, L2-resident).
+template <typename T>
+__global__ void __launch_bounds__(512) k_inv(const PartDesc* __restrict__ parts, int t,
+                                             const double* __restrict__ B, T* __restrict__ G,
+                                             int* __restrict__ status, int smem_max_m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.x];
+  if (t >= p.L) return;
+  const int m = p.m;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const long long o = p.blk + (long long)t * m * m;
+  T* g = G + o;
+  int* perm = reinterpret_cast<int*>(smem_raw);
+  int* idx = perm + kMaxM;
+  T* colk = reinterpret_cast<T*>(idx + kMaxM);
+  T* rowk = colk + kMaxM;
+  __shared__ int s_p, s_bad;
+  __shared__ T s_inv, s_akk, s_apk;
+  const bool in_smem = m <= smem_max_m;
+  T* a;
+  int lda;
+  if (in_smem) {
+    a = rowk + kMaxM;
+    lda = m + 1;
+  } else {
+    a = g;
+    lda = m;
+  }
+  if (tid == 0) s_bad = 0;
+  const int i0 = tid >> 5, istep = nthr >> 5, j0 = tid & 31;
+  if (t == 0) {
+    const double* bsrc = B + o;
+    for (int i = i0; i < m; i += istep)
+      for (int j = j0; j < m; j += 32) a[i * lda + j] = (T)bsrc[(long long)i * m + j];
+  } else if (in_smem) {
+    for (int i = i0; i < m; i += istep)
+      for (int j = j0; j < m; j += 32) a[i * lda + j] = g[(long long)i * m + j];
+  }
+  __syncthreads();
+
+  for (int k = 0; k < m; ++k) {
+    if (tid < 32) {
+      // pivot search over rows k..m-1 of column k; ties go to the lowest row
+      T best = (T)-1;
+      int bi = k;
+      for (int i = k + tid; i < m; i += 32) {
+        const T v = fabs(a[i * lda + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        const T akk = a[k * lda + k], apk = a[bi * lda + k];
+        T inv = (T)1 / apk;
+        if (!(fabs(apk) > (T)0) || !isfinite(inv)) {
+          s_bad = 1;
+          inv = (T)0;
+        }
+        perm[k] = bi;
+        s_p = bi;
+        s_inv = inv;
+        s_akk = akk;
+        s_apk = apk;
+      }
+    }
+    __syncthreads();
+    const int pr = s_p;
+    const T inv = s_inv;
+    for (int j = tid; j < m; j += nthr) {
+      const T vk = a[k * lda + j], vp = a[pr * lda + j];
+      if (pr != k) {
+        a[k * lda + j] = vp;
+        a[pr * lda + j] = vk;
+      }
+      rowk[j] = vp * inv;
+    }
+    for (int i = tid; i < m; i += nthr)
+      colk[i] = (i == k) ? s_apk : (i == pr ? s_akk : a[i * lda + k]);
+    __syncthreads();
+    for (int i = i0; i < m; i += istep) {
+      const T ci = colk[i];
+      if (i == k) {
+        for (int j = j0; j < m; j += 32) a[i * lda + j] = (j == k) ? inv : rowk[j];
+      } else {
+        for (int j = j0; j < m; j += 32)
+          a[i * lda + j] = (j == k) ? -ci * inv : fma(-ci, rowk[j], a[i * lda + j]);
+      }
+    }
+    __syncthreads();
+  }
+  // D^{-1} = inv(Pi D) Pi: undo the row exchanges on the columns, last first.
+  if (in_smem) {
+    if (tid == 0) {
+      for (int c = 0; c < m; ++c) idx[c] = c;
+      for (int k = m - 1; k >= 0; --k) {
+        const int q = perm[k];
+        const int tmp = idx[k];
+        idx[k] = idx[q];
+        idx[q] = tmp;
+      }
+    }
+    __syncthreads();
+    for (int i = i0; i < m; i += istep)
+      for (int j = j0; j < m; j += 32) g[(long long)i * m + j] = a[i * lda + idx[j]];
+  } else {
+    for (int k = m - 1; k >= 0; --k) {
+      const int q = perm[k];
+      if (q != k) {
+        for (int i = tid; i < m; i += nthr) {
+          const T v = a[i * lda + k];
+          a[i * lda + k] = a[i * lda + q];
+          a[i * lda + q] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Forward step t of the factor sweep (Section 3, applied to subsystem S^k
+// with right-hand sides W_R^k, Eq. e231).  Tile types:
+//   0: Acal_t[:, J] = G_t C_t[:, J], then D_{t+1}[:, J] = B_{t+1}[:, J] - A_{t+1} Acal_t[:, J]
+//      (written into G's row t+1 slot for the next inversion).  At the last
+//      row of a subsystem with a right spike the product G_t C_t is the
+//      spike's only non-zero forward block and goes to ZR.
+//   1: left spike (k > 0): Bcal_t = G_t A_first at t = 0, else G_t (-A_t Bcal_{t-1}).
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_fwd_factor(const PartDesc* __restrict__ parts, int t,
+                                                         int tiles, const double* __restrict__ A,
+                                                         const double* __restrict__ B,
+                                                         const double* __restrict__ C,
+                                                         T* __restrict__ G, T* __restrict__ Acal,
+                                                         T* __restrict__ ZL, T* __restrict__ ZR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  if (t >= p.L) return;
+  const int m = p.m;
+  const int type = blockIdx.x / tiles, c0 = (blockIdx.x - type * tiles) * W;
+  if (c0 >= m) return;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Xs = Rs + m * W;
+  T* Lc = Xs + m * W;
+  const long long mm = (long long)m * m;
+  const long long o = p.blk + (long long)t * mm;
+  const T* Gt = G + o;
+  if (type == 0) {
+    const bool last = (t == p.L - 1);
+    if (last && !(p.flags & HAS_RIGHT)) return;
+    load_panel<T, double, W>(Rs, C + o, m, m, c0, m, (T)1);
+    __syncthreads();
+    T* dst = last ? ZR + o : Acal + o;
+    panel_mm<T, T, T, W>(m, Gt, Rs, (const T*)nullptr, (const T*)nullptr, Lc,
+                         [&](int row, int col, T v) {
+                           Xs[row * W + col] = v;
+                           if (c0 + col < m) dst[(long long)row * m + c0 + col] = v;
+                         });
+    if (last) return;
+    __syncthreads();
+    const double* Bn = B + o + mm;
+    T* Dn = G + o + mm;
+    panel_mm<T, double, double, W>(m, A + o + mm, Xs, (const double*)nullptr, (const T*)nullptr, Lc,
+                                   [&](int row, int col, T v) {
+                                     if (c0 + col < m) {
+                                       const long long e = (long long)row * m + c0 + col;
+                                       Dn[e] = (T)Bn[e] - v;
+                                     }
+                                   });
+  } else {
+    if (!(p.flags & HAS_LEFT)) return;
+    if (t == 0) {
+      load_panel<T, double, W>(Rs, A + o, m, m, c0, m, (T)1);
+    } else {
+      load_panel<T, T, W>(Xs, ZL + o - mm, m, m, c0, m, (T)1);
+      __syncthreads();
+      panel_mm<T, double, double, W>(m, A + o, Xs, (const double*)nullptr, (const T*)nullptr, Lc,
+                                     [&](int row, int col, T v) { Rs[row * W + col] = -v; });
+    }
+    __syncthreads();
+    T* dst = ZL + o;
+    panel_mm<T, T, T, W>(m, Gt, Rs, (const T*)nullptr, (const T*)nullptr, Lc,
+                         [&](int row, int col, T v) {
+                           if (c0 + col < m) dst[(long long)row * m + c0 + col] = v;
+                         });
+  }
+}
+
+// Backward step s of the spike sweeps, row t = L-2-s of each subsystem:
+//   0: ZL_t = Bcal_t - Acal_t ZL_{t+1}   (in place over the forward blocks)
+//   1: ZR_t = -Acal_t ZR_{t+1}           (the right spike's forward blocks above its last row are zero)
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_back_factor(const PartDesc* __restrict__ parts, int s,
+                                                          int tiles, const T* __restrict__ Acal,
+                                                          T* __restrict__ ZL, T* __restrict__ ZR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  const int t = p.L - 2 - s;
+  if (t < 0) return;
+  const int m = p.m;
+  const int type = blockIdx.x / tiles, c0 = (blockIdx.x - type * tiles) * W;
+  if (c0 >= m) return;
+  if (type == 0 && !(p.flags & HAS_LEFT)) return;
+  if (type == 1 && !(p.flags & HAS_RIGHT)) return;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Lc = Rs + m * W;
+  const long long mm = (long long)m * m;
+  const long long o = p.blk + (long long)t * mm;
+  T* Y = (type == 0 ? ZL : ZR) + o;
+  load_panel<T, T, W>(Rs, Y + mm, m, m, c0, m, (T)1);
+  __syncthreads();
+  const bool keep = (type == 0);
+  panel_mm<T, T, T, W>(m, Acal + o, Rs, (const T*)nullptr, (const T*)nullptr, Lc,
+                       [&](int row, int col, T v) {
+                         if (c0 + col < m) {
+                           const long long e = (long long)row * m + c0 + col;
+                           Y[e] = (keep ? Y[e] : (T)0) - v;
+                         }
+                       });
+}
+
+// Forward step t for a right-hand side: z_t = G_t (F_t - A_t z_{t-1}).
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_fwd_solve(const PartDesc* __restrict__ parts, int t,
+                                                        int tiles, const double* __restrict__ A,
+                                                        const T* __restrict__ G,
+                                                        const double* __restrict__ F,
+                                                        T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  if (t >= p.L) return;
+  const int m = p.m, r = p.r;
+  const int c0 = blockIdx.x * W;
+  if (c0 >= r) return;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Xs = Rs + m * W;
+  T* Lc = Xs + m * W;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  const double* Ft = F + v;
+  if (t == 0) {
+    load_panel<T, double, W>(Rs, Ft, m, r, c0, r, (T)1);
+  } else {
+    load_panel<T, T, W>(Xs, z + v - mr, m, r, c0, r, (T)1);
+    __syncthreads();
+    panel_mm<T, double, double, W>(m, A + o, Xs, (const double*)nullptr, (const T*)nullptr, Lc,
+                                   [&](int row, int col, T val) {
+                                     Rs[row * W + col] =
+                                         (c0 + col < r) ? (T)Ft[(long long)row * r + c0 + col] - val : (T)0;
+                                   });
+  }
+  __syncthreads();
+  T* dst = z + v;
+  panel_mm<T, T, T, W>(m, G + o, Rs, (const T*)nullptr, (const T*)nullptr, Lc,
+                       [&](int row, int col, T val) {
+                         if (c0 + col < r) dst[(long long)row * r + c0 + col] = val;
+                       });
+}
+
+// Backward step s for a right-hand side: z_t -= Acal_t z_{t+1}, t = L-2-s.
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_back_solve(const PartDesc* __restrict__ parts, int s,
+                                                         int tiles, const T* __restrict__ Acal,
+                                                         T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  const int t = p.L - 2 - s;
+  if (t < 0) return;
+  const int m = p.m, r = p.r;
+  const int c0 = blockIdx.x * W;
+  if (c0 >= r) return;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Lc = Rs + m * W;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  T* Y = z + v;
+  load_panel<T, T, W>(Rs, Y + mr, m, r, c0, r, (T)1);
+  __syncthreads();
+  panel_mm<T, T, T, W>(m, Acal + o, Rs, (const T*)nullptr, (const T*)nullptr, Lc,
+                       [&](int row, int col, T val) {
+                         if (c0 + col < r) {
+                           const long long e = (long long)row * r + c0 + col;
+                           Y[e] = Y[e] - val;
+                         }
+                       });
+}
+
+// Supplementary matrix (Eq. e2311), separator j at row q, in float64:
+//   0: HB_j = B_q - A_q ZR^j[q-1] - C_q ZL^{j+1}[q+1]
+//   1: HA_j = -A_q ZL^j[q-1]        (j > 0)
+//   2: HC_j = -C_q ZR^{j+1}[q+1]    (j < P-2)
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_assemble_h(const SepDesc* __restrict__ seps, int tiles,
+                                                         const double* __restrict__ A,
+                                                         const double* __restrict__ B,
+                                                         const double* __restrict__ C,
+                                                         const T* __restrict__ ZL,
+                                                         const T* __restrict__ ZR,
+                                                         double* __restrict__ HA,
+                                                         double* __restrict__ HB,
+                                                         double* __restrict__ HC) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SepDesc sp = seps[blockIdx.y];
+  const int m = sp.m;
+  const int type = blockIdx.x / tiles, c0 = (blockIdx.x - type * tiles) * W;
+  if (c0 >= m) return;
+  if (type == 1 && !(sp.flags & HAS_HA)) return;
+  if (type == 2 && !(sp.flags & HAS_HC)) return;
+  double* R1 = reinterpret_cast<double*>(smem_raw);
+  double* R2 = R1 + m * W;
+  double* Lc = R2 + m * W;
+  const double* Aq = A + sp.blk_q;
+  const double* Cq = C + sp.blk_q;
+  if (type == 0) {
+    load_panel<double, T, W>(R1, ZR + sp.blk_prev, m, m, c0, m, 1.0);
+    load_panel<double, T, W>(R2, ZL + sp.blk_next, m, m, c0, m, 1.0);
+    __syncthreads();
+    const double* Bq = B + sp.blk_q;
+    double* dst = HB + sp.hblk;
+    panel_mm<double, double, double, W>(m, Aq, R1, Cq, R2, Lc, [&](int row, int col, double v) {
+      if (c0 + col < m) {
+        const long long e = (long long)row * m + c0 + col;
+        dst[e] = Bq[e] - v;
+      }
+    });
+  } else {
+    const T* Z = (type == 1) ? ZL + sp.blk_prev : ZR + sp.blk_next;
+    const double* Lop = (type == 1) ? Aq : Cq;
+    double* dst = ((type == 1) ? HA : HC) + sp.hblk;
+    load_panel<double, T, W>(R1, Z, m, m, c0, m, 1.0);
+    __syncthreads();
+    panel_mm<double, double, double, W>(m, Lop, R1, (const double*)nullptr, (const double*)nullptr, Lc,
+                                        [&](int row, int col, double v) {
+                                          if (c0 + col < m) dst[(long long)row * m + c0 + col] = -v;
+                                        });
+  }
+}
+
+// Supplementary right-hand side (Eq. e2311): fh_j = F_q - A_q z^j[q-1] - C_q z^{j+1}[q+1].
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_assemble_f(const SepDesc* __restrict__ seps, int tiles,
+                                                         const double* __restrict__ A,
+                                                         const double* __restrict__ C,
+                                                         const double* __restrict__ F,
+                                                         const T* __restrict__ z,
+                                                         double* __restrict__ fh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SepDesc sp = seps[blockIdx.y];
+  const int m = sp.m, r = sp.r;
+  const int c0 = blockIdx.x * W;
+  if (c0 >= r) return;
+  double* R1 = reinterpret_cast<double*>(smem_raw);
+  double* R2 = R1 + m * W;
+  double* Lc = R2 + m * W;
+  load_panel<double, T, W>(R1, z + sp.vec_prev, m, r, c0, r, 1.0);
+  load_panel<double, T, W>(R2, z + sp.vec_next, m, r, c0, r, 1.0);
+  __syncthreads();
+  const double* Fq = F + sp.vec_q;
+  double* dst = fh + sp.hvec;
+  panel_mm<double, double, double, W>(m, A + sp.blk_q, R1, C + sp.blk_q, R2, Lc,
+                                      [&](int row, int col, double v) {
+                                        if (c0 + col < r) {
+                                          const long long e = (long long)row * r + c0 + col;
+                                          dst[e] = Fq[e] - v;
+                                        }
+                                      });
+}
+
+// Back-substitution (Eq. endSolution) for row t of each subsystem, in float64:
+//   x_t = z_t - ZL_t h^{k-1} - ZR_t h^k.
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_backsub(const PartDesc* __restrict__ parts, int tiles,
+                                                      const T* __restrict__ ZL,
+                                                      const T* __restrict__ ZR,
+                                                      const T* __restrict__ z,
+                                                      const double* __restrict__ h,
+                                                      double* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  const int t = blockIdx.x / tiles;
+  if (t >= p.L) return;
+  const int m = p.m, r = p.r;
+  const int c0 = (blockIdx.x - t * tiles) * W;
+  if (c0 >= r) return;
+  double* R1 = reinterpret_cast<double*>(smem_raw);
+  double* R2 = R1 + m * W;
+  double* Lc = R2 + m * W;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
+  if (hl) load_panel<double, double, W>(R1, h + p.hprev, m, r, c0, r, 1.0);
+  if (hr) load_panel<double, double, W>(R2, h + p.hnext, m, r, c0, r, 1.0);
+  __syncthreads();
+  const T* zt = z + v;
+  double* xt = x + v;
+  auto epi = [&](int row, int col, double val) {
+    if (c0 + col < r) {
+      const long long e = (long long)row * r + c0 + col;
+      xt[e] = (double)zt[e] - val;
+    }
+  };
+  if (hl && hr) {
+    panel_mm<double, T, T, W>(m, ZL + o, R1, ZR + o, R2, Lc, epi);
+  } else if (hl) {
+    panel_mm<double, T, T, W>(m, ZL + o, R1, (const T*)nullptr, (const double*)nullptr, Lc, epi);
+  } else if (hr) {
+    panel_mm<double, T, T, W>(m, ZR + o, R2, (const T*)nullptr, (const double*)nullptr, Lc, epi);
+  } else {
+    for (int e = threadIdx.x; e < m * W; e += kThreads) {
+      const int row = e / W, col = e - row * W;
+      if (c0 + col < r) xt[(long long)row * r + c0 + col] = (double)zt[(long long)row * r + c0 + col];
+    }
+  }
+}
+
+__global__ void k_sep_copy(const SepDesc* __restrict__ seps, const double* __restrict__ h,
+                           double* __restrict__ x) {
+  const SepDesc sp = seps[blockIdx.x];
+  const int n = sp.m * sp.r;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) x[sp.vec_q + e] = h[sp.hvec + e];
+}
+
+// ---------------------------------------------------------------------------
+// Residual r_i = b_i - A_i x_{i-1} - B_i x_i - C_i x_{i+1} in float64.  One CTA
+// per block row; a warp per output row reads A/B/C rows coalesced and reduces
+// with shuffles; x_{i-1}, x_i, x_{i+1} are staged in shared memory 16 columns
+// at a time.  Column sums of r^2 and b^2 go to nrm by atomics.
+__global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sys,
+                                                  const double* __restrict__ A,
+                                                  const double* __restrict__ B,
+                                                  const double* __restrict__ C,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ b,
+                                                  double* __restrict__ rout,
+                                                  double* __restrict__ nrm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[2 * kMaxR];
+  const SysDesc sd = sys[blockIdx.y];
+  const int i = blockIdx.x;
+  if (i >= sd.N) return;
+  const int m = sd.m, r = sd.r;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = sd.blk + i * mm, v = sd.vec + i * mr;
+  double* xs = reinterpret_cast<double*>(smem_raw);  // [3][m][16]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 2 * r; e += blockDim.x) red[e] = 0.0;
+  const bool hasA = i > 0, hasC = i < sd.N - 1;
+  for (int c0 = 0; c0 < r; c0 += 16) {
+    const int nc = min(16, r - c0);
+    __syncthreads();
+    for (int e = tid; e < 3 * m * 16; e += blockDim.x) {
+      const int which = e / (m * 16), rem = e - which * m * 16, k = rem >> 4, c = rem & 15;
+      const int row = i - 1 + which;
+      xs[e] = (row >= 0 && row < sd.N && c < nc) ? x[sd.vec + row * mr + (long long)k * r + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int row = warp; row < m; row += 8) {
+      double acc[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+      for (int k = lane; k < m; k += 32) {
+        const double a = hasA ? A[o + (long long)row * m + k] : 0.0;
+        const double bb = B[o + (long long)row * m + k];
+        const double cc = hasC ? C[o + (long long)row * m + k] : 0.0;
+        const double* xm = xs + k * 16;
+        const double* x0 = xm + m * 16;
+        const double* xp = x0 + m * 16;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = fma(a, xm[c], fma(bb, x0[c], fma(cc, xp[c], acc[c])));
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        double s = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        acc[c] = s;
+      }
+      if (lane < nc) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c == lane) s = acc[c];
+        const long long e = v + (long long)row * r + c0 + lane;
+        const double bv = b[e];
+        const double rv = bv - s;
+        rout[e] = rv;
+        atomicAdd(&red[c0 + lane], rv * rv);
+        atomicAdd(&red[r + c0 + lane], bv * bv);
+      }
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < r; c += blockDim.x) {
+    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + c], red[c]);
+    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + kMaxR + c], red[r + c]);
+  }
+}
+
+// x += d per block row, with column sums of d^2 and (updated) x^2.
+__global__ void __launch_bounds__(256) k_axpy_norms(const SysDesc* __restrict__ sys,
+                                                    const double* __restrict__ d,
+                                                    double* __restrict__ x,
+                                                    double* __restrict__ nrm) {
+  __shared__ double red[2 * kMaxR];
+  const SysDesc sd = sys[blockIdx.y];
+  const int i = blockIdx.x;
+  if (i >= sd.N) return;
+  const int r = sd.r;
+  const long long mr = (long long)sd.m * r, v = sd.vec + i * mr;
+  for (int e = threadIdx.x; e < 2 * r; e += blockDim.x) red[e] = 0.0;
+  __syncthreads();
+  for (long long e = threadIdx.x; e < mr; e += blockDim.x) {
+    const double dv = d[v + e];
+    const double xv = x[v + e] + dv;
+    x[v + e] = xv;
+    const int c = (int)(e % r);
+    atomicAdd(&red[c], dv * dv);
+    atomicAdd(&red[r + c], xv * xv);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + 2 * kMaxR + c], red[c]);
+    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + 3 * kMaxR + c], red[r + c]);
+  }
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+int inv_smem_max_m() {
+  // working matrix (m x (m+1)) + perm/idx/colk/rowk, within 227 KB
+  const size_t budget = 227 * 1024 - 2 * kMaxM * sizeof(int) - 2 * kMaxM * sizeof(T) - 256;
+  int m = 1;
+  while ((size_t)(m + 1) * (m + 2) * sizeof(T) <= budget) ++m;
+  return m;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+template <typename T>
+void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G, int* status,
+                int max_m, cudaStream_t st) {
+  if (nparts <= 0) return;
+  const int smax = inv_smem_max_m<T>();
+  const size_t base = 2 * kMaxM * sizeof(int) + 2 * kMaxM * sizeof(T);
+  const size_t bytes = base + (max_m <= smax ? (size_t)max_m * (max_m + 1) * sizeof(T) : 0);
+  allow_smem(k_inv<T>, bytes);
+  const int thr = max_m >= 128 ? 512 : (max_m >= 48 ? 256 : 128);
+  // capacity actually allocated: every block up to max_m fits, or none does
+  const int cap = max_m <= smax ? max_m : 0;
+  k_inv<T><<<nparts, thr, bytes, st>>>(parts, t, B, G, status, cap);
+}
+
+template <typename T>
+void launch_fwd_factor(const PartDesc* parts, int nparts, int t, int max_m, const double* A,
+                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st) {
+  if (nparts <= 0) return;
+  if (max_m <= 256) {
+    constexpr int W = 32;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
+    allow_smem(k_fwd_factor<T, W>, bytes);
+    k_fwd_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, A, B, C, G, Acal, ZL, ZR);
+  } else {
+    constexpr int W = 16;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
+    allow_smem(k_fwd_factor<T, W>, bytes);
+    k_fwd_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, A, B, C, G, Acal, ZL, ZR);
+  }
+}
+
+template <typename T>
+void launch_back_factor(const PartDesc* parts, int nparts, int s, int max_m, const T* Acal, T* ZL,
+                        T* ZR, cudaStream_t st) {
+  if (nparts <= 0) return;
+  if (max_m <= 256) {
+    constexpr int W = 32;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<T>(max_m, W, 1);
+    allow_smem(k_back_factor<T, W>, bytes);
+    k_back_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, s, tiles, Acal, ZL, ZR);
+  } else {
+    constexpr int W = 16;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<T>(max_m, W, 1);
+    allow_smem(k_back_factor<T, W>, bytes);
+    k_back_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, s, tiles, Acal, ZL, ZR);
+  }
+}
+
+template <typename T>
+void launch_fwd_solve(const PartDesc* parts, int nparts, int t, int max_m, int max_r,
+                      const double* A, const T* G, const double* F, T* z, cudaStream_t st) {
+  if (nparts <= 0) return;
+  if (max_r <= 16) {
+    constexpr int W = 16;
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
+    allow_smem(k_fwd_solve<T, W>, bytes);
+    k_fwd_solve<T, W><<<dim3(ntiles<W>(max_r), nparts), kThreads, bytes, st>>>(parts, t, 1, A, G, F, z);
+  } else {
+    constexpr int W = 32;
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
+    allow_smem(k_fwd_solve<T, W>, bytes);
+    k_fwd_solve<T, W><<<dim3(ntiles<W>(max_r), nparts), kThreads, bytes, st>>>(parts, t, 1, A, G, F, z);
+  }
+}
+
+template <typename T>
+void launch_back_solve(const PartDesc* parts, int nparts, int s, int max_m, int max_r,
+                       const T* Acal, T* z, cudaStream_t st) {
+  if (nparts <= 0) return;
+  if (max_r <= 16) {
+    constexpr int W = 16;
+    const size_t bytes = panel_smem<T>(max_m, W, 1);
+    allow_smem(k_back_solve<T, W>, bytes);
+    k_back_solve<T, W><<<dim3(ntiles<W>(max_r), nparts), kThreads, bytes, st>>>(parts, s, 1, Acal, z);
+  } else {
+    constexpr int W = 32;
+    const size_t bytes = panel_smem<T>(max_m, W, 1);
+    allow_smem(k_back_solve<T, W>, bytes);
+    k_back_solve<T, W><<<dim3(ntiles<W>(max_r), nparts), kThreads, bytes, st>>>(parts, s, 1, Acal, z);
+  }
+}
+
+template <typename T>
+void launch_assemble_h(const SepDesc* seps, int nseps, int max_m, const double* A, const double* B,
+                       const double* C, const T* ZL, const T* ZR, double* HA, double* HB,
+                       double* HC, cudaStream_t st) {
+  if (nseps <= 0) return;
+  if (max_m <= 256) {
+    constexpr int W = 32;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_assemble_h<T, W>, bytes);
+    k_assemble_h<T, W><<<dim3(3 * tiles, nseps), kThreads, bytes, st>>>(seps, tiles, A, B, C, ZL, ZR, HA, HB, HC);
+  } else {
+    constexpr int W = 16;
+    const int tiles = ntiles<W>(max_m);
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_assemble_h<T, W>, bytes);
+    k_assemble_h<T, W><<<dim3(3 * tiles, nseps), kThreads, bytes, st>>>(seps, tiles, A, B, C, ZL, ZR, HA, HB, HC);
+  }
+}
+
+template <typename T>
+void launch_assemble_f(const SepDesc* seps, int nseps, int max_m, int max_r, const double* A,
+                       const double* C, const double* F, const T* z, double* fh, cudaStream_t st) {
+  if (nseps <= 0) return;
+  if (max_r <= 16) {
+    constexpr int W = 16;
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_assemble_f<T, W>, bytes);
+    k_assemble_f<T, W><<<dim3(ntiles<W>(max_r), nseps), kThreads, bytes, st>>>(seps, 1, A, C, F, z, fh);
+  } else {
+    constexpr int W = 32;
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_assemble_f<T, W>, bytes);
+    k_assemble_f<T, W><<<dim3(ntiles<W>(max_r), nseps), kThreads, bytes, st>>>(seps, 1, A, C, F, z, fh);
+  }
+}
+
+template <typename T>
+void launch_backsub(const PartDesc* parts, int nparts, int Lmax, int max_m, int max_r, const T* ZL,
+                    const T* ZR, const T* z, const double* h, double* x, cudaStream_t st) {
+  if (nparts <= 0 || Lmax <= 0) return;
+  if (max_r <= 16) {
+    constexpr int W = 16;
+    const int tiles = ntiles<W>(max_r);
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_backsub<T, W>, bytes);
+    k_backsub<T, W><<<dim3(Lmax * tiles, nparts), kThreads, bytes, st>>>(parts, tiles, ZL, ZR, z, h, x);
+  } else {
+    constexpr int W = 32;
+    const int tiles = ntiles<W>(max_r);
+    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    allow_smem(k_backsub<T, W>, bytes);
+    k_backsub<T, W><<<dim3(Lmax * tiles, nparts), kThreads, bytes, st>>>(parts, tiles, ZL, ZR, z, h, x);
+  }
+}
+
+void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const double* h,
+                     double* x, cudaStream_t st) {
+  if (nseps <= 0) return;
+  k_sep_copy<<<nseps, 256, 0, st>>>(seps, h, x);
+}
+
+void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* A,
+                     const double* B, const double* C, const double* x, const double* b, double* r,
+                     double* nrm, cudaStream_t st) {
+  if (nsys <= 0 || Nmax <= 0) return;
+  const size_t bytes = sizeof(double) * 3 * (size_t)max_m * 16;
+  allow_smem(k_residual, bytes);
+  k_residual<<<dim3(Nmax, nsys), 256, bytes, st>>>(sys, A, B, C, x, b, r, nrm);
+}
+
+void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
+                       double* x, double* nrm, cudaStream_t st) {
+  if (nsys <= 0 || Nmax <= 0) return;
+  k_axpy_norms<<<dim3(Nmax, nsys), 256, 0, st>>>(sys, d, x, nrm);
+}
+
+#define DM_INST(T)                                                                                  \
+  template void launch_inv<T>(const PartDesc*, int, int, const double*, T*, int*, int, cudaStream_t); \
+  template void launch_fwd_factor<T>(const PartDesc*, int, int, int, const double*, const double*,  \
+                                     const double*, T*, T*, T*, T*, cudaStream_t);                  \
+  template void launch_back_factor<T>(const PartDesc*, int, int, int, const T*, T*, T*, cudaStream_t); \
+  template void launch_fwd_solve<T>(const PartDesc*, int, int, int, int, const double*, const T*,   \
+                                    const double*, T*, cudaStream_t);                               \
+  template void launch_back_solve<T>(const PartDesc*, int, int, int, int, const T*, T*, cudaStream_t); \
+  template void launch_assemble_h<T>(const SepDesc*, int, int, const double*, const double*,        \
+                                     const double*, const T*, const T*, double*, double*, double*,  \
+                                     cudaStream_t);                                                 \
+  template void launch_assemble_f<T>(const SepDesc*, int, int, int, const double*, const double*,   \
+                                     const double*, const T*, double*, cudaStream_t);               \
+  template void launch_backsub<T>(const PartDesc*, int, int, int, int, const T*, const T*, const T*, \
+                                  const double*, double*, cudaStream_t);
+
+DM_INST(double)
+DM_INST(float)
+
+}  // namespace dm

@@ -1,0 +1,86 @@
+// Host-side plan structures of the decomposition-method solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dm_internal.cuh"
+
+namespace dm {
+
+// Sizes and decomposition of one system.
+struct SysSpec {
+  int N = 0, m = 0, r = 0;
+  int P = 1;       // subsystems (the paper's M)
+  int levels = 1;  // 1: supplementary system by block Thomas; L > 1: by DM, L-1 levels
+  int P2 = 1;      // subsystems of the supplementary system when levels > 1
+};
+
+// One level of the recursion: a set of independent systems, each split into
+// subsystems, with the float64 supplementary systems one level down.
+struct Level {
+  bool f32 = false;  // factors stored and multiplied in float32 (else float64)
+  int nsys = 0;
+  std::vector<SysSpec> spec;
+  std::vector<long long> blk0, vec0;  // per-system offsets of row 0
+  long long nblk = 0, nvec = 0;       // elements of the [rows][m][m] and [rows][m][r] arrays
+  int max_m = 1, max_r = 1, Nmax = 0, Lmax = 0, nparts = 0, nseps = 0;
+  std::vector<PartDesc> parts;
+  std::vector<SepDesc> seps;
+  std::vector<SysDesc> sysd;
+  std::vector<int> active_fwd, active_back;  // subsystems still active at each step (prefix counts)
+  PartDesc* d_parts = nullptr;
+  SepDesc* d_seps = nullptr;
+  SysDesc* d_sys = nullptr;
+  int* status = nullptr;
+  double *A = nullptr, *B = nullptr, *C = nullptr;  // float64 blocks of the level's systems
+  void *G = nullptr, *Acal = nullptr, *ZL = nullptr, *ZR = nullptr, *z = nullptr;
+  double *F = nullptr, *X = nullptr;  // right-hand sides and solutions (supplementary: fh and h)
+  std::unique_ptr<Level> supp;
+  std::vector<void*> owned;
+
+  int build(const std::vector<SysSpec>& specs, bool fp32_factors);
+  size_t bytes_needed() const;
+  int allocate();
+  ~Level();
+};
+
+struct Plan {
+  int precision = 0;
+  Level top;
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+  double* R = nullptr;    // float64 residual
+  double* Dx = nullptr;   // refinement correction
+  double* nrm = nullptr;  // [nsys][4][kMaxR] column norms
+  std::vector<double> h_nrm, relres;
+  bool factored = false;
+  double tol = 1e-12;
+  int max_iters = 30;
+  int last_iters = 0;
+  double last_corr = 0.0;
+  double factor_flops = 0, solve_flops = 0;
+  size_t device_bytes = 0;
+
+  int init(const std::vector<SysSpec>& specs, int precision);
+  int factor(const double* A, const double* B, const double* C);
+  int solve(const double* b, double* x, double* relres_out);
+  int solve_device(const double* b_dev, double* x_dev);
+  ~Plan();
+};
+
+int set_error(int code, const char* fmt, ...);
+void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps);
+int tuner_seed_p(int N, int m, int r);
+int supp_partitions(int Ms, int P, int r, int m);
+int make_spec(int N, int m, int r, int P, int levels, SysSpec* out);
+void factor_level(Level& L, cudaStream_t st);
+void solve_level(Level& L, const double* F, double* X, cudaStream_t st);
+void level_flops(const Level& L, double* ffac, double* fsol);
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+}  // namespace dm

@@ -1,0 +1,161 @@
+"""Python binding of the C ABI in include/dm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: arrays are passed by pointer to libdm_gb300.so.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA); they
+must be float64 and C-contiguous with the layouts of include/dm.h:
+A, B, C as [N, m, m], b and x as [N, m, nrhs].
+
+The library must have been built (``paper_1505_06864_gb300.build.build()`` or
+``__graft_entry__.build()``); loading raises if it is missing, there is no
+other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+DM_OK, DM_PENDING = 0, 1
+DM_EINVAL, DM_ENOMEM, DM_ESINGULAR, DM_ENOTCONV = -1, -2, -3, -4
+DM_EAGAIN, DM_ECUDA, DM_ESTATE, DM_ETIMEOUT = -5, -6, -7, -8
+DM_FP64, DM_FP32, DM_TF32, DM_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": DM_FP64, "fp32": DM_FP32, "tf32": DM_TF32, "bf16x3": DM_BF16X3}
+_NAMES = {0: "DM_OK", 1: "DM_PENDING", -1: "DM_EINVAL", -2: "DM_ENOMEM", -3: "DM_ESINGULAR",
+          -4: "DM_ENOTCONV", -5: "DM_EAGAIN", -6: "DM_ECUDA", -7: "DM_ESTATE", -8: "DM_ETIMEOUT"}
+
+
+class DMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dm_plan_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("m", ctypes.c_int), ("nrhs", ctypes.c_int), ("P", ctypes.c_int),
+                ("levels", ctypes.c_int), ("P2", ctypes.c_int), ("precision", ctypes.c_int),
+                ("count", ctypes.c_int), ("last_iters", ctypes.c_int), ("max_rows", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("last_relres", ctypes.c_double),
+                ("last_correction", ctypes.c_double), ("factor_flops", ctypes.c_double),
+                ("solve_flops", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} not found: build it first (paper_1505_06864_gb300.build.build())")
+        L = ctypes.CDLL(LIB)
+        P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+        sig = {
+            "dm_plan": (I, [ctypes.POINTER(P), I, I, I, I, I, I]),
+            "dm_plan_batch": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                  ctypes.POINTER(I), I]),
+            "dm_plan_tune": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "dm_factor": (I, [P, P, P, P]),
+            "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
+            "dm_set_stream": (I, [P, P]),
+            "dm_set_refinement": (I, [P, D, I]),
+            "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
+            "dm_destroy": (V, [P]),
+            "dm_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def dm_last_error() -> str:
+    return lib().dm_last_error().decode()
+
+
+def _check(rc, allow=(DM_OK,)):
+    if rc not in allow:
+        raise DMError(rc, dm_last_error())
+    return rc
+
+
+def _ptr(a, writable=False):
+    """Raw pointer of a float64 C-contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be float64 and C-contiguous")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("output array is read-only")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors must be float64 and contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def dm_plan(N, m, nrhs, P=0, levels=0, precision=DM_FP64):
+    """Create a plan; returns an opaque handle (free with dm_destroy)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = ctypes.c_void_p()
+    _check(lib().dm_plan(ctypes.byref(h), int(N), int(m), int(nrhs), int(P), int(levels), int(precision)))
+    return h
+
+
+def dm_plan_batch(Ns, ms, rs, precision=DM_FP64):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    n = len(Ns)
+    arr = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+    h = ctypes.c_void_p()
+    _check(lib().dm_plan_batch(ctypes.byref(h), n, arr(Ns), arr(ms), arr(rs), int(precision)))
+    return h
+
+
+def dm_plan_tune(N, m, nrhs, P=0, levels=0):
+    """(P, levels, P2) that dm_plan would use; host only, no GPU needed."""
+    p, lv, p2 = ctypes.c_int(P), ctypes.c_int(levels), ctypes.c_int(0)
+    _check(lib().dm_plan_tune(int(N), int(m), int(nrhs), ctypes.byref(p), ctypes.byref(lv), ctypes.byref(p2)))
+    return p.value, lv.value, p2.value
+
+
+def dm_factor(plan, A, B, C):
+    return _check(lib().dm_factor(plan, _ptr(A), _ptr(B), _ptr(C)))
+
+
+def dm_solve(plan, b, x, count=1, allow_notconv=False):
+    """Solve into x (preallocated, same shape as b); returns the relative
+    residual(s) max_c ||b - T x||/||b|| (a float, or a list for batch plans)."""
+    rel = (ctypes.c_double * max(1, count))()
+    rc = lib().dm_solve(plan, _ptr(b), _ptr(x, True), rel)
+    _check(rc, (DM_OK, DM_ENOTCONV) if allow_notconv else (DM_OK,))
+    return rel[0] if count == 1 else list(rel)
+
+
+def dm_set_stream(plan, stream):
+    """stream: a torch.cuda.Stream, an int handle, or None for the plan's own."""
+    h = getattr(stream, "cuda_stream", stream)
+    return _check(lib().dm_set_stream(plan, ctypes.c_void_p(h) if h else None))
+
+
+def dm_set_refinement(plan, tol, max_iters):
+    return _check(lib().dm_set_refinement(plan, float(tol), int(max_iters)))
+
+
+def dm_plan_query(plan) -> dict:
+    info = dm_plan_info()
+    _check(lib().dm_plan_query(plan, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in dm_plan_info._fields_}
+
+
+def dm_destroy(plan):
+    if plan:
+        lib().dm_destroy(plan)

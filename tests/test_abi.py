@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every entry point include/dm.h declares, validates arguments before
+touching the device, and its tuner seed follows the paper's formulas."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_1505_06864_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dm():
+    B.build()
+    from paper_1505_06864_gb300 import dm as D
+    return D
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "dm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(dm_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(dm):
+    names = declared_functions()
+    assert "dm_plan" in names and "dm_solve" in names and len(names) >= 10
+    L = ctypes.CDLL(B.LIB)
+    for n in names:
+        assert hasattr(L, n), n
+    # the binding exposes the same names
+    for n in names:
+        assert hasattr(dm, n), n
+
+
+def test_invalid_arguments_rejected_without_gpu(dm):
+    bad = [dict(N=0, m=4, nrhs=1), dict(N=10, m=0, nrhs=1), dict(N=10, m=4, nrhs=0),
+           dict(N=10, m=600, nrhs=1), dict(N=10, m=4, nrhs=65), dict(N=9, m=4, nrhs=1, P=6),
+           dict(N=4, m=2, nrhs=1, P=3), dict(N=10, m=4, nrhs=1, P=-1)]
+    for kw in bad:
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_plan(precision=dm.DM_FP64, **kw)
+        assert e.value.code == dm.DM_EINVAL, kw
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_plan(10, 4, 1, 2, 1, precision=9)
+    assert e.value.code == dm.DM_EINVAL
+    assert dm.dm_last_error()
+
+
+def test_tuner_seed_is_paper_optimum(dm):
+    from oracle import dm_oracle as o
+    for N, m, r in [(2048, 256, 1), (4096, 128, 8), (64, 16, 1), (3071, 400, 1), (5, 3, 1)]:
+        P, levels, P2 = dm.dm_plan_tune(N, m, r)
+        ref = min(max(1, round(o.p_opt_mp(N, m, r))), (N + 1) // 2)
+        assert P == ref
+        assert levels == (2 if P >= 21 else 1)
+        if levels == 2:
+            assert P2 == o.supp_partitions(P - 1, P, r, m)
+    # explicit choices pass through; P2 follows Eq. (SuppMatrM) or its boundary P/3
+    assert dm.dm_plan_tune(2048, 256, 1, P=64, levels=2) == (64, 2, o_supp(64, 1, 256))
+    assert dm.dm_plan_tune(2048, 256, 1, P=16, levels=2)[2] == round(16 / 3)
+    assert dm.dm_plan_tune(2048, 256, 1, P=4, levels=1) == (4, 1, 1)
+    assert dm.dm_plan_tune(64, 16, 1, P=1, levels=3) == (1, 1, 1)
+
+
+def o_supp(P, r, m):
+    from oracle import dm_oracle as o
+    return o.supp_partitions(P - 1, P, r, m)

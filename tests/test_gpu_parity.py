@@ -1,0 +1,190 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (spec targets): plain float64 GPU DM within 1e-12 relative
+of the float64 oracle; mixed precision with float64 iterative refinement
+within 1e-10.  Every comparison is element by element (|x - x_ref| <= tol *
+max|x_ref| per right-hand-side column) and normwise (max over columns of
+||x - x_ref||_2 / ||x_ref||_2).
+"""
+import numpy as np
+import pytest
+
+from oracle import dm_oracle as o
+from paper_1505_06864_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1505_06864_gb300 import build
+    build.build()
+    from paper_1505_06864_gb300 import dm as D
+    return D
+
+
+def solve(dm, s, P, levels, prec="fp64", b=None):
+    plan = dm.dm_plan(s.N, s.m, s.nrhs, P, levels, prec)
+    try:
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        b = s.b if b is None else b
+        x = np.zeros_like(b)
+        rel = dm.dm_solve(plan, b, x)
+        info = dm.dm_plan_query(plan)
+    finally:
+        dm.dm_destroy(plan)
+    return x, rel, info
+
+
+def check(x, xref, tol):
+    assert np.all(np.isfinite(x))
+    scale = np.max(np.abs(xref), axis=(0, 1))
+    err = np.max(np.abs(x - xref), axis=(0, 1))
+    assert np.all(err <= tol * scale), (err / scale, tol)
+    assert o.rel_err(x, xref) <= tol
+
+
+def test_config1_exact_shape(dm):
+    """N=64, m=16, P=4, 1 right-hand side, dominant generator, seed 1."""
+    s = w.dominant_system(64, 16, 1, 1)
+    x, rel, info = solve(dm, s, 4, 1)
+    check(x, o.dm(s.A, s.B, s.C, s.b, 4), TOL64)
+    assert rel < 1e-14
+    assert info["P"] == 4 and info["levels"] == 1 and info["max_rows"] == 16
+
+
+CASES = [
+    # N, m, nrhs, P, levels
+    (1, 1, 1, 1, 1), (2, 3, 1, 1, 1), (3, 2, 1, 2, 1), (10, 5, 3, 3, 1), (33, 17, 2, 4, 1),
+    (50, 33, 20, 5, 2), (97, 40, 3, 7, 2), (200, 8, 1, 30, 2), (200, 8, 1, 30, 3),
+    (40, 64, 4, 6, 1), (12, 200, 2, 3, 1), (7, 300, 1, 2, 1), (5, 512, 1, 2, 1),
+    (65, 48, 16, 32, 2), (31, 24, 17, 16, 1),
+]
+
+
+@pytest.mark.parametrize("N,m,r,P,levels", CASES)
+def test_fp64_matches_oracle(dm, N, m, r, P, levels):
+    s = w.dominant_system(N, m, r, 100 + N + m)
+    x, rel, info = solve(dm, s, P, levels)
+    check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None), TOL64)
+    check(x, s.x_true, 1e-11)
+
+
+def test_fp64_pivoting_conditioned_blocks(dm):
+    s = w.conditioned_system(40, 32, 2, 7, cond=1e4)
+    xt = o.refine_truth(s.A, s.B, s.C, s.b)
+    for P in (1, 4, 13):
+        x, rel, _ = solve(dm, s, P, 1)
+        check(x, xt, 1e-11)
+
+
+def test_pde_banded_shape(dm):
+    s = w.pde_banded_system(130, 64, 1, 2)
+    for P, lv in ((4, 1), (16, 2), (64, 2)):
+        x, rel, info = solve(dm, s, P, lv)
+        check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=info["P2"] if info["P2"] > 1 else None), TOL64)
+
+
+@pytest.mark.parametrize("N,m,r,P,levels", [(64, 16, 1, 4, 1), (97, 40, 3, 7, 2), (40, 128, 8, 8, 1),
+                                            (9, 256, 2, 2, 1)])
+def test_fp32_refined_matches_oracle(dm, N, m, r, P, levels):
+    s = w.dominant_system(N, m, r, 7 + N)
+    x, rel, info = solve(dm, s, P, levels, "fp32")
+    check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None), TOLMIX)
+    assert info["last_iters"] >= 2 and info["last_correction"] <= 1e-12
+
+
+def test_fp32_refined_conditioned(dm):
+    s = w.conditioned_system(64, 32, 4, 3, cond=1e4)
+    xt = o.refine_truth(s.A, s.B, s.C, s.b)
+    x, rel, info = solve(dm, s, 8, 1, "fp32")
+    check(x, xt, TOLMIX)
+
+
+def test_repeat_rhs_on_resident_factors(dm):
+    s = w.dominant_system(80, 24, 3, 11)
+    plan = dm.dm_plan(80, 24, 3, 6, 2, "fp64")
+    try:
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        for k in range(3):
+            b = w.random_rhs(80, 24, 3, 50 + k)
+            x = np.zeros_like(b)
+            dm.dm_solve(plan, b, x)
+            check(x, o.dm(s.A, s.B, s.C, b, 6, levels=2, P2=dm.dm_plan_query(plan)["P2"]), TOL64)
+    finally:
+        dm.dm_destroy(plan)
+
+
+def test_device_pointers_and_alias(dm):
+    import torch
+    s = w.dominant_system(50, 20, 2, 5)
+    T = lambda a: torch.from_numpy(a).cuda()
+    plan = dm.dm_plan(50, 20, 2, 5, 1, "fp64")
+    try:
+        dm.dm_factor(plan, T(s.A), T(s.B), T(s.C))
+        bx = T(s.b)
+        dm.dm_solve(plan, bx, bx)   # x aliases b
+        torch.cuda.synchronize()
+        check(bx.cpu().numpy(), o.dm(s.A, s.B, s.C, s.b, 5), TOL64)
+    finally:
+        dm.dm_destroy(plan)
+
+
+def test_singular_block_reported(dm):
+    s = w.dominant_system(6, 4, 1, 1)
+    s.B[3] = 0.0
+    s.A[3] = 0.0
+    s.C[2] = 0.0   # row 3 decoupled from row 2: its Schur complement is exactly zero
+    plan = dm.dm_plan(6, 4, 1, 1, 1, "fp64")
+    try:
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_factor(plan, s.A, s.B, s.C)
+        assert e.value.code == dm.DM_ESINGULAR
+        assert "block row 3" in str(e.value)
+    finally:
+        dm.dm_destroy(plan)
+
+
+def test_solve_before_factor(dm):
+    plan = dm.dm_plan(8, 4, 1, 2, 1, "fp64")
+    try:
+        b = np.ones((8, 4, 1))
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_solve(plan, b, np.zeros_like(b))
+        assert e.value.code == dm.DM_ESTATE
+    finally:
+        dm.dm_destroy(plan)
+
+
+@pytest.mark.parametrize("P,levels", [(64, 1), (64, 2), (16, 2), (4, 1)])
+def test_config2_full_size(dm, P, levels):
+    """N=2048 grid points x m=256 spline block, banded blocks, 1 right-hand side,
+    float64 (the benchmarked workload), compared in full with the oracle."""
+    s = _config2()
+    x, rel, info = solve(dm, s, P, levels)
+    xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
+    check(x, xo, TOL64)
+    assert rel < 1e-14
+
+
+_C2 = {}
+
+
+def _config2():
+    if "s" not in _C2:
+        _C2["s"] = w.pde_banded_system(2048, 256, 1, 2)
+    return _C2["s"]
+
+
+def test_config3_fp32_refined_full_size(dm):
+    """N=4096, m=128 dense blocks with cond(B_i)=1e4, 8 right-hand sides, float32
+    factors refined in float64 to the mixed-precision tolerance."""
+    s = w.conditioned_system(4096, 128, 8, 3, cond=1e4)
+    x, rel, info = solve(dm, s, 0, 0, "fp32")
+    xo = o.dm(s.A, s.B, s.C, s.b, info["P"], levels=info["levels"], P2=info["P2"] if info["P2"] > 1 else None)
+    check(x, xo, TOLMIX)
