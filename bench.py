@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the decomposition-method (DM) solver on one GB300 per rank.
+
+Workload (default): the PDE-shaped block-tridiagonal system -- second-order
+finite differences over N = 2048 grid points times cubic-spline collocation
+with m = 256 (banded blocks, half-bandwidth 3, stored dense), one right-hand
+side, float64 DM with P = 64 subsystems and DM on the supplementary system
+(levels = 2).  A step is one factor + solve of the whole system (every stage
+of the method: subsystem sweeps, supplementary assembly and solve,
+back-substitution, float64 residual), inputs resident in device memory.
+
+Printed: one JSON line (rank 0).  `value` is solved systems per second over
+all ranks (each rank solves its own replica: the method has no data-path
+exchange across GPUs here).  Also reported: TFLOP/s, per-step latency
+percentiles, the roofline of the dominant kernel (CUDA events inside the
+timed region), an end-to-end figure through the C ABI with host buffers, the
+CPU oracle timed on the host cores, a sweep over P and recursion depth, and
+the mixed-precision (float32 factors + float64 refinement) path on the same
+workload.
+
+`--impl reference` times the CPU oracle (oracle/dm_oracle.py, numpy float64)
+on the same workload instead: the reference arm of this benchmark.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_, M_, R_, P_, LEV_ = 2048, 256, 1, 64, 2
+SEED = 2
+FP64_PEAK_TFLOPS = 1.25     # GB300 nominal float64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip sweep, mixed, e2e and cpu legs")
+    ap.add_argument("--N", type=int, default=2048, help="block rows (smaller cases for profiler captures)")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1505_06864_gb300 import workloads as w
+    return w.pde_banded_system(N_, M_, R_, SEED)
+
+
+def workload_name():
+    return f"pde-banded block-tridiagonal N={N_} m={M_} hb=3 nrhs={R_} seed={SEED}"
+
+
+def blas_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [os.cpu_count() or 1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_solve(s):
+    from oracle import dm_oracle as o
+    t0 = time.perf_counter()
+    x = o.dm(s.A, s.B, s.C, s.b, P_, levels=LEV_)
+    return time.perf_counter() - t0, x
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons (every 200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.proc, self.path = dev, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    global N_
+    N_ = args.N
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    s = workload()
+    for _ in range(args.warmup):
+        cpu_oracle_solve(s)
+    times = []
+    for _ in range(args.steps):
+        t, x = cpu_oracle_solve(s)
+        times.append(t)
+    total = sum(times)
+    v = args.steps / total
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "solved systems/s", "value": v, "unit": "systems/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "P": P_, "levels": LEV_, "precision": "fp64"},
+        "cpu_baseline": {"value": v, "unit": "systems/s", "cores": cores, "kind": "oracle",
+                         "sample": "the full workload, one oracle DM solve per step"},
+        "e2e": {"value": v, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    global N_
+    args = parse()
+    N_ = args.N
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_06864_gb300 import dm
+
+    s = workload()
+    dev = torch.device("cuda", local)
+    A, B, C = (torch.from_numpy(v).to(dev) for v in (s.A, s.B, s.C))
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.empty_like(b)
+    stream = torch.cuda.Stream(device=dev)
+    plan = dm.dm_plan(N_, M_, R_, P_, LEV_, dm.DM_FP64)
+    dm.dm_set_stream(plan, stream)
+    info = dm.dm_plan_query(plan)
+
+    def step():
+        dm.dm_factor(plan, A, B, C)
+        return dm.dm_solve(plan, b, x)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    dm.dm_profile(plan, True)
+    launches0 = dm.dm_launch_count(plan)
+    barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        relres = step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = dm.dm_profile(plan, False)
+    launches = dm.dm_launch_count(plan) - launches0
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    xh = x.cpu().numpy()
+    rel_true = rel_err(xh, s.x_true)
+    flops_step = info["factor_flops"] + info["solve_flops"]
+    value = ws * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel class (largest summed event time)
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    kname, kd = top
+    achieved = kd["flops"] / (kd["ms"] / 1e3) / 1e12
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": read_traffic(kname),
+            "peak_source": "GB300 nominal float64 rate (152 SMs x 2.07 GHz x 4 flop/clk/SM)",
+            "launches": kd["launches"], "avg_launch_ms": kd["ms"] / kd["launches"],
+            "share_of_step": kd["ms"] / sum(v["ms"] for v in prof.values())}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": "solved systems/s", "value": value, "unit": "systems/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(), "P": info["P"], "levels": info["levels"], "P2": info["P2"],
+                   "precision": "fp64", "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (3.2 GB of blocks per step)"},
+        "tflops": flops_step * value / 1e12,
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "relres": relres, "rel_err_vs_xtrue": rel_true,
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(dm, s, stream, ws)
+        line["sweep"] = sweep_leg(dm, A, B, C, b, stream)
+        line["mixed"] = mixed_leg(dm, A, B, C, b, stream, xh)
+        if ws == 1:
+            t, xo = cpu_oracle_solve(s)
+            line["cpu_baseline"] = {"value": 1.0 / t, "unit": "systems/s", "cores": blas_threads(),
+                                    "kind": "oracle",
+                                    "sample": "the full workload: one numpy float64 DM solve (P=64, levels=2)"}
+            line["rel_err_vs_oracle"] = rel_err(xh, xo)
+    elif rank == 0:
+        line["e2e"] = None
+    dm.dm_destroy(plan)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def rel_err(x, xref):
+    """max over right-hand-side columns of ||x - xref||_2 / ||xref||_2"""
+    x = x.reshape(-1, x.shape[-1])
+    xref = xref.reshape(-1, xref.shape[-1])
+    return float(np.max(np.linalg.norm(x - xref, axis=0) / np.maximum(np.linalg.norm(xref, axis=0), 1e-300)))
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 2 and f[0] == kernel:
+            try:
+                return float(f[1])
+            except ValueError:
+                return None
+    return None
+
+
+def e2e_leg(dm, s, stream, ws, steps=3):
+    """Same metric through the C ABI with pinned host buffers (copies timed)."""
+    import torch
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    A, B, C, b = pin(s.A), pin(s.B), pin(s.C), pin(s.b)
+    x = torch.empty_like(b).pin_memory()
+    plan = dm.dm_plan(N_, M_, R_, P_, LEV_, dm.DM_FP64)
+    dm.dm_set_stream(plan, stream)
+    dm.dm_factor(plan, A, B, C)
+    dm.dm_solve(plan, b, x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dm.dm_factor(plan, A, B, C)
+        dm.dm_solve(plan, b, x)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    dm.dm_destroy(plan)
+    h2d = 8 * (3 * N_ * M_ * M_ + N_ * M_ * R_)
+    return {"value": ws / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * N_ * M_ * R_,
+            "ms_per_step": 1e3 * dt}
+
+
+def timed(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, out
+
+
+def sweep_leg(dm, A, B, C, b, stream):
+    """P in {4, 16, 64} x recursion depth {1, 2}: one warm-up and one timed step each."""
+    import torch
+    out = []
+    x = torch.empty_like(b)
+    for P in (4, 16, 64):
+        for lv in (1, 2):
+            plan = dm.dm_plan(N_, M_, R_, P, lv, dm.DM_FP64)
+            dm.dm_set_stream(plan, stream)
+            q = dm.dm_plan_query(plan)
+            dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x))[1])
+            out.append({"P": P, "levels": q["levels"], "P2": q["P2"], "systems_per_s": 1.0 / dt,
+                        "ms": 1e3 * dt, "relres": rel})
+            dm.dm_destroy(plan)
+    return out
+
+
+def mixed_leg(dm, A, B, C, b, stream, x64):
+    """float32 factors + float64 refinement on the same workload."""
+    import torch
+    out = {}
+    x = torch.empty_like(b)
+    for name in ("fp32",):
+        plan = dm.dm_plan(N_, M_, R_, P_, LEV_, name)
+        dm.dm_set_stream(plan, stream)
+        dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x, allow_notconv=True))[1], reps=3)
+        q = dm.dm_plan_query(plan)
+        out[name] = {"systems_per_s": 1.0 / dt, "ms": 1e3 * dt, "iters": q["last_iters"], "relres": rel,
+                     "rel_err_vs_fp64_dm": rel_err(x.cpu().numpy(), x64)}
+        dm.dm_destroy(plan)
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -121,6 +121,25 @@ int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out);
  * effective P, levels and P2.  DM_EINVAL for invalid sizes. */
 int dm_plan_tune(int N, int m, int nrhs, int* P, int* levels, int* P2);
 
+/* Per-kernel timing for benchmarks.  Every kernel the library launches for a
+ * plan belongs to a class (inv, fwd_factor, back_factor, assemble_h,
+ * fwd_solve, back_solve, assemble_f, backsub, sep_copy, residual,
+ * axpy_norms).  With profiling enabled each launch is bracketed by a pair of
+ * CUDA events recorded on the plan's stream.  dm_profile first writes (when
+ * out != NULL) one entry per class seen since the previous call -- launches,
+ * summed event time in ms, and the launches' algorithmic flops (2 per
+ * multiply-add) and bytes (operands read once, results written once) --
+ * then clears the sums and switches profiling on (enable = 1) or off. */
+typedef struct dm_profile_entry {
+  char name[24];
+  long long launches;
+  double ms, flops, bytes;
+} dm_profile_entry;
+int dm_profile(dm_plan_t plan, int enable, dm_profile_entry* out, int max_entries, int* n_entries);
+
+/* Number of kernels this plan has launched so far (always counted). */
+long long dm_launch_count(dm_plan_t plan);
+
 /* Optional settings and queries. */
 int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */
 int dm_set_refinement(dm_plan_t plan, double tol, int max_iters); /* default 1e-12, 30 */

@@ -163,7 +163,64 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors) {
     while (c < nparts && parts[c].L >= s + 2) ++c;
     active_back[s] = c;
   }
+  compute_costs();
   return DM_OK;
+}
+
+// Algorithmic flops and bytes of every launch (see Cost).
+void Level::compute_costs() {
+  const double es = f32 ? 4.0 : 8.0;
+  c_inv.assign(std::max(Lmax, 1), Cost());
+  c_fwd.assign(std::max(Lmax, 1), Cost());
+  c_back.assign(std::max(Lmax, 1), Cost());
+  c_fwds.assign(std::max(Lmax, 1), Cost());
+  c_backs.assign(std::max(Lmax, 1), Cost());
+  c_asm_h = c_asm_f = c_backsub = c_resid = c_axpy = c_sepcopy = Cost();
+  for (const PartDesc& p : parts) {
+    const double m2 = (double)p.m * p.m, m3 = 2.0 * m2 * p.m, mr = (double)p.m * p.r, m2r = 2.0 * m2 * p.r;
+    const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
+    for (int t = 0; t < p.L; ++t) {
+      Cost& ci = c_inv[t];
+      ci.flops += m3;
+      ci.bytes += (t == 0 ? 8.0 : es) * m2 + es * m2;
+      Cost& cf = c_fwd[t];
+      if (t < p.L - 1) { cf.flops += 2 * m3; cf.bytes += es * m2 * 3 + 24.0 * m2; }
+      else if (hr) { cf.flops += m3; cf.bytes += es * m2 * 2 + 8.0 * m2; }
+      if (hl) { cf.flops += (t == 0 ? m3 : 2 * m3); cf.bytes += 8.0 * m2 + es * m2 * (t == 0 ? 1 : 2) + (hl && t + 1 < p.L ? 0 : 0); }
+      Cost& cs = c_fwds[t];
+      cs.flops += (t == 0 ? m2r : 2 * m2r);
+      cs.bytes += es * m2 + (t ? 8.0 * m2 + es * mr : 0) + 8.0 * mr + es * mr;
+      if (t + 1 < p.L) {
+        const int s = p.L - 2 - t;
+        Cost& cb = c_back[s];
+        if (hl || hr) cb.bytes += es * m2;
+        if (hl) { cb.flops += m3; cb.bytes += 3 * es * m2; }
+        if (hr) { cb.flops += m3; cb.bytes += 2 * es * m2; }
+        Cost& cbs = c_backs[s];
+        cbs.flops += m2r;
+        cbs.bytes += es * m2 + 3 * es * mr;
+      }
+      const int ns = (hl ? 1 : 0) + (hr ? 1 : 0);
+      c_backsub.flops += ns * m2r;
+      c_backsub.bytes += ns * es * m2 + es * mr + 8.0 * mr;
+    }
+  }
+  for (const SepDesc& d : seps) {
+    const double m2 = (double)d.m * d.m, m3 = 2.0 * m2 * d.m, mr = (double)d.m * d.r, m2r = 2.0 * m2 * d.r;
+    const int extra = ((d.flags & HAS_HA) ? 1 : 0) + ((d.flags & HAS_HC) ? 1 : 0);
+    c_asm_h.flops += (2 + extra) * m3;
+    c_asm_h.bytes += 24.0 * m2 + (2 + extra) * (8.0 + 0.0) * m2 + (2 + extra) * es * m2;
+    c_asm_f.flops += 2 * m2r;
+    c_asm_f.bytes += 16.0 * m2 + 8.0 * mr * 2 + 2 * es * mr;
+    c_sepcopy.bytes += 16.0 * mr;
+  }
+  for (const SysDesc& d : sysd) {
+    const double m2 = (double)d.m * d.m, mr = (double)d.m * d.r;
+    c_resid.flops += d.N * 6.0 * m2 * d.r;
+    c_resid.bytes += d.N * (24.0 * m2 + 24.0 * mr);
+    c_axpy.flops += d.N * 2.0 * mr;
+    c_axpy.bytes += d.N * 24.0 * mr;
+  }
 }
 
 size_t Level::bytes_needed() const {
@@ -226,57 +283,140 @@ Level::~Level() {
   for (void* p : owned) cudaFree(p);
 }
 
+// ---------------------------------------------------------------------------
+// Profiler
+const char* const kClassNames[K_NCLASS] = {
+    "inv", "fwd_factor", "back_factor", "assemble_h", "fwd_solve", "back_solve", "assemble_f",
+    "backsub", "sep_copy", "residual", "axpy_norms"};
+
+cudaEvent_t Prof::take() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Prof::begin(cudaStream_t st, cudaEvent_t* e0) {
+  *e0 = nullptr;
+  if (!on) return;
+  *e0 = take();
+  cudaEventRecord(*e0, st);
+}
+
+void Prof::end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, bool launched) {
+  if (launched) ++launches;
+  if (!on || !e0) return;
+  if (!launched) {
+    pool.push_back(e0);
+    return;
+  }
+  cudaEvent_t e1 = take();
+  cudaEventRecord(e1, st);
+  recs.push_back(Rec{cls, e0, e1, fl, by});
+}
+
+int Prof::collect() {
+  for (Rec& r : recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    n[r.cls] += 1;
+    ms[r.cls] += t;
+    flops[r.cls] += r.flops;
+    bytes[r.cls] += r.bytes;
+    pool.push_back(r.e0);
+    pool.push_back(r.e1);
+  }
+  recs.clear();
+  return DM_OK;
+}
+
+void Prof::reset() {
+  collect();
+  for (int i = 0; i < K_NCLASS; ++i) n[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
+}
+
+Prof::~Prof() {
+  for (Rec& r : recs) pool.push_back(r.e0), pool.push_back(r.e1);
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+#define DM_LAUNCH(pf, st, cls, cost, active, call)             \
+  do {                                                         \
+    cudaEvent_t e0_;                                           \
+    (pf).begin((st), &e0_);                                    \
+    call;                                                      \
+    (pf).end((st), e0_, (cls), (cost).flops, (cost).bytes, (active) > 0); \
+  } while (0)
+
 // Forward and backward spike sweeps, assembly, and the factorisation of the
 // supplementary level (recursively).  A, B, C must hold the level's blocks.
 template <typename T>
-static void factor_level_t(Level& L, cudaStream_t st) {
+static void factor_level_t(Level& L, cudaStream_t st, Prof& pf) {
   T* G = static_cast<T*>(L.G);
   T* Ac = static_cast<T*>(L.Acal);
   T* ZL = static_cast<T*>(L.ZL);
   T* ZR = static_cast<T*>(L.ZR);
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t];
-    launch_inv<T>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st);
-    launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st);
+    DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<T>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwd[t], np,
+              launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st));
   }
   for (int s = 0; s + 1 < L.Lmax; ++s)
-    launch_back_factor<T>(L.d_parts, L.active_back[s], s, L.max_m, Ac, ZL, ZR, st);
-  if (L.supp) launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C, st);
+    DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], L.active_back[s],
+              launch_back_factor<T>(L.d_parts, L.active_back[s], s, L.max_m, Ac, ZL, ZR, st));
+  if (L.supp)
+    DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
+              launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
+                                   L.supp->C, st));
 }
 
-void factor_level(Level& L, cudaStream_t st) {
+void factor_level(Level& L, cudaStream_t st, Prof& pf) {
   cudaMemsetAsync(L.status, 0x7f, std::max(1, L.nsys) * sizeof(int), st);
   if (L.f32)
-    factor_level_t<float>(L, st);
+    factor_level_t<float>(L, st, pf);
   else
-    factor_level_t<double>(L, st);
-  if (L.supp) factor_level(*L.supp, st);
+    factor_level_t<double>(L, st, pf);
+  if (L.supp) factor_level(*L.supp, st, pf);
 }
 
 // Solve with resident factors: F -> X for every system of the level.
 template <typename T>
-static void solve_level_t(Level& L, const double* F, double* X, cudaStream_t st) {
+static void solve_level_t(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf) {
   T* z = static_cast<T*>(L.z);
   const T* G = static_cast<const T*>(L.G);
   const T* Ac = static_cast<const T*>(L.Acal);
   for (int t = 0; t < L.Lmax; ++t)
-    launch_fwd_solve<T>(L.d_parts, L.active_fwd[t], t, L.max_m, L.max_r, L.A, G, F, z, st);
+    DM_LAUNCH(pf, st, K_FWD_SOLVE, L.c_fwds[t], L.active_fwd[t],
+              launch_fwd_solve<T>(L.d_parts, L.active_fwd[t], t, L.max_m, L.max_r, L.A, G, F, z, st));
   for (int s = 0; s + 1 < L.Lmax; ++s)
-    launch_back_solve<T>(L.d_parts, L.active_back[s], s, L.max_m, L.max_r, Ac, z, st);
+    DM_LAUNCH(pf, st, K_BACK_SOLVE, L.c_backs[s], L.active_back[s],
+              launch_back_solve<T>(L.d_parts, L.active_back[s], s, L.max_m, L.max_r, Ac, z, st));
   if (L.supp) {
-    launch_assemble_f<T>(L.d_seps, L.nseps, L.max_m, L.max_r, L.A, L.C, F, z, L.supp->F, st);
-    solve_level(*L.supp, L.supp->F, L.supp->X, st);
+    DM_LAUNCH(pf, st, K_ASSEMBLE_F, L.c_asm_f, L.nseps,
+              launch_assemble_f<T>(L.d_seps, L.nseps, L.max_m, L.max_r, L.A, L.C, F, z, L.supp->F, st));
+    solve_level(*L.supp, L.supp->F, L.supp->X, st, pf);
   }
-  launch_backsub<T>(L.d_parts, L.nparts, L.Lmax, L.max_m, L.max_r, static_cast<const T*>(L.ZL),
-                    static_cast<const T*>(L.ZR), z, L.supp ? L.supp->X : nullptr, X, st);
-  if (L.supp) launch_sep_copy(L.d_seps, L.nseps, L.max_m, L.max_r, L.supp->X, X, st);
+  DM_LAUNCH(pf, st, K_BACKSUB, L.c_backsub, L.nparts,
+            launch_backsub<T>(L.d_parts, L.nparts, L.Lmax, L.max_m, L.max_r, static_cast<const T*>(L.ZL),
+                              static_cast<const T*>(L.ZR), z, L.supp ? L.supp->X : nullptr, X, st));
+  if (L.supp)
+    DM_LAUNCH(pf, st, K_SEP_COPY, L.c_sepcopy, L.nseps,
+              launch_sep_copy(L.d_seps, L.nseps, L.max_m, L.max_r, L.supp->X, X, st));
 }
 
-void solve_level(Level& L, const double* F, double* X, cudaStream_t st) {
+void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf) {
   if (L.f32)
-    solve_level_t<float>(L, F, X, st);
+    solve_level_t<float>(L, F, X, st, pf);
   else
-    solve_level_t<double>(L, F, X, st);
+    solve_level_t<double>(L, F, X, st, pf);
 }
 
 // first failing block row per system (host check after a factorisation)
@@ -382,7 +522,7 @@ int Plan::factor(const double* A, const double* B, const double* C) {
   if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
-  factor_level(top, st);
+  factor_level(top, st, prof);
   DM_CUDA(cudaGetLastError());
   rc = check_status(top, st, 0);
   factored = (rc == DM_OK);
@@ -405,9 +545,11 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
   cudaStream_t st = stream;
   const size_t nb = (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double);
   if (precision == DM_FP64) {
-    solve_level(top, b_dev, x_dev, st);
+    solve_level(top, b_dev, x_dev, st, prof);
     DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
-    launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev, b_dev, R, nrm, st);
+    DM_LAUNCH(prof, st, K_RESIDUAL, top.c_resid, top.nsys,
+              launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                              b_dev, R, nrm, st));
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));
@@ -424,10 +566,13 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
   int it = 0;
   double corr = 0.0;
   for (it = 1; it <= max_iters; ++it) {
-    solve_level(top, rhs, Dx, st);
+    solve_level(top, rhs, Dx, st, prof);
     DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
-    launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, st);
-    launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev, b_dev, R, nrm, st);
+    DM_LAUNCH(prof, st, K_AXPY, top.c_axpy, top.nsys,
+              launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, st));
+    DM_LAUNCH(prof, st, K_RESIDUAL, top.c_resid, top.nsys,
+              launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                              b_dev, R, nrm, st));
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));
@@ -635,6 +780,33 @@ int dm_plan_query(dm_plan_t plan, dm_plan_info* info) {
   info->solve_flops = p.solve_flops;
   return DM_OK;
 }
+
+int dm_profile(dm_plan_t plan, int enable, dm_profile_entry* out, int max_entries, int* n_entries) {
+  if (!plan) return set_error(DM_EINVAL, "NULL plan");
+  Prof& pf = plan->plan.prof;
+  if (out && max_entries > 0) {
+    pf.collect();
+    int k = 0;
+    for (int c = 0; c < K_NCLASS && k < max_entries; ++c) {
+      if (pf.n[c] == 0) continue;
+      dm_profile_entry& e = out[k++];
+      std::memset(e.name, 0, sizeof e.name);
+      std::strncpy(e.name, kClassNames[c], sizeof e.name - 1);
+      e.launches = pf.n[c];
+      e.ms = pf.ms[c];
+      e.flops = pf.flops[c];
+      e.bytes = pf.bytes[c];
+    }
+    if (n_entries) *n_entries = k;
+  } else if (n_entries) {
+    *n_entries = 0;
+  }
+  pf.reset();
+  pf.on = enable != 0;
+  return DM_OK;
+}
+
+long long dm_launch_count(dm_plan_t plan) { return plan ? plan->plan.prof.launches : -1; }
 
 void dm_destroy(dm_plan_t plan) { delete plan; }
 

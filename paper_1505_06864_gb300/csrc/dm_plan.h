@@ -12,6 +12,40 @@
 
 namespace dm {
 
+// Kernel classes of the profiler (one per launcher).
+enum KClass {
+  K_INV, K_FWD_FACTOR, K_BACK_FACTOR, K_ASSEMBLE_H, K_FWD_SOLVE, K_BACK_SOLVE, K_ASSEMBLE_F,
+  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_NCLASS
+};
+extern const char* const kClassNames[K_NCLASS];
+
+// Launch counter and optional CUDA-event timing of every launch.
+struct Prof {
+  bool on = false;
+  long long launches = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long n[K_NCLASS] = {};
+  double ms[K_NCLASS] = {}, flops[K_NCLASS] = {}, bytes[K_NCLASS] = {};
+  cudaEvent_t take();
+  void begin(cudaStream_t st, cudaEvent_t* e0);
+  void end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, bool launched);
+  int collect();  // fold finished records into the per-class sums
+  void reset();
+  ~Prof();
+};
+
+// Algorithmic flops (2 per multiply-add) and bytes (operands read once, results
+// written once) of one launch.
+struct Cost {
+  double flops = 0, bytes = 0;
+};
+
 // Sizes and decomposition of one system.
 struct SysSpec {
   int N = 0, m = 0, r = 0;
@@ -33,6 +67,9 @@ struct Level {
   std::vector<SepDesc> seps;
   std::vector<SysDesc> sysd;
   std::vector<int> active_fwd, active_back;  // subsystems still active at each step (prefix counts)
+  // per-step launch costs
+  std::vector<Cost> c_inv, c_fwd, c_back, c_fwds, c_backs;
+  Cost c_asm_h, c_asm_f, c_backsub, c_resid, c_axpy, c_sepcopy;
   PartDesc* d_parts = nullptr;
   SepDesc* d_seps = nullptr;
   SysDesc* d_sys = nullptr;
@@ -44,6 +81,7 @@ struct Level {
   std::vector<void*> owned;
 
   int build(const std::vector<SysSpec>& specs, bool fp32_factors);
+  void compute_costs();
   size_t bytes_needed() const;
   int allocate();
   ~Level();
@@ -64,6 +102,7 @@ struct Plan {
   double last_corr = 0.0;
   double factor_flops = 0, solve_flops = 0;
   size_t device_bytes = 0;
+  Prof prof;
 
   int init(const std::vector<SysSpec>& specs, int precision);
   int factor(const double* A, const double* B, const double* C);
@@ -77,8 +116,8 @@ void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& le
 int tuner_seed_p(int N, int m, int r);
 int supp_partitions(int Ms, int P, int r, int m);
 int make_spec(int N, int m, int r, int P, int levels, SysSpec* out);
-void factor_level(Level& L, cudaStream_t st);
-void solve_level(Level& L, const double* F, double* X, cudaStream_t st);
+void factor_level(Level& L, cudaStream_t st, Prof& pf);
+void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf);
 void level_flops(const Level& L, double* ffac, double* fsol);
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);

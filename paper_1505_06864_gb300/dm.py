@@ -43,6 +43,11 @@ class dm_plan_info(ctypes.Structure):
                 ("solve_flops", ctypes.c_double)]
 
 
+class dm_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -64,6 +69,8 @@ def lib():
             "dm_set_stream": (I, [P, P]),
             "dm_set_refinement": (I, [P, D, I]),
             "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
+            "dm_profile": (I, [P, I, ctypes.POINTER(dm_profile_entry), I, ctypes.POINTER(I)]),
+            "dm_launch_count": (ctypes.c_longlong, [P]),
             "dm_destroy": (V, [P]),
             "dm_last_error": (ctypes.c_char_p, []),
         }
@@ -154,6 +161,20 @@ def dm_plan_query(plan) -> dict:
     info = dm_plan_info()
     _check(lib().dm_plan_query(plan, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in dm_plan_info._fields_}
+
+
+def dm_profile(plan, enable=True):
+    """Per-kernel-class sums since the last call (launches, ms, flops, bytes);
+    then clears them and switches event timing on or off."""
+    buf = (dm_profile_entry * 32)()
+    n = ctypes.c_int(0)
+    _check(lib().dm_profile(plan, 1 if enable else 0, buf, 32, ctypes.byref(n)))
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
+                                       bytes=buf[i].bytes) for i in range(n.value)}
+
+
+def dm_launch_count(plan) -> int:
+    return int(lib().dm_launch_count(plan))
 
 
 def dm_destroy(plan):
