@@ -140,6 +140,29 @@ int dm_profile(dm_plan_t plan, int enable, dm_profile_entry* out, int max_entrie
 /* Number of kernels this plan has launched so far (always counted). */
 long long dm_launch_count(dm_plan_t plan);
 
+/* Factor and solve one system without allocating anything, for callers that
+ * cannot call cudaMalloc (code running while another component owns the
+ * device memory pool, plug-ins whose host forbids allocation on the solve
+ * path, real-time loops that must not enter the allocator).  The paper has no
+ * counterpart: this is a deployment variant of dm_plan(N, m, nrhs, P, 1,
+ * DM_FP64) + dm_factor + dm_solve and gives the same x.
+ *
+ * A, B, C ([N][m][m]), b and x ([N][m][nrhs]) must be device pointers on the
+ * current device; x must not alias b.  The workspace is one static 32 MiB
+ * __device__ array compiled into the library (held by every GPU that loads
+ * it until the process exits): the system must fit it, roughly
+ * 4 N m^2 + 5 (P-1) m^2 doubles below 4 Mi, and P <= 256, else DM_EINVAL
+ * (nothing is launched).  The supplementary system is solved by block Thomas.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU (other threads, other streams) race and give
+ * wrong results, so serialise them.  Work is queued on `stream` (NULL: the
+ * default stream) and the call returns after it finished.  DM_ESINGULAR as
+ * for dm_factor. */
+int dm_solve_noalloc(int N, int m, int nrhs, int P, const double* A, const double* B, const double* C,
+                     const double* b, double* x, void* stream);
+
 /* Optional settings and queries. */
 int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */
 int dm_set_refinement(dm_plan_t plan, double tol, int max_iters); /* default 1e-12, 30 */

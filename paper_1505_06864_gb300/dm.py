@@ -71,6 +71,7 @@ def lib():
             "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
             "dm_profile": (I, [P, I, ctypes.POINTER(dm_profile_entry), I, ctypes.POINTER(I)]),
             "dm_launch_count": (ctypes.c_longlong, [P]),
+            "dm_solve_noalloc": (I, [I, I, I, I, P, P, P, P, P, P]),
             "dm_destroy": (V, [P]),
             "dm_last_error": (ctypes.c_char_p, []),
         }
@@ -175,6 +176,14 @@ def dm_profile(plan, enable=True):
 
 def dm_launch_count(plan) -> int:
     return int(lib().dm_launch_count(plan))
+
+
+def dm_solve_noalloc(N, m, nrhs, P, A, B, C, b, x, stream=None):
+    """Factor + solve one system in the library's static device workspace
+    (no allocation).  All arrays must be CUDA tensors; x must not alias b."""
+    h = getattr(stream, "cuda_stream", stream)
+    return _check(lib().dm_solve_noalloc(int(N), int(m), int(nrhs), int(P), _ptr(A), _ptr(B), _ptr(C),
+                                         _ptr(b), _ptr(x, True), ctypes.c_void_p(h) if h else None))
 
 
 def dm_destroy(plan):
