@@ -352,8 +352,13 @@ def mixed_leg(dm, A, B, C, b, stream, x64):
         dm.dm_set_stream(plan, stream)
         dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x, allow_notconv=True))[1], reps=3)
         q = dm.dm_plan_query(plan)
+        dm.dm_profile(plan, True)
+        dm.dm_factor(plan, A, B, C)
+        dm.dm_solve(plan, b, x, allow_notconv=True)
+        prof = dm.dm_profile(plan, False)
         out[name] = {"systems_per_s": 1.0 / dt, "ms": 1e3 * dt, "iters": q["last_iters"], "relres": rel,
-                     "rel_err_vs_fp64_dm": rel_err(x.cpu().numpy(), x64)}
+                     "rel_err_vs_fp64_dm": rel_err(x.cpu().numpy(), x64),
+                     "kernels_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
         dm.dm_destroy(plan)
     return out
 

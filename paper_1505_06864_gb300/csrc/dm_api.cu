@@ -176,10 +176,13 @@ void Level::compute_costs() {
   c_fwds.assign(std::max(Lmax, 1), Cost());
   c_backs.assign(std::max(Lmax, 1), Cost());
   c_asm_h = c_asm_f = c_backsub = c_resid = c_axpy = c_sepcopy = Cost();
+  std::vector<double> chain(std::max(Lmax, 1), 0.0);
   for (const PartDesc& p : parts) {
     const double m2 = (double)p.m * p.m, m3 = 2.0 * m2 * p.m, mr = (double)p.m * p.r, m2r = 2.0 * m2 * p.r;
     const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
     for (int t = 0; t < p.L; ++t) {
+      if (t < p.L - 1) chain[t] += 2 * m3;
+      else if (hr) chain[t] += m3;
       Cost& ci = c_inv[t];
       ci.flops += m3;
       ci.bytes += (t == 0 ? 8.0 : es) * m2 + es * m2;
@@ -205,6 +208,8 @@ void Level::compute_costs() {
       c_backsub.bytes += ns * es * m2 + es * mr + 8.0 * mr;
     }
   }
+  fwd_chain_frac.assign(std::max(Lmax, 1), 1.0);
+  for (int t = 0; t < Lmax; ++t) fwd_chain_frac[t] = c_fwd[t].flops > 0 ? chain[t] / c_fwd[t].flops : 1.0;
   for (const SepDesc& d : seps) {
     const double m2 = (double)d.m * d.m, m3 = 2.0 * m2 * d.m, mr = (double)d.m * d.r, m2r = 2.0 * m2 * d.r;
     const int extra = ((d.flags & HAS_HA) ? 1 : 0) + ((d.flags & HAS_HC) ? 1 : 0);
@@ -358,16 +363,42 @@ Prof::~Prof() {
 // Forward and backward spike sweeps, assembly, and the factorisation of the
 // supplementary level (recursively).  A, B, C must hold the level's blocks.
 template <typename T>
-static void factor_level_t(Level& L, cudaStream_t st, Prof& pf) {
+static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   T* G = static_cast<T*>(L.G);
   T* Ac = static_cast<T*>(L.Acal);
   T* ZL = static_cast<T*>(L.ZL);
   T* ZR = static_cast<T*>(L.ZR);
+  // With a side stream, the left-spike tiles of step t (type 1) run there,
+  // overlapping the next inversion, which depends only on the type-0 tiles.
+  const bool split = aux && aux->st;
+  cudaStream_t sb = split ? aux->st : st;
+  if (split) {
+    cudaEventRecord(aux->ev_main, st);
+    cudaStreamWaitEvent(sb, aux->ev_main, 0);
+  }
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t];
     DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<T>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
-    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwd[t], np,
-              launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st));
+    if (split) {
+      cudaEventRecord(aux->ev_main, st);
+      cudaStreamWaitEvent(sb, aux->ev_main, 0);
+      Cost c0 = L.c_fwd[t], c1 = L.c_fwd[t];
+      c0.flops *= L.fwd_chain_frac[t];
+      c0.bytes *= L.fwd_chain_frac[t];
+      c1.flops -= c0.flops;
+      c1.bytes -= c0.bytes;
+      DM_LAUNCH(pf, st, K_FWD_FACTOR, c0, np,
+                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st, 0, 1));
+      DM_LAUNCH(pf, sb, K_FWD_FACTOR, c1, np,
+                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, sb, 1, 2));
+    } else {
+      DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwd[t], np,
+                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st));
+    }
+  }
+  if (split) {
+    cudaEventRecord(aux->ev_aux, sb);
+    cudaStreamWaitEvent(st, aux->ev_aux, 0);
   }
   for (int s = 0; s + 1 < L.Lmax; ++s)
     DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], L.active_back[s],
@@ -378,13 +409,13 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf) {
                                    L.supp->C, st));
 }
 
-void factor_level(Level& L, cudaStream_t st, Prof& pf) {
+void factor_level(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   cudaMemsetAsync(L.status, 0x7f, std::max(1, L.nsys) * sizeof(int), st);
   if (L.f32)
-    factor_level_t<float>(L, st, pf);
+    factor_level_t<float>(L, st, pf, aux);
   else
-    factor_level_t<double>(L, st, pf);
-  if (L.supp) factor_level(*L.supp, st, pf);
+    factor_level_t<double>(L, st, pf, aux);
+  if (L.supp) factor_level(*L.supp, st, pf, aux);
 }
 
 // Solve with resident factors: F -> X for every system of the level.
@@ -489,6 +520,9 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   if (rc) return rc;
   DM_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
   stream = own_stream;
+  DM_CUDA(cudaStreamCreateWithFlags(&aux.st, cudaStreamNonBlocking));
+  DM_CUDA(cudaEventCreateWithFlags(&aux.ev_main, cudaEventDisableTiming));
+  DM_CUDA(cudaEventCreateWithFlags(&aux.ev_aux, cudaEventDisableTiming));
   rc = top.allocate();
   if (rc) return rc;
   auto alloc = [&](void** p, size_t bytes) -> int {
@@ -514,6 +548,9 @@ Plan::~Plan() {
   if (Dx) cudaFree(Dx);
   if (nrm) cudaFree(nrm);
   if (own_stream) cudaStreamDestroy(own_stream);
+  if (aux.st) cudaStreamDestroy(aux.st);
+  if (aux.ev_main) cudaEventDestroy(aux.ev_main);
+  if (aux.ev_aux) cudaEventDestroy(aux.ev_aux);
 }
 
 int Plan::factor(const double* A, const double* B, const double* C) {
@@ -522,7 +559,7 @@ int Plan::factor(const double* A, const double* B, const double* C) {
   if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
-  factor_level(top, st, prof);
+  factor_level(top, st, prof, &aux);
   DM_CUDA(cudaGetLastError());
   rc = check_status(top, st, 0);
   factored = (rc == DM_OK);

@@ -46,9 +46,12 @@ struct SysDesc {
 template <typename T>
 void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G, int* status,
                 int max_m, cudaStream_t st);
+// type_lo..type_hi-1 select the tile types: 0 = Acal_t and the next Schur
+// block (the inversion chain), 1 = left spike (off the chain).
 template <typename T>
 void launch_fwd_factor(const PartDesc* parts, int nparts, int t, int max_m, const double* A,
-                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st);
+                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st,
+                       int type_lo = 0, int type_hi = 2);
 template <typename T>
 void launch_back_factor(const PartDesc* parts, int nparts, int s, int max_m, const T* Acal, T* ZL,
                         T* ZR, cudaStream_t st);

@@ -17,6 +17,9 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "dm_internal.cuh"
 
@@ -231,6 +234,137 @@ __global__ void __launch_bounds__(512) k_inv(const PartDesc* __restrict__ parts,
 }
 
 // ---------------------------------------------------------------------------
+// The same block inverse with the columns split over a thread-block cluster
+// of `cs` CTAs: CTA r keeps columns [r w, (r+1) w) of the working matrix in
+// its shared memory (w = ceil(m / cs)).  Step k: the CTA owning column k
+// searches the pivot in that column, exchanges rows k and p in it and
+// publishes the column (and p) in its shared memory; one cluster barrier;
+// every CTA reads the published column through distributed shared memory,
+// exchanges rows k and p in its own columns and applies the rank-1 update to
+// them.  The published column is double-buffered: a CTA can only overwrite
+// buffer k&1 at step k+2, after every CTA has passed step k+1's barrier and
+// therefore finished reading it.  No CTA of a cluster returns early except
+// all together, and a final barrier keeps every CTA's shared memory alive
+// until the last remote read.
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_cluster(const PartDesc* __restrict__ parts, int t,
+                                                     const double* __restrict__ B, T* __restrict__ G,
+                                                     int* __restrict__ status, int cs) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const PartDesc p = parts[blockIdx.x / cs];
+  if (t >= p.L) return;  // the same for every CTA of the cluster
+  const int m = p.m;
+  const int w = (m + cs - 1) / cs, c0 = rank * w, wc = max(0, min(w, m - c0));
+  const int lda = w + 1;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  T* pub = reinterpret_cast<T*>(smem_raw);  // [2][kMaxM]
+  T* colk = pub + 2 * kMaxM;                // [kMaxM]
+  T* rowk = colk + kMaxM;                   // [128]
+  T* a = rowk + 128;                        // [m][w+1]
+  int* perm = reinterpret_cast<int*>(a + (size_t)m * lda);  // [kMaxM]
+  int* idx = perm + kMaxM;                                  // [kMaxM]
+  int* inv_idx = idx + kMaxM;                               // [kMaxM]
+  __shared__ int pubp[2];
+  __shared__ int s_p, s_bad;
+  __shared__ T s_akk, s_apk;
+  const long long o = p.blk + (long long)t * m * m;
+  T* g = G + o;
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < m * wc; e += nthr) {
+    const int i = e / wc, jl = e - i * wc;
+    a[i * lda + jl] = (t == 0) ? (T)B[o + (long long)i * m + c0 + jl] : g[(long long)i * m + c0 + jl];
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  for (int k = 0; k < m; ++k) {
+    const int owner = k / w, kl = k - owner * w;
+    const int buf = k & 1;
+    const bool own = (rank == owner);
+    if (own && warp == 0) {
+      // pivot search over rows k..m-1 of column k (ties to the lowest row),
+      // then publish the column as it reads after exchanging rows k and p
+      T best = (T)-1;
+      int bi = k;
+      for (int i = k + lane; i < m; i += 32) {
+        const T v = fabs(a[i * lda + kl]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      bi = __shfl_sync(0xffffffffu, bi, 0);
+      const T akk = a[k * lda + kl], apk = a[bi * lda + kl];
+      T* pb = pub + buf * kMaxM;
+      for (int i = lane; i < m; i += 32) pb[i] = (i == k) ? apk : (i == bi ? akk : a[i * lda + kl]);
+      if (lane == 0) pubp[buf] = bi;
+    }
+    cl.sync();
+    const T* rb = cl.map_shared_rank(pub + buf * kMaxM, owner);
+    const int pr = *cl.map_shared_rank(&pubp[buf], owner);
+    const T piv = rb[k];
+    T inv = (T)1 / piv;
+    if (!(fabs(piv) > (T)0) || !isfinite(inv)) {
+      inv = (T)0;
+      if (tid == 0 && own) s_bad = 1;
+    }
+    for (int i = tid; i < m; i += nthr) colk[i] = rb[i];
+    for (int jl = tid; jl < wc; jl += nthr) {
+      const T vk = a[k * lda + jl], vp = a[pr * lda + jl];
+      if (pr != k) {
+        a[k * lda + jl] = vp;
+        a[pr * lda + jl] = vk;
+      }
+      rowk[jl] = vp * inv;
+    }
+    if (tid == 0) perm[k] = pr;
+    __syncthreads();
+    // rank-1 update of every local column; rowk stays in registers
+    for (int jl = lane; jl < wc; jl += 32) {
+      const T rj = rowk[jl];
+      int i = warp;
+      for (; i + 3 * nwarp < m; i += 4 * nwarp) {
+        const int i1 = i + nwarp, i2 = i + 2 * nwarp, i3 = i + 3 * nwarp;
+        const T c0v = colk[i], c1v = colk[i1], c2v = colk[i2], c3v = colk[i3];
+        const T a0 = a[i * lda + jl], a1 = a[i1 * lda + jl], a2 = a[i2 * lda + jl], a3 = a[i3 * lda + jl];
+        a[i * lda + jl] = (i == k) ? rj : fma(-c0v, rj, a0);
+        a[i1 * lda + jl] = (i1 == k) ? rj : fma(-c1v, rj, a1);
+        a[i2 * lda + jl] = (i2 == k) ? rj : fma(-c2v, rj, a2);
+        a[i3 * lda + jl] = (i3 == k) ? rj : fma(-c3v, rj, a3);
+      }
+      for (; i < m; i += nwarp) a[i * lda + jl] = (i == k) ? rj : fma(-colk[i], rj, a[i * lda + jl]);
+    }
+    __syncthreads();
+    // column k itself becomes the k-th column of the running inverse
+    if (own)
+      for (int i = tid; i < m; i += nthr) a[i * lda + kl] = (i == k) ? inv : -colk[i] * inv;
+  }
+  cl.sync();  // every remote read of this CTA's buffers is done
+  if (tid == 0) {
+    for (int c = 0; c < m; ++c) idx[c] = c;
+    for (int k = m - 1; k >= 0; --k) {
+      const int q = perm[k];
+      const int tmp = idx[k];
+      idx[k] = idx[q];
+      idx[q] = tmp;
+    }
+    for (int c = 0; c < m; ++c) inv_idx[idx[c]] = c;
+  }
+  __syncthreads();
+  // column c0 + jl of inv(Pi D) is column inv_idx[c0 + jl] of D^{-1}
+  for (int e = tid; e < m * wc; e += nthr) {
+    const int i = e / wc, jl = e - i * wc;
+    g[(long long)i * m + inv_idx[c0 + jl]] = a[i * lda + jl];
+  }
+  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+}
+
+// ---------------------------------------------------------------------------
 // Forward step t of the factor sweep (Section 3, applied to subsystem S^k
 // with right-hand sides W_R^k, Eq. e231).  Tile types:
 //   0: Acal_t[:, J] = G_t C_t[:, J], then D_{t+1}[:, J] = B_{t+1}[:, J] - A_{t+1} Acal_t[:, J]
@@ -240,7 +374,7 @@ __global__ void __launch_bounds__(512) k_inv(const PartDesc* __restrict__ parts,
 //   1: left spike (k > 0): Bcal_t = G_t A_first at t = 0, else G_t (-A_t Bcal_{t-1}).
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_fwd_factor(const PartDesc* __restrict__ parts, int t,
-                                                         int tiles, const double* __restrict__ A,
+                                                         int tiles, int type_lo, const double* __restrict__ A,
                                                          const double* __restrict__ B,
                                                          const double* __restrict__ C,
                                                          T* __restrict__ G, T* __restrict__ Acal,
@@ -249,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor(const PartDesc* __restr
   const PartDesc p = parts[blockIdx.y];
   if (t >= p.L) return;
   const int m = p.m;
-  const int type = blockIdx.x / tiles, c0 = (blockIdx.x - type * tiles) * W;
+  const int tb = blockIdx.x / tiles, type = type_lo + tb, c0 = (blockIdx.x - tb * tiles) * W;
   if (c0 >= m) return;
   T* Rs = reinterpret_cast<T*>(smem_raw);
   T* Xs = Rs + m * W;
@@ -525,6 +659,172 @@ __global__ void __launch_bounds__(kThreads) k_backsub(const PartDesc* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Narrow products for right-hand sides with r <= RM <= 16 columns: a warp per
+// output row, lanes striding over k (coalesced reads of the m x m block), RM
+// partial sums per lane reduced with shuffles.  R panels live in shared memory
+// as [m][RM], zero past column r.  No multiply-add is spent on padding beyond
+// the bucket RM in {1, 2, 4, 8, 16}.
+template <typename T, typename TL1, typename TL2, int RM, typename Epi>
+__device__ __forceinline__ void narrow_mm(int m, const TL1* __restrict__ L1, const T* __restrict__ R1,
+                                          const TL2* __restrict__ L2, const T* __restrict__ R2, Epi epi) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < m; i += nw) {
+    T acc[RM];
+#pragma unroll
+    for (int c = 0; c < RM; ++c) acc[c] = (T)0;
+    const TL1* l1 = L1 + (long long)i * m;
+    for (int k = lane; k < m; k += 32) {
+      const T lv = (T)l1[k];
+#pragma unroll
+      for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R1[k * RM + c], acc[c]);
+    }
+    if (L2 != nullptr) {
+      const TL2* l2 = L2 + (long long)i * m;
+      for (int k = lane; k < m; k += 32) {
+        const T lv = (T)l2[k];
+#pragma unroll
+        for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R2[k * RM + c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      T v = acc[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      acc[c] = v;
+    }
+    T mine = (T)0;
+#pragma unroll
+    for (int c = 0; c < RM; ++c)
+      if (c == lane) mine = acc[c];
+    if (lane < RM) epi(i, lane, mine);
+  }
+}
+
+// Rs[k][c] = src[k * r + c] for c < r, zero up to RM.
+template <typename T, typename TS, int RM>
+__device__ __forceinline__ void load_narrow(T* Rs, const TS* __restrict__ src, int m, int r) {
+  for (int e = threadIdx.x; e < m * RM; e += blockDim.x) {
+    const int k = e / RM, c = e - k * RM;
+    Rs[e] = c < r ? (T)src[(long long)k * r + c] : (T)0;
+  }
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(256) k_fwd_solve_n(const PartDesc* __restrict__ parts, int t,
+                                                     const double* __restrict__ A, const T* __restrict__ G,
+                                                     const double* __restrict__ F, T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.x];
+  if (t >= p.L) return;
+  const int m = p.m, r = p.r;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Xs = Rs + m * RM;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  const double* Ft = F + v;
+  if (t == 0) {
+    load_narrow<T, double, RM>(Rs, Ft, m, r);
+  } else {
+    load_narrow<T, T, RM>(Xs, z + v - mr, m, r);
+    __syncthreads();
+    narrow_mm<T, double, double, RM>(m, A + o, Xs, (const double*)nullptr, (const T*)nullptr,
+                                     [&](int row, int col, T val) {
+                                       Rs[row * RM + col] = col < r ? (T)Ft[(long long)row * r + col] - val : (T)0;
+                                     });
+  }
+  __syncthreads();
+  T* dst = z + v;
+  narrow_mm<T, T, T, RM>(m, G + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
+    if (col < r) dst[(long long)row * r + col] = val;
+  });
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(256) k_back_solve_n(const PartDesc* __restrict__ parts, int s,
+                                                      const T* __restrict__ Acal, T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.x];
+  const int t = p.L - 2 - s;
+  if (t < 0) return;
+  const int m = p.m, r = p.r;
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  T* Y = z + v;
+  load_narrow<T, T, RM>(Rs, Y + mr, m, r);
+  __syncthreads();
+  narrow_mm<T, T, T, RM>(m, Acal + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
+    if (col < r) {
+      const long long e = (long long)row * r + col;
+      Y[e] = Y[e] - val;
+    }
+  });
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(256) k_assemble_f_n(const SepDesc* __restrict__ seps,
+                                                      const double* __restrict__ A,
+                                                      const double* __restrict__ C,
+                                                      const double* __restrict__ F,
+                                                      const T* __restrict__ z, double* __restrict__ fh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SepDesc sp = seps[blockIdx.x];
+  const int m = sp.m, r = sp.r;
+  double* R1 = reinterpret_cast<double*>(smem_raw);
+  double* R2 = R1 + m * RM;
+  load_narrow<double, T, RM>(R1, z + sp.vec_prev, m, r);
+  load_narrow<double, T, RM>(R2, z + sp.vec_next, m, r);
+  __syncthreads();
+  const double* Fq = F + sp.vec_q;
+  double* dst = fh + sp.hvec;
+  narrow_mm<double, double, double, RM>(m, A + sp.blk_q, R1, C + sp.blk_q, R2, [&](int row, int col, double v) {
+    if (col < r) {
+      const long long e = (long long)row * r + col;
+      dst[e] = Fq[e] - v;
+    }
+  });
+}
+
+// Back-substitution for row t = blockIdx.x of subsystem blockIdx.y.
+template <typename T, int RM>
+__global__ void __launch_bounds__(256) k_backsub_n(const PartDesc* __restrict__ parts,
+                                                   const T* __restrict__ ZL, const T* __restrict__ ZR,
+                                                   const T* __restrict__ z, const double* __restrict__ h,
+                                                   double* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PartDesc p = parts[blockIdx.y];
+  const int t = blockIdx.x;
+  if (t >= p.L) return;
+  const int m = p.m, r = p.r;
+  double* R1 = reinterpret_cast<double*>(smem_raw);
+  double* R2 = R1 + m * RM;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+  const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
+  if (hl) load_narrow<double, double, RM>(R1, h + p.hprev, m, r);
+  if (hr) load_narrow<double, double, RM>(R2, h + p.hnext, m, r);
+  __syncthreads();
+  const T* zt = z + v;
+  double* xt = x + v;
+  auto epi = [&](int row, int col, double val) {
+    if (col < r) {
+      const long long e = (long long)row * r + col;
+      xt[e] = (double)zt[e] - val;
+    }
+  };
+  if (hl && hr) {
+    narrow_mm<double, T, T, RM>(m, ZL + o, R1, ZR + o, R2, epi);
+  } else if (hl) {
+    narrow_mm<double, T, T, RM>(m, ZL + o, R1, (const T*)nullptr, (const double*)nullptr, epi);
+  } else if (hr) {
+    narrow_mm<double, T, T, RM>(m, ZR + o, R2, (const T*)nullptr, (const double*)nullptr, epi);
+  } else {
+    for (int e = threadIdx.x; e < mr; e += blockDim.x) xt[e] = (double)zt[e];
+  }
+}
+
 __global__ void k_sep_copy(const SepDesc* __restrict__ seps, const double* __restrict__ h,
                            double* __restrict__ x) {
   const SepDesc sp = seps[blockIdx.x];
@@ -535,8 +835,11 @@ __global__ void k_sep_copy(const SepDesc* __restrict__ seps, const double* __res
 // ---------------------------------------------------------------------------
 // Residual r_i = b_i - A_i x_{i-1} - B_i x_i - C_i x_{i+1} in float64.  One CTA
 // per block row; a warp per output row reads A/B/C rows coalesced and reduces
-// with shuffles; x_{i-1}, x_i, x_{i+1} are staged in shared memory 16 columns
-// at a time.  Column sums of r^2 and b^2 go to nrm by atomics.
+// with shuffles; x_{i-1}, x_i, x_{i+1} are staged in shared memory RM columns
+// at a time (RM in {1, 2, 4, 8, 16}, the smallest bucket >= nrhs, so no
+// multiply-add is spent on padding columns).  Column sums of r^2 and b^2 go
+// to nrm by atomics.
+template <int RM>
 __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sys,
                                                   const double* __restrict__ A,
                                                   const double* __restrict__ B,
@@ -553,35 +856,35 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
   const int m = sd.m, r = sd.r;
   const long long mm = (long long)m * m, mr = (long long)m * r;
   const long long o = sd.blk + i * mm, v = sd.vec + i * mr;
-  double* xs = reinterpret_cast<double*>(smem_raw);  // [3][m][16]
+  double* xs = reinterpret_cast<double*>(smem_raw);  // [3][m][RM]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < 2 * r; e += blockDim.x) red[e] = 0.0;
   const bool hasA = i > 0, hasC = i < sd.N - 1;
-  for (int c0 = 0; c0 < r; c0 += 16) {
-    const int nc = min(16, r - c0);
+  for (int c0 = 0; c0 < r; c0 += RM) {
+    const int nc = min(RM, r - c0);
     __syncthreads();
-    for (int e = tid; e < 3 * m * 16; e += blockDim.x) {
-      const int which = e / (m * 16), rem = e - which * m * 16, k = rem >> 4, c = rem & 15;
+    for (int e = tid; e < 3 * m * RM; e += blockDim.x) {
+      const int which = e / (m * RM), rem = e - which * m * RM, k = rem / RM, c = rem - k * RM;
       const int row = i - 1 + which;
       xs[e] = (row >= 0 && row < sd.N && c < nc) ? x[sd.vec + row * mr + (long long)k * r + c0 + c] : 0.0;
     }
     __syncthreads();
     for (int row = warp; row < m; row += 8) {
-      double acc[16];
+      double acc[RM];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+      for (int c = 0; c < RM; ++c) acc[c] = 0.0;
       for (int k = lane; k < m; k += 32) {
         const double a = hasA ? A[o + (long long)row * m + k] : 0.0;
         const double bb = B[o + (long long)row * m + k];
         const double cc = hasC ? C[o + (long long)row * m + k] : 0.0;
-        const double* xm = xs + k * 16;
-        const double* x0 = xm + m * 16;
-        const double* xp = x0 + m * 16;
+        const double* xm = xs + k * RM;
+        const double* x0 = xm + m * RM;
+        const double* xp = x0 + m * RM;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = fma(a, xm[c], fma(bb, x0[c], fma(cc, xp[c], acc[c])));
+        for (int c = 0; c < RM; ++c) acc[c] = fma(a, xm[c], fma(bb, x0[c], fma(cc, xp[c], acc[c])));
       }
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < RM; ++c) {
         double s = acc[c];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -590,7 +893,7 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
       if (lane < nc) {
         double s = 0.0;
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
+        for (int c = 0; c < RM; ++c)
           if (c == lane) s = acc[c];
         const long long e = v + (long long)row * r + c0 + lane;
         const double bv = b[e];
@@ -654,10 +957,54 @@ int inv_smem_max_m() {
 
 // ---------------------------------------------------------------------------
 // launchers
+// r <= 16: call f with the smallest bucket RM >= r as a compile-time constant
+template <typename F>
+bool narrow_dispatch(int max_r, F&& f) {
+  if (max_r <= 1) return f(std::integral_constant<int, 1>()), true;
+  if (max_r <= 2) return f(std::integral_constant<int, 2>()), true;
+  if (max_r <= 4) return f(std::integral_constant<int, 4>()), true;
+  if (max_r <= 8) return f(std::integral_constant<int, 8>()), true;
+  if (max_r <= 16) return f(std::integral_constant<int, 16>()), true;
+  return false;
+}
+
+template <typename T>
+int inv_cluster_size(int max_m) {
+  // float64: ~32 columns per CTA so the FP64 pipes of cs SMs share a block;
+  // float32: one CTA up to m = 128, else 64 columns per CTA (the update is
+// cheap, barriers dominate).
+  if (sizeof(T) == 4 && max_m <= 128) return 1;
+  const int per = sizeof(T) == 8 ? 32 : 64;
+  int cs = 1;
+  while (cs * per < max_m) cs *= 2;
+  return cs;
+}
+
 template <typename T>
 void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G, int* status,
                 int max_m, cudaStream_t st) {
   if (nparts <= 0) return;
+  const int cs = inv_cluster_size<T>(max_m);
+  if (cs <= 8) {
+    const int w = (max_m + cs - 1) / cs;
+    const size_t bytes = sizeof(T) * (3 * (size_t)kMaxM + 128 + (size_t)max_m * (w + 1)) + 3 * kMaxM * sizeof(int);
+    allow_smem(k_inv_cluster<T>, bytes);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nparts * cs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_inv_cluster<T>, parts, t, B, G, status, cs);
+    return;
+  }
+  // float64 blocks above m = 256: one CTA per block, working matrix in global memory
   const int smax = inv_smem_max_m<T>();
   const size_t base = 2 * kMaxM * sizeof(int) + 2 * kMaxM * sizeof(T);
   const size_t bytes = base + (max_m <= smax ? (size_t)max_m * (max_m + 1) * sizeof(T) : 0);
@@ -670,20 +1017,24 @@ void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G,
 
 template <typename T>
 void launch_fwd_factor(const PartDesc* parts, int nparts, int t, int max_m, const double* A,
-                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st) {
-  if (nparts <= 0) return;
+                       const double* B, const double* C, T* G, T* Acal, T* ZL, T* ZR, cudaStream_t st,
+                       int type_lo, int type_hi) {
+  if (nparts <= 0 || type_hi <= type_lo) return;
+  const int nt = type_hi - type_lo;
   if (max_m <= 256) {
     constexpr int W = 32;
     const int tiles = ntiles<W>(max_m);
     const size_t bytes = panel_smem<T>(max_m, W, 2);
     allow_smem(k_fwd_factor<T, W>, bytes);
-    k_fwd_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, A, B, C, G, Acal, ZL, ZR);
+    k_fwd_factor<T, W><<<dim3(nt * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, type_lo, A, B, C, G, Acal,
+                                                                          ZL, ZR);
   } else {
     constexpr int W = 16;
     const int tiles = ntiles<W>(max_m);
     const size_t bytes = panel_smem<T>(max_m, W, 2);
     allow_smem(k_fwd_factor<T, W>, bytes);
-    k_fwd_factor<T, W><<<dim3(2 * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, A, B, C, G, Acal, ZL, ZR);
+    k_fwd_factor<T, W><<<dim3(nt * tiles, nparts), kThreads, bytes, st>>>(parts, t, tiles, type_lo, A, B, C, G, Acal,
+                                                                          ZL, ZR);
   }
 }
 
@@ -710,6 +1061,13 @@ template <typename T>
 void launch_fwd_solve(const PartDesc* parts, int nparts, int t, int max_m, int max_r,
                       const double* A, const T* G, const double* F, T* z, cudaStream_t st) {
   if (nparts <= 0) return;
+  if (narrow_dispatch(max_r, [&](auto rm) {
+        constexpr int RM = decltype(rm)::value;
+        const size_t bytes = sizeof(T) * 2 * (size_t)max_m * RM;
+        allow_smem(k_fwd_solve_n<T, RM>, bytes);
+        k_fwd_solve_n<T, RM><<<nparts, 256, bytes, st>>>(parts, t, A, G, F, z);
+      }))
+    return;
   if (max_r <= 16) {
     constexpr int W = 16;
     const size_t bytes = panel_smem<T>(max_m, W, 2);
@@ -727,6 +1085,13 @@ template <typename T>
 void launch_back_solve(const PartDesc* parts, int nparts, int s, int max_m, int max_r,
                        const T* Acal, T* z, cudaStream_t st) {
   if (nparts <= 0) return;
+  if (narrow_dispatch(max_r, [&](auto rm) {
+        constexpr int RM = decltype(rm)::value;
+        const size_t bytes = sizeof(T) * (size_t)max_m * RM;
+        allow_smem(k_back_solve_n<T, RM>, bytes);
+        k_back_solve_n<T, RM><<<nparts, 256, bytes, st>>>(parts, s, Acal, z);
+      }))
+    return;
   if (max_r <= 16) {
     constexpr int W = 16;
     const size_t bytes = panel_smem<T>(max_m, W, 1);
@@ -764,6 +1129,13 @@ template <typename T>
 void launch_assemble_f(const SepDesc* seps, int nseps, int max_m, int max_r, const double* A,
                        const double* C, const double* F, const T* z, double* fh, cudaStream_t st) {
   if (nseps <= 0) return;
+  if (narrow_dispatch(max_r, [&](auto rm) {
+        constexpr int RM = decltype(rm)::value;
+        const size_t bytes = sizeof(double) * 2 * (size_t)max_m * RM;
+        allow_smem(k_assemble_f_n<T, RM>, bytes);
+        k_assemble_f_n<T, RM><<<nseps, 256, bytes, st>>>(seps, A, C, F, z, fh);
+      }))
+    return;
   if (max_r <= 16) {
     constexpr int W = 16;
     const size_t bytes = panel_smem<double>(max_m, W, 2);
@@ -781,6 +1153,13 @@ template <typename T>
 void launch_backsub(const PartDesc* parts, int nparts, int Lmax, int max_m, int max_r, const T* ZL,
                     const T* ZR, const T* z, const double* h, double* x, cudaStream_t st) {
   if (nparts <= 0 || Lmax <= 0) return;
+  if (narrow_dispatch(max_r, [&](auto rm) {
+        constexpr int RM = decltype(rm)::value;
+        const size_t bytes = sizeof(double) * 2 * (size_t)max_m * RM;
+        allow_smem(k_backsub_n<T, RM>, bytes);
+        k_backsub_n<T, RM><<<dim3(Lmax, nparts), 256, bytes, st>>>(parts, ZL, ZR, z, h, x);
+      }))
+    return;
   if (max_r <= 16) {
     constexpr int W = 16;
     const int tiles = ntiles<W>(max_r);
@@ -806,9 +1185,13 @@ void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_
                      const double* B, const double* C, const double* x, const double* b, double* r,
                      double* nrm, cudaStream_t st) {
   if (nsys <= 0 || Nmax <= 0) return;
-  const size_t bytes = sizeof(double) * 3 * (size_t)max_m * 16;
-  allow_smem(k_residual, bytes);
-  k_residual<<<dim3(Nmax, nsys), 256, bytes, st>>>(sys, A, B, C, x, b, r, nrm);
+  auto go = [&](auto rm) {
+    constexpr int RM = decltype(rm)::value;
+    const size_t bytes = sizeof(double) * 3 * (size_t)max_m * RM;
+    allow_smem(k_residual<RM>, bytes);
+    k_residual<RM><<<dim3(Nmax, nsys), 256, bytes, st>>>(sys, A, B, C, x, b, r, nrm);
+  };
+  if (!narrow_dispatch(max_r, go)) go(std::integral_constant<int, 16>());
 }
 
 void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
@@ -820,7 +1203,7 @@ void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int ma
 #define DM_INST(T)                                                                                  \
   template void launch_inv<T>(const PartDesc*, int, int, const double*, T*, int*, int, cudaStream_t); \
   template void launch_fwd_factor<T>(const PartDesc*, int, int, int, const double*, const double*,  \
-                                     const double*, T*, T*, T*, T*, cudaStream_t);                  \
+                                     const double*, T*, T*, T*, T*, cudaStream_t, int, int);        \
   template void launch_back_factor<T>(const PartDesc*, int, int, int, const T*, T*, T*, cudaStream_t); \
   template void launch_fwd_solve<T>(const PartDesc*, int, int, int, int, const double*, const T*,   \
                                     const double*, T*, cudaStream_t);                               \

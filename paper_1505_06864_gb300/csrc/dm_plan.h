@@ -46,6 +46,13 @@ struct Cost {
   double flops = 0, bytes = 0;
 };
 
+// Side stream for work off the inversion chain, with the two events that
+// order it against the main stream.
+struct Aux {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_aux = nullptr;
+};
+
 // Sizes and decomposition of one system.
 struct SysSpec {
   int N = 0, m = 0, r = 0;
@@ -69,6 +76,7 @@ struct Level {
   std::vector<int> active_fwd, active_back;  // subsystems still active at each step (prefix counts)
   // per-step launch costs
   std::vector<Cost> c_inv, c_fwd, c_back, c_fwds, c_backs;
+  std::vector<double> fwd_chain_frac;  // share of c_fwd[t] in the type-0 (chain) tiles
   Cost c_asm_h, c_asm_f, c_backsub, c_resid, c_axpy, c_sepcopy;
   PartDesc* d_parts = nullptr;
   SepDesc* d_seps = nullptr;
@@ -103,6 +111,7 @@ struct Plan {
   double factor_flops = 0, solve_flops = 0;
   size_t device_bytes = 0;
   Prof prof;
+  Aux aux;
 
   int init(const std::vector<SysSpec>& specs, int precision);
   int factor(const double* A, const double* B, const double* C);
@@ -116,7 +125,7 @@ void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& le
 int tuner_seed_p(int N, int m, int r);
 int supp_partitions(int Ms, int P, int r, int m);
 int make_spec(int N, int m, int r, int P, int levels, SysSpec* out);
-void factor_level(Level& L, cudaStream_t st, Prof& pf);
+void factor_level(Level& L, cudaStream_t st, Prof& pf, Aux* aux = nullptr);
 void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf);
 void level_flops(const Level& L, double* ffac, double* fsol);
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
