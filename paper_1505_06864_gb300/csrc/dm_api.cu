@@ -514,6 +514,43 @@ int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   return DM_OK;
 }
 
+template <typename F>
+int Plan::run(GraphCache& g, F&& body) {
+  cudaStream_t st = stream;
+  if (prof.on || !use_graphs || g.broken || g.uses == 0) {
+    const long long l0 = prof.launches;
+    body();
+    if (g.uses == 0) g.launches = prof.launches - l0;
+    ++g.uses;
+    DM_CUDA(cudaGetLastError());
+    return DM_OK;
+  }
+  if (!g.exec) {
+    const long long l0 = prof.launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g.broken = true;
+      return run(g, body);
+    }
+    body();
+    prof.launches = l0;  // the capture itself launches nothing
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      g.broken = true;
+      return run(g, body);
+    }
+  }
+  DM_CUDA(cudaGraphLaunch(g.exec, st));
+  prof.launches += g.launches;
+  ++g.uses;
+  return DM_OK;
+}
+
 int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
   int rc = top.build(specs, prec != DM_FP64);
@@ -547,6 +584,8 @@ Plan::~Plan() {
   if (R) cudaFree(R);
   if (Dx) cudaFree(Dx);
   if (nrm) cudaFree(nrm);
+  for (GraphCache* g : {&g_factor, &g_solve, &g_iter_first, &g_iter_next})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
   if (own_stream) cudaStreamDestroy(own_stream);
   if (aux.st) cudaStreamDestroy(aux.st);
   if (aux.ev_main) cudaEventDestroy(aux.ev_main);
@@ -559,8 +598,8 @@ int Plan::factor(const double* A, const double* B, const double* C) {
   if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
   if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
-  factor_level(top, st, prof, &aux);
-  DM_CUDA(cudaGetLastError());
+  rc = run(g_factor, [&] { factor_level(top, stream, prof, &aux); });
+  if (rc) return rc;
   rc = check_status(top, st, 0);
   factored = (rc == DM_OK);
   return rc;
@@ -582,11 +621,15 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
   cudaStream_t st = stream;
   const size_t nb = (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double);
   if (precision == DM_FP64) {
-    solve_level(top, b_dev, x_dev, st, prof);
-    DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
-    DM_LAUNCH(prof, st, K_RESIDUAL, top.c_resid, top.nsys,
-              launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                              b_dev, R, nrm, st));
+    auto body = [&] {
+      solve_level(top, b_dev, x_dev, stream, prof);
+      cudaMemsetAsync(nrm, 0, nb, stream);
+      DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
+                launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                                b_dev, R, nrm, stream));
+    };
+    int rc0 = (b_dev == top.F && x_dev == top.X) ? run(g_solve, body) : (body(), DM_OK);
+    if (rc0) return rc0;
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));
@@ -603,13 +646,17 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
   int it = 0;
   double corr = 0.0;
   for (it = 1; it <= max_iters; ++it) {
-    solve_level(top, rhs, Dx, st, prof);
-    DM_CUDA(cudaMemsetAsync(nrm, 0, nb, st));
-    DM_LAUNCH(prof, st, K_AXPY, top.c_axpy, top.nsys,
-              launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, st));
-    DM_LAUNCH(prof, st, K_RESIDUAL, top.c_resid, top.nsys,
-              launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                              b_dev, R, nrm, st));
+    auto body = [&] {
+      solve_level(top, rhs, Dx, stream, prof);
+      cudaMemsetAsync(nrm, 0, nb, stream);
+      DM_LAUNCH(prof, stream, K_AXPY, top.c_axpy, top.nsys,
+                launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, stream));
+      DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
+                launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                                b_dev, R, nrm, stream));
+    };
+    int rc0 = (b_dev == top.F && x_dev == top.X) ? run(it == 1 ? g_iter_first : g_iter_next, body) : (body(), DM_OK);
+    if (rc0) return rc0;
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));

@@ -17,7 +17,9 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include <cooperative_groups.h>
 
@@ -939,9 +941,22 @@ __global__ void __launch_bounds__(256) k_axpy_norms(const SysDesc* __restrict__ 
   }
 }
 
+// Raise a kernel's dynamic shared memory limit once per kernel (to the
+// largest size asked for so far), so that launches inside a stream capture
+// make no attribute calls.
+std::mutex g_smem_mu;
+std::unordered_map<const void*, size_t> g_smem_granted;
+
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes <= 48 * 1024) return;
+  const void* key = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& g = g_smem_granted[key];
+  if (bytes > g) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    g = bytes;
+  }
 }
 
 template <typename T>

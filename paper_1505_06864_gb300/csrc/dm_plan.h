@@ -95,6 +95,15 @@ struct Level {
   ~Level();
 };
 
+// A captured launch sequence: the first use runs eagerly, the second captures
+// it into a CUDA graph, later uses replay the graph.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  int uses = 0;
+  long long launches = 0;  // kernels in one replay
+  bool broken = false;     // capture failed: stay eager
+};
+
 struct Plan {
   int precision = 0;
   Level top;
@@ -112,6 +121,10 @@ struct Plan {
   size_t device_bytes = 0;
   Prof prof;
   Aux aux;
+  bool use_graphs = true;
+  GraphCache g_factor, g_solve, g_iter_first, g_iter_next;
+  template <typename F>
+  int run(GraphCache& g, F&& body);
 
   int init(const std::vector<SysSpec>& specs, int precision);
   int factor(const double* A, const double* B, const double* C);

@@ -188,3 +188,78 @@ def test_config3_fp32_refined_full_size(dm):
     x, rel, info = solve(dm, s, 0, 0, "fp32")
     xo = o.dm(s.A, s.B, s.C, s.b, info["P"], levels=info["levels"], P2=info["P2"] if info["P2"] > 1 else None)
     check(x, xo, TOLMIX)
+
+
+def _batch(shapes, seed0):
+    systems = [w.dominant_system(N, m, r, seed0 + i) for i, (N, m, r) in enumerate(shapes)]
+    cat = lambda k: np.concatenate([getattr(s, k).reshape(-1) for s in systems])
+    return systems, cat("A"), cat("B"), cat("C"), cat("b")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOLMIX)])
+def test_batch_uneven_systems(dm, prec, tol):
+    """Independent systems of uneven N, m, nrhs (the batching workload's shape
+    distribution, with N capped) factored and solved in the same launches;
+    every system compared with the oracle at the decomposition the tuner gives it."""
+    shapes = w.batch_shapes(24, 4, n_lo=5, n_hi=300, ms=(8, 16, 24, 32), r_lo=1, r_hi=6)
+    shapes += [(1, 4, 1), (2, 3, 2), (300, 40, 3)]
+    systems, A, B, C, b = _batch(shapes, 40)
+    Ns, ms, rs = zip(*shapes)
+    plan = dm.dm_plan_batch(Ns, ms, rs, prec)
+    try:
+        dm.dm_factor(plan, A, B, C)
+        x = np.zeros_like(b)
+        rel = dm.dm_solve(plan, b, x, count=len(shapes))
+    finally:
+        dm.dm_destroy(plan)
+    off = 0
+    for s, (N, m, r) in zip(systems, shapes):
+        xs = x[off:off + N * m * r].reshape(N, m, r)
+        off += N * m * r
+        P, lv, P2 = dm.dm_plan_tune(N, m, r)
+        check(xs, o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=P2 if P2 > 1 else None), tol)
+    assert max(rel) < 1e-13
+
+
+def test_batch_same_as_alone(dm):
+    """A system's x from a batch equals (within tolerance) its x solved alone."""
+    shapes = [(120, 16, 2), (37, 24, 1), (200, 8, 3)]
+    systems, A, B, C, b = _batch(shapes, 70)
+    plan = dm.dm_plan_batch(*zip(*shapes), "fp64")
+    try:
+        dm.dm_factor(plan, A, B, C)
+        x = np.zeros_like(b)
+        dm.dm_solve(plan, b, x, count=3)
+    finally:
+        dm.dm_destroy(plan)
+    off = 0
+    for s, (N, m, r) in zip(systems, shapes):
+        P, lv, _ = dm.dm_plan_tune(N, m, r)
+        xa, _, _ = solve(dm, s, P, lv)
+        check(x[off:off + N * m * r].reshape(N, m, r), xa, TOL64)
+        off += N * m * r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_repeats(dm, prec):
+    """Repeated factor + solve on one plan: the first call runs eagerly, the
+    second captures CUDA graphs, later calls replay them; all results agree
+    and the launch counter advances by the same amount each time."""
+    s = w.dominant_system(70, 24, 2, 21)
+    plan = dm.dm_plan(70, 24, 2, 6, 2, prec)
+    try:
+        xs, counts = [], []
+        for _ in range(4):
+            c0 = dm.dm_launch_count(plan)
+            dm.dm_factor(plan, s.A, s.B, s.C)
+            x = np.zeros_like(s.b)
+            dm.dm_solve(plan, s.b, x)
+            counts.append(dm.dm_launch_count(plan) - c0)
+            xs.append(x)
+    finally:
+        dm.dm_destroy(plan)
+    tol = TOL64 if prec == "fp64" else TOLMIX
+    ref = o.dm(s.A, s.B, s.C, s.b, 6, levels=2, P2=dm.dm_plan_tune(70, 24, 2, 6, 2)[2])
+    for x in xs:
+        check(x, ref, tol)
+    assert len(set(counts)) == 1 and counts[0] > 0
