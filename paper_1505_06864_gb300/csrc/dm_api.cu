@@ -18,6 +18,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dm.h"
@@ -48,8 +49,9 @@ int set_error(int code, const char* fmt, ...) {
 
 // ---------------------------------------------------------------------------
 // Level construction
-int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors) {
+int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tensor_mode) {
   f32 = fp32_factors;
+  tc_mode = fp32_factors ? tensor_mode : -1;
   nsys = (int)specs.size();
   spec = specs;
   blk0.assign(nsys, 0);
@@ -270,6 +272,7 @@ int Level::allocate() {
   DM_ALLOC(d_seps, std::max<size_t>(1, seps.size()) * sizeof(SepDesc));
   DM_ALLOC(d_sys, std::max<size_t>(1, sysd.size()) * sizeof(SysDesc));
   DM_ALLOC(status, std::max(1, nsys) * sizeof(int));
+  DM_ALLOC(d_err, sizeof(int));
 #undef DM_ALLOC
   if (!parts.empty()) DM_CUDA(cudaMemcpy(d_parts, parts.data(), parts.size() * sizeof(PartDesc), cudaMemcpyHostToDevice));
   if (!seps.empty()) DM_CUDA(cudaMemcpy(d_seps, seps.data(), seps.size() * sizeof(SepDesc), cudaMemcpyHostToDevice));
@@ -372,6 +375,25 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   // overlapping the next inversion, which depends only on the type-0 tiles.
   const bool split = aux && aux->st;
   cudaStream_t sb = split ? aux->st : st;
+  // block products on the tensor cores (float32 levels with a tensor mode) or CUDA cores
+  auto fwd = [&](int np, int t, cudaStream_t s, int lo, int hi) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.tc_mode >= 0) {
+        launch_fwd_factor_tc(L.tc_mode, L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, L.d_err, s, lo, hi);
+        return;
+      }
+    }
+    launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, s, lo, hi);
+  };
+  auto back = [&](int np, int s) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.tc_mode >= 0) {
+        launch_back_factor_tc(L.tc_mode, L.d_parts, np, s, L.max_m, Ac, ZL, ZR, L.d_err, st);
+        return;
+      }
+    }
+    launch_back_factor<T>(L.d_parts, np, s, L.max_m, Ac, ZL, ZR, st);
+  };
   if (split) {
     cudaEventRecord(aux->ev_main, st);
     cudaStreamWaitEvent(sb, aux->ev_main, 0);
@@ -387,13 +409,10 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
       c0.bytes *= L.fwd_chain_frac[t];
       c1.flops -= c0.flops;
       c1.bytes -= c0.bytes;
-      DM_LAUNCH(pf, st, K_FWD_FACTOR, c0, np,
-                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st, 0, 1));
-      DM_LAUNCH(pf, sb, K_FWD_FACTOR, c1, np,
-                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, sb, 1, 2));
+      DM_LAUNCH(pf, st, K_FWD_FACTOR, c0, np, fwd(np, t, st, 0, 1));
+      DM_LAUNCH(pf, sb, K_FWD_FACTOR, c1, np, fwd(np, t, sb, 1, 2));
     } else {
-      DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwd[t], np,
-                launch_fwd_factor<T>(L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, st));
+      DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwd[t], np, fwd(np, t, st, 0, 2));
     }
   }
   if (split) {
@@ -401,8 +420,7 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
     cudaStreamWaitEvent(st, aux->ev_aux, 0);
   }
   for (int s = 0; s + 1 < L.Lmax; ++s)
-    DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], L.active_back[s],
-              launch_back_factor<T>(L.d_parts, L.active_back[s], s, L.max_m, Ac, ZL, ZR, st));
+    DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], L.active_back[s], back(L.active_back[s], s));
   if (L.supp)
     DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
               launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
@@ -411,6 +429,7 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
 
 void factor_level(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   cudaMemsetAsync(L.status, 0x7f, std::max(1, L.nsys) * sizeof(int), st);
+  cudaMemsetAsync(L.d_err, 0, sizeof(int), st);
   if (L.f32)
     factor_level_t<float>(L, st, pf, aux);
   else
@@ -453,8 +472,11 @@ void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf
 // first failing block row per system (host check after a factorisation)
 static int check_status(Level& L, cudaStream_t st, int depth) {
   std::vector<int> h(std::max(1, L.nsys));
+  int herr = 0;
   DM_CUDA(cudaMemcpyAsync(h.data(), L.status, h.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DM_CUDA(cudaMemcpyAsync(&herr, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   DM_CUDA(cudaStreamSynchronize(st));
+  if (herr) return set_error(DM_ETIMEOUT, "a tensor-core wait expired at level %d", depth);
   for (int s = 0; s < L.nsys; ++s)
     if (h[s] != 0x7f7f7f7f)
       return set_error(DM_ESINGULAR, "singular pivot: level %d, system %d, block row %d (0-based)", depth, s,
@@ -553,7 +575,7 @@ int Plan::run(GraphCache& g, F&& body) {
 
 int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
-  int rc = top.build(specs, prec != DM_FP64);
+  int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
   DM_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
   stream = own_stream;
@@ -780,8 +802,8 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
   if (!out) return set_error(DM_EINVAL, "out is NULL");
   if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
     return set_error(DM_EINVAL, "unknown precision %d", precision);
-  if (precision == DM_TF32 || precision == DM_BF16X3)
-    return set_error(DM_EINVAL, "precision %d needs the tcgen05 kernels, not in this build", precision);
+  if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)
+    return set_error(DM_EINVAL, "tensor-core precisions support m <= %d", kMaxMTensor);
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, levels, &s);
   if (rc) return rc;
@@ -798,6 +820,8 @@ int dm_plan_batch(dm_plan_t* out, int count, const int* N, const int* m, const i
     return set_error(DM_EINVAL, "unknown precision %d", precision);
   std::vector<SysSpec> specs(count);
   for (int s = 0; s < count; ++s) {
+    if ((precision == DM_TF32 || precision == DM_BF16X3) && m[s] > kMaxMTensor)
+      return set_error(DM_EINVAL, "tensor-core precisions support m <= %d", kMaxMTensor);
     int rc = make_spec(N[s], m[s], nrhs[s], 0, 0, &specs[s]);
     if (rc) return rc;
   }

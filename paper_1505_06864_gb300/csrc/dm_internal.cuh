@@ -82,6 +82,15 @@ void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_
 void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
                        double* x, double* nrm, cudaStream_t st);
 
+// tcgen05 block products of the float32 factor sweeps (dm_tc.cu); mode 0 =
+// TF32, 1 = split bf16 (three products).  m <= 256.
+void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const double* A,
+                          const double* B, const double* C, float* G, float* Acal, float* ZL, float* ZR,
+                          int* errflag, cudaStream_t st, int type_lo, int type_hi);
+void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, int max_m, const float* Acal,
+                           float* ZL, float* ZR, int* errflag, cudaStream_t st);
+constexpr int kMaxMTensor = 256;
+
 constexpr int kMaxM = 512;
 constexpr int kMaxR = 64;
 

@@ -65,6 +65,8 @@ struct SysSpec {
 // subsystems, with the float64 supplementary systems one level down.
 struct Level {
   bool f32 = false;  // factors stored and multiplied in float32 (else float64)
+  int tc_mode = -1;   // float32 factors: -1 CUDA cores, 0 tcgen05 TF32, 1 tcgen05 split bf16
+  int* d_err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0
@@ -88,7 +90,7 @@ struct Level {
   std::unique_ptr<Level> supp;
   std::vector<void*> owned;
 
-  int build(const std::vector<SysSpec>& specs, bool fp32_factors);
+  int build(const std::vector<SysSpec>& specs, bool fp32_factors, int tensor_mode = -1);
   void compute_costs();
   size_t bytes_needed() const;
   int allocate();

@@ -1,0 +1,538 @@
+// Block products of the mixed-precision factor sweeps on the 5th-generation
+// tensor cores (tcgen05, sm_103a).
+//
+// The sweeps' m x m x m products (Acal_t = G_t C_t, the next Schur block
+// D_{t+1} = B_{t+1} - A_{t+1} Acal_t, the left spike G_t (-A_t Bcal_{t-1}),
+// and the spike back-sweeps; Section 3 applied to Eq. e231) are computed in
+// m x 64 output panels, one CTA of 128 threads per panel:
+//
+//   * the left operand (an m x m block, float64 or float32 in global memory)
+//     streams through shared memory in K-slabs of one 128-byte swizzle atom,
+//     converted to TF32 (DM_TF32) or split into bf16 hi + lo parts
+//     (DM_BF16X3), double-buffered so that the loads of slab s+1 overlap the
+//     MMAs of slab s;
+//   * the right operand (the m x 64 panel) is held transposed (K-major) in
+//     shared memory for the whole K;
+//   * one thread issues tcgen05.mma (M = 128 rows per tile, N = 64, K = 8 for
+//     TF32 / 16 for bf16) into a float32 accumulator in tensor memory and
+//     commits to an mbarrier; DM_BF16X3 issues hi*hi + hi*lo + lo*hi;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = rows of the tile) and either writes the result to
+//     global memory or stages it, transposed, as the next product's right
+//     operand (the chain Acal_t -> D_{t+1} stays in one CTA).
+//
+// Shared-memory operand layout: canonical K-major, 128-byte swizzle: rows of
+// 128 bytes, 8-row atoms of 1024 bytes (stride-byte-offset 1024), the 16-byte
+// chunk index XOR-ed with the row index within the atom.  Every wait on an
+// mbarrier is bounded; on expiry the kernel records an error flag, stops
+// issuing, frees its tensor memory and returns.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "dm_internal.cuh"
+
+namespace dm {
+namespace tc {
+
+constexpr int kThreads = 128;
+constexpr int NP = 64;          // panel width = MMA N
+constexpr int MT = 128;         // MMA M (rows per tile)
+constexpr int kMaxTiles = 2;    // m <= 256
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One full warp: allocate `ncols` TMEM columns, address written to *slot.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// K-major, 128-byte swizzle shared-memory matrix descriptor.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8-row atoms of 1024 bytes
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: float32 accumulate, K-major A and B, M x N.
+// fmt: 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if (MODE == 0) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive float32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+
+// byte offset of (row, byte-in-row kb) inside a K-major SW128 tile
+__device__ __forceinline__ uint32_t sw128_off(int row, int kb) {
+  const int chunk = kb >> 4;
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((chunk ^ (row & 7)) & 7) << 4) + (kb & 15));
+}
+
+// ---------------------------------------------------------------- operand staging
+// Element size in shared memory and K elements per 128-byte atom.
+template <int MODE>
+struct Fmt {
+  static constexpr int esz = MODE == 0 ? 4 : 2;
+  static constexpr int katom = 128 / esz;   // 32 (tf32) or 64 (bf16)
+  static constexpr int kstep = MODE == 0 ? 8 : 16;
+  static constexpr int parts = MODE == 0 ? 1 : 2;  // hi (+ lo)
+};
+
+// Store value v at (row, k) of an operand whose K-slabs are `slab_bytes`
+// apart (k = slab * katom + kk); part 0 = TF32 / bf16 hi, part 1 = bf16 lo
+// at `lo_off` bytes further.
+template <int MODE>
+__device__ __forceinline__ void put(uint8_t* base, int slab_bytes, int lo_off, int row, int k, float v) {
+  constexpr int KA = Fmt<MODE>::katom;
+  const int s = k / KA, kk = k - s * KA;
+  uint8_t* p = base + (size_t)s * slab_bytes;
+  if (MODE == 0) {
+    *reinterpret_cast<float*>(p + sw128_off(row, kk * 4)) = to_tf32(v);
+  } else {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    *reinterpret_cast<__nv_bfloat16*>(p + sw128_off(row, kk * 2)) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(p + lo_off + sw128_off(row, kk * 2)) = lo;
+  }
+}
+
+// Left-operand K-slab `slab` of the m x m row-major block L (rows padded to
+// MT * tiles, columns past m zero) into buffer `dst` (tile t at t * tile_bytes).
+template <int MODE, typename TL>
+__device__ __forceinline__ void stage_left(uint8_t* dst, const TL* __restrict__ L, int m, int slab, int tiles,
+                                           int tile_bytes, int lo_off) {
+  constexpr int KA = Fmt<MODE>::katom;
+  const int k0 = slab * KA;
+  const int rows = tiles * MT;
+  for (int e = threadIdx.x; e < rows * KA; e += kThreads) {
+    const int r = e / KA, kk = e - r * KA, k = k0 + kk;
+    const float v = (r < m && k < m) ? (float)L[(long long)r * m + k] : 0.f;
+    put<MODE>(dst + (r / MT) * tile_bytes, 0, lo_off, r % MT, kk, v);
+  }
+}
+
+// Right operand: the m x NP panel R[k][c0 + n] (row stride ld, columns past
+// `cols` zero, scaled by `sc`) stored transposed: row n, K index k.
+template <int MODE, typename TR>
+__device__ __forceinline__ void stage_right(uint8_t* dst, int slab_bytes, int lo_off, const TR* __restrict__ R,
+                                            int m, int ld, int c0, int cols, float sc) {
+  constexpr int KA = Fmt<MODE>::katom;
+  const int kpad = ((m + KA - 1) / KA) * KA;
+  for (int e = threadIdx.x; e < kpad * NP; e += kThreads) {
+    const int k = e / NP, n = e - k * NP;
+    const float v = (k < m && c0 + n < cols) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
+    put<MODE>(dst, slab_bytes, lo_off, n, k, v);
+  }
+}
+
+// Shared-memory plan of a CTA (bytes), m <= 256.
+template <int MODE>
+struct Smem {
+  static constexpr int KA = Fmt<MODE>::katom;
+  static constexpr int P = Fmt<MODE>::parts;
+  static constexpr int tile_bytes = MT * 128 * P;     // one M-tile of one left K-slab (hi [+ lo])
+  static constexpr int left_lo = MT * 128;            // lo part offset inside a tile
+  static constexpr int lbuf_bytes = kMaxTiles * tile_bytes;
+  static constexpr int rslab_bytes = NP * 128 * P;    // one K-slab of the right panel (hi [+ lo])
+  static constexpr int right_lo = NP * 128;
+  static constexpr int nslabs_max = 256 / KA;
+  static constexpr int right_bytes = nslabs_max * rslab_bytes;
+  static constexpr int total = 1024 /*align*/ + 2 * lbuf_bytes + right_bytes + 64;
+};
+
+// acc(TMEM) = L (m x m) * Rpanel (K-major in `right`): streams L's K-slabs
+// through the two left buffers.  `ph` tracks the two mbarriers' phases.
+// Returns false if a wait expired.
+template <int MODE, typename TL>
+__device__ bool product(const TL* __restrict__ L, int m, int tiles, uint8_t* lbuf0, uint8_t* right,
+                        uint64_t* bars, uint32_t (&ph)[2], uint32_t tmem, bool elect) {
+  using S = Smem<MODE>;
+  constexpr int KA = Fmt<MODE>::katom;
+  constexpr int KS = Fmt<MODE>::kstep;
+  constexpr uint32_t idesc = make_idesc(MODE == 0 ? 2u : 1u, MT, NP);
+  const int nslab = (m + KA - 1) / KA;
+  bool ok = true;
+  for (int s = 0; s < nslab; ++s) {
+    const int b = s & 1;
+    uint8_t* lb = lbuf0 + b * S::lbuf_bytes;
+    if (s >= 2) {  // the MMAs of slab s-2 read this buffer
+      if (!mbar_wait(&bars[b], ph[b])) ok = false;
+      ph[b] ^= 1u;
+    }
+    stage_left<MODE, TL>(lb, L, m, s, tiles, S::tile_bytes, S::left_lo);
+    fence_async_shared();
+    if (!__syncthreads_and(ok)) return false;
+    tc_fence_after();
+    if (elect) {
+      for (int t = 0; t < tiles; ++t) {
+        const uint32_t dt = tmem + (uint32_t)(t * NP);
+        const uint32_t la = smem_u32(lb + t * S::tile_bytes);
+        const uint32_t ra = smem_u32(right + s * S::rslab_bytes);
+        for (int j = 0; j < KA / KS; ++j) {
+          const uint32_t kb = (uint32_t)(j * KS * Fmt<MODE>::esz);
+          const uint64_t ad = sw128_desc(la + kb), bd = sw128_desc(ra + kb);
+          const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+          mma<MODE>(dt, ad, bd, idesc, acc);
+          if (MODE == 1) {
+            const uint64_t bl = sw128_desc(ra + S::right_lo + kb);
+            const uint64_t al = sw128_desc(la + S::left_lo + kb);
+            mma<MODE>(dt, ad, bl, idesc, 1u);
+            mma<MODE>(dt, al, bd, idesc, 1u);
+          }
+        }
+      }
+      mma_commit(&bars[b]);
+    }
+    __syncwarp();
+  }
+  // drain: wait for the last one or two commits
+  for (int s = (nslab >= 2 ? nslab - 2 : 0); s < nslab; ++s) {
+    const int b = s & 1;
+    if (!mbar_wait(&bars[b], ph[b])) ok = false;
+    ph[b] ^= 1u;
+  }
+  tc_fence_after();
+  return __syncthreads_and(ok);
+}
+
+// Epilogue: f(row, col, value) for every (row < m, col < NP) of the tiles' accumulators.
+template <typename F>
+__device__ __forceinline__ void drain_acc(uint32_t tmem, int tiles, int m, F&& f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = 0; t < tiles; ++t) {
+    const int row = t * MT + warp * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < NP; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NP + c), v);
+      if (row < m) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) f(row, c + i, v[i]);
+      }
+    }
+  }
+}
+
+struct TcState {
+  uint64_t bars[2];
+  uint32_t tmem;
+  int err;
+};
+
+template <int MODE>
+__device__ __forceinline__ uint8_t* carve(uint8_t* raw, uint8_t** lbuf, uint8_t** right) {
+  using S = Smem<MODE>;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  *lbuf = base;
+  *right = base + 2 * S::lbuf_bytes;
+  return base;
+}
+
+__device__ __forceinline__ void tc_setup(TcState* st, int ncols) {
+  if (threadIdx.x < 32) tmem_alloc(&st->tmem, (uint32_t)ncols);
+  if (threadIdx.x == 0) {
+    mbar_init(&st->bars[0], 1);
+    mbar_init(&st->bars[1], 1);
+    st->err = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void tc_teardown(TcState* st, int ncols, int* errflag) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(st->tmem, (uint32_t)ncols);
+  if (threadIdx.x == 0 && st->err && errflag) atomicExch(errflag, 1);
+}
+
+__device__ __forceinline__ int tmem_cols(int tiles) {
+  const int need = tiles * NP;
+  return need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : 256));
+}
+
+// ---------------------------------------------------------------- kernels
+// Forward factor step t, tile types as in the SIMT kernel:
+//   0: Acal_t[:, J] = G_t C_t[:, J]; D_{t+1}[:, J] = B_{t+1}[:, J] - A_{t+1} Acal_t[:, J]
+//      (last row with a right spike: ZR_t[:, J] = G_t C_t[:, J])
+//   1: left spike: Bcal_t[:, J] = G_t A_first[:, J] (t = 0) or G_t (-A_t Bcal_{t-1}[:, J])
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __restrict__ parts, int t, int tiles_n,
+                                                            int type_lo, const double* __restrict__ A,
+                                                            const double* __restrict__ B,
+                                                            const double* __restrict__ C, float* __restrict__ G,
+                                                            float* __restrict__ Acal, float* __restrict__ ZL,
+                                                            float* __restrict__ ZR, int* __restrict__ errflag) {
+  using S = Smem<MODE>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ TcState st;
+  const PartDesc p = parts[blockIdx.y];
+  if (t >= p.L) return;
+  const int m = p.m;
+  const int tb = blockIdx.x / tiles_n, type = type_lo + tb, c0 = (blockIdx.x - tb * tiles_n) * NP;
+  if (c0 >= m) return;
+  const bool last = (t == p.L - 1);
+  if (type == 0 && last && !(p.flags & HAS_RIGHT)) return;
+  if (type == 1 && !(p.flags & HAS_LEFT)) return;
+  uint8_t *lbuf, *right;
+  carve<MODE>(smem_raw, &lbuf, &right);
+  const int tiles = (m + MT - 1) / MT;
+  const int ncols = tmem_cols(tiles);
+  tc_setup(&st, ncols);
+  uint32_t ph[2] = {0u, 0u};
+  const bool elect = threadIdx.x == 0;
+  const long long mm = (long long)m * m;
+  const long long o = p.blk + (long long)t * mm;
+  bool ok = true;
+  if (type == 0) {
+    stage_right<MODE, double>(right, S::rslab_bytes, S::right_lo, C + o, m, m, c0, m, 1.f);
+    fence_async_shared();
+    __syncthreads();
+    ok = product<MODE, float>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    if (ok) {
+      float* dst = last ? ZR + o : Acal + o;
+      // result to global, and (not last) transposed into `right` for the next product
+      drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+        if (c0 + col < m) dst[(long long)row * m + c0 + col] = v;
+      });
+      if (!last) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+          put<MODE>(right, S::rslab_bytes, S::right_lo, col, row, c0 + col < m ? v : 0.f);
+        });
+        fence_async_shared();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        ok = product<MODE, double>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+        if (ok) {
+          const double* Bn = B + o + mm;
+          float* Dn = G + o + mm;
+          drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+            if (c0 + col < m) {
+              const long long e = (long long)row * m + c0 + col;
+              Dn[e] = (float)Bn[e] - v;
+            }
+          });
+        }
+      }
+    }
+  } else {
+    if (t == 0) {
+      stage_right<MODE, double>(right, S::rslab_bytes, S::right_lo, A + o, m, m, c0, m, 1.f);
+    } else {
+      stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, ZL + o - mm, m, m, c0, m, 1.f);
+      fence_async_shared();
+      __syncthreads();
+      ok = product<MODE, double>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+      if (ok) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+          put<MODE>(right, S::rslab_bytes, S::right_lo, col, row, c0 + col < m ? -v : 0.f);
+        });
+      }
+    }
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (ok) ok = product<MODE, float>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    if (ok) {
+      float* dst = ZL + o;
+      drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+        if (c0 + col < m) dst[(long long)row * m + c0 + col] = v;
+      });
+    }
+  }
+  if (!ok && threadIdx.x == 0) st.err = 1;
+  tc_teardown(&st, ncols, errflag);
+}
+
+// Backward factor step s, row t = L-2-s:  0: ZL_t -= Acal_t ZL_{t+1};  1: ZR_t = -Acal_t ZR_{t+1}.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __restrict__ parts, int s, int tiles_n,
+                                                             const float* __restrict__ Acal, float* __restrict__ ZL,
+                                                             float* __restrict__ ZR, int* __restrict__ errflag) {
+  using S = Smem<MODE>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ TcState st;
+  const PartDesc p = parts[blockIdx.y];
+  const int t = p.L - 2 - s;
+  if (t < 0) return;
+  const int m = p.m;
+  const int type = blockIdx.x / tiles_n, c0 = (blockIdx.x - type * tiles_n) * NP;
+  if (c0 >= m) return;
+  if (type == 0 && !(p.flags & HAS_LEFT)) return;
+  if (type == 1 && !(p.flags & HAS_RIGHT)) return;
+  uint8_t *lbuf, *right;
+  carve<MODE>(smem_raw, &lbuf, &right);
+  const int tiles = (m + MT - 1) / MT;
+  const int ncols = tmem_cols(tiles);
+  tc_setup(&st, ncols);
+  uint32_t ph[2] = {0u, 0u};
+  const long long mm = (long long)m * m;
+  const long long o = p.blk + (long long)t * mm;
+  float* Y = (type == 0 ? ZL : ZR) + o;
+  stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, Y + mm, m, m, c0, m, 1.f);
+  fence_async_shared();
+  __syncthreads();
+  bool ok = product<MODE, float>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0);
+  if (ok) {
+    const bool keep = (type == 0);
+    drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
+      if (c0 + col < m) {
+        const long long e = (long long)row * m + c0 + col;
+        Y[e] = (keep ? Y[e] : 0.f) - v;
+      }
+    });
+  }
+  if (!ok && threadIdx.x == 0) st.err = 1;
+  tc_teardown(&st, ncols, errflag);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- launchers
+namespace {
+template <typename K>
+void raise_smem_once(K kernel, int bytes, bool* done) {
+  if (!*done) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    *done = true;
+  }
+}
+bool g_set_fwd[2], g_set_back[2];
+}  // namespace
+
+void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const double* A,
+                          const double* B, const double* C, float* G, float* Acal, float* ZL, float* ZR,
+                          int* errflag, cudaStream_t st, int type_lo, int type_hi) {
+  if (nparts <= 0 || type_hi <= type_lo) return;
+  const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
+  const dim3 grid((type_hi - type_lo) * tiles_n, nparts);
+  if (mode == 0) {
+    const int bytes = tc::Smem<0>::total;
+    raise_smem_once(tc::k_fwd_factor_tc<0>, bytes, &g_set_fwd[0]);
+    tc::k_fwd_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
+                                                              errflag);
+  } else {
+    const int bytes = tc::Smem<1>::total;
+    raise_smem_once(tc::k_fwd_factor_tc<1>, bytes, &g_set_fwd[1]);
+    tc::k_fwd_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
+                                                              errflag);
+  }
+}
+
+void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, int max_m, const float* Acal,
+                           float* ZL, float* ZR, int* errflag, cudaStream_t st) {
+  if (nparts <= 0) return;
+  const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
+  const dim3 grid(2 * tiles_n, nparts);
+  if (mode == 0) {
+    const int bytes = tc::Smem<0>::total;
+    raise_smem_once(tc::k_back_factor_tc<0>, bytes, &g_set_back[0]);
+    tc::k_back_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag);
+  } else {
+    const int bytes = tc::Smem<1>::total;
+    raise_smem_once(tc::k_back_factor_tc<1>, bytes, &g_set_back[1]);
+    tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag);
+  }
+}
+
+int tc_smem_bytes(int mode) { return mode == 0 ? tc::Smem<0>::total : tc::Smem<1>::total; }
+
+}  // namespace dm
