@@ -347,7 +347,7 @@ def mixed_leg(dm, A, B, C, b, stream, x64):
     import torch
     out = {}
     x = torch.empty_like(b)
-    for name in ("fp32",):
+    for name in ("fp32", "tf32", "bf16x3"):
         plan = dm.dm_plan(N_, M_, R_, P_, LEV_, name)
         dm.dm_set_stream(plan, stream)
         dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x, allow_notconv=True))[1], reps=3)
