@@ -233,6 +233,7 @@ void Level::compute_costs() {
 size_t Level::bytes_needed() const {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   size_t b = 3 * nblk * sizeof(double);     // A, B, C
+  if (tc_mode >= 0) b += 3 * nblk * sizeof(float);
   b += 4 * nblk * es;                       // G, Acal, ZL, ZR
   b += nvec * es;                           // z
   b += 2 * nvec * sizeof(double);           // F, X
@@ -273,6 +274,11 @@ int Level::allocate() {
   DM_ALLOC(d_sys, std::max<size_t>(1, sysd.size()) * sizeof(SysDesc));
   DM_ALLOC(status, std::max(1, nsys) * sizeof(int));
   DM_ALLOC(d_err, sizeof(int));
+  if (tc_mode >= 0) {
+    DM_ALLOC(A32, nblk * sizeof(float));
+    DM_ALLOC(B32, nblk * sizeof(float));
+    DM_ALLOC(C32, nblk * sizeof(float));
+  }
 #undef DM_ALLOC
   if (!parts.empty()) DM_CUDA(cudaMemcpy(d_parts, parts.data(), parts.size() * sizeof(PartDesc), cudaMemcpyHostToDevice));
   if (!seps.empty()) DM_CUDA(cudaMemcpy(d_seps, seps.data(), seps.size() * sizeof(SepDesc), cudaMemcpyHostToDevice));
@@ -375,11 +381,17 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   // overlapping the next inversion, which depends only on the type-0 tiles.
   const bool split = aux && aux->st;
   cudaStream_t sb = split ? aux->st : st;
+  if (L.tc_mode >= 0) {
+    launch_to_f32(L.A, L.A32, L.nblk, st);
+    launch_to_f32(L.B, L.B32, L.nblk, st);
+    launch_to_f32(L.C, L.C32, L.nblk, st);
+  }
   // block products on the tensor cores (float32 levels with a tensor mode) or CUDA cores
   auto fwd = [&](int np, int t, cudaStream_t s, int lo, int hi) {
     if constexpr (std::is_same<T, float>::value) {
       if (L.tc_mode >= 0) {
-        launch_fwd_factor_tc(L.tc_mode, L.d_parts, np, t, L.max_m, L.A, L.B, L.C, G, Ac, ZL, ZR, L.d_err, s, lo, hi);
+        launch_fwd_factor_tc(L.tc_mode, L.d_parts, np, t, L.max_m, L.A32, L.B32, L.C32, G, Ac, ZL, ZR, L.d_err, s,
+                             lo, hi);
         return;
       }
     }

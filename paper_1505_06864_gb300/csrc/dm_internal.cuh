@@ -84,9 +84,10 @@ void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int ma
 
 // tcgen05 block products of the float32 factor sweeps (dm_tc.cu); mode 0 =
 // TF32, 1 = split bf16 (three products).  m <= 256.
-void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const double* A,
-                          const double* B, const double* C, float* G, float* Acal, float* ZL, float* ZR,
+void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const float* A,
+                          const float* B, const float* C, float* G, float* Acal, float* ZL, float* ZR,
                           int* errflag, cudaStream_t st, int type_lo, int type_hi);
+void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, int max_m, const float* Acal,
                            float* ZL, float* ZR, int* errflag, cudaStream_t st);
 constexpr int kMaxMTensor = 256;

@@ -67,6 +67,7 @@ struct Level {
   bool f32 = false;  // factors stored and multiplied in float32 (else float64)
   int tc_mode = -1;   // float32 factors: -1 CUDA cores, 0 tcgen05 TF32, 1 tcgen05 split bf16
   int* d_err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
+  float *A32 = nullptr, *B32 = nullptr, *C32 = nullptr;  // float32 copies streamed by the tensor-core sweeps
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0

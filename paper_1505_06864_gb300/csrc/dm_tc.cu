@@ -183,17 +183,64 @@ __device__ __forceinline__ void put(uint8_t* base, int slab_bytes, int lo_off, i
   }
 }
 
-// Left-operand K-slab `slab` of the m x m row-major block L (rows padded to
-// MT * tiles, columns past m zero) into buffer `dst` (tile t at t * tile_bytes).
-template <int MODE, typename TL>
-__device__ __forceinline__ void stage_left(uint8_t* dst, const TL* __restrict__ L, int m, int slab, int tiles,
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Left-operand K-slab `slab` of the m x m row-major float32 block L (rows
+// padded to MT * tiles, columns past m zero) into buffer `dst` (M-tile t at
+// t * tile_bytes).  TF32 with m % 4 == 0: 16-byte cp.async copies straight
+// into their swizzled chunks (the tensor core reads the float32 bits as TF32),
+// asynchronous -- the caller waits.  Otherwise: 4-wide vector loads, TF32
+// rounding or the bf16 hi/lo split in registers, stores to shared memory.
+template <int MODE>
+__device__ __forceinline__ void stage_left(uint8_t* dst, const float* __restrict__ L, int m, int slab, int tiles,
                                            int tile_bytes, int lo_off) {
   constexpr int KA = Fmt<MODE>::katom;
   const int k0 = slab * KA;
   const int rows = tiles * MT;
+  const bool vec = (m & 3) == 0 && (reinterpret_cast<uintptr_t>(L) & 15) == 0;
+  if (MODE == 0 && vec) {
+    for (int e = threadIdx.x; e < rows * (KA / 4); e += kThreads) {
+      const int r = e / (KA / 4), c = e - r * (KA / 4), k = k0 + 4 * c;
+      const bool ok = r < m && k < m;
+      const float* src = ok ? L + (long long)r * m + k : L;
+      cp_async16(smem_u32(dst + (r / MT) * tile_bytes + sw128_off(r % MT, c * 16)), src, ok ? 16u : 0u);
+    }
+    cp_commit();
+    return;
+  }
+  if (vec) {
+    constexpr int U = 4;  // independent vector loads in flight per thread
+    const int n4 = rows * (KA / 4);
+    for (int e0 = threadIdx.x; e0 < n4; e0 += U * kThreads) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kThreads;
+        const int r = e / (KA / 4), k = k0 + 4 * (e - r * (KA / 4));
+        v[u] = (e < n4 && r < m && k < m) ? *reinterpret_cast<const float4*>(L + (long long)r * m + k)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= n4) break;
+        const int r = e / (KA / 4), kk = 4 * (e - r * (KA / 4));
+        uint8_t* t = dst + (r / MT) * tile_bytes;
+        put<MODE>(t, 0, lo_off, r % MT, kk + 0, v[u].x);
+        put<MODE>(t, 0, lo_off, r % MT, kk + 1, v[u].y);
+        put<MODE>(t, 0, lo_off, r % MT, kk + 2, v[u].z);
+        put<MODE>(t, 0, lo_off, r % MT, kk + 3, v[u].w);
+      }
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < rows * KA; e += kThreads) {
     const int r = e / KA, kk = e - r * KA, k = k0 + kk;
-    const float v = (r < m && k < m) ? (float)L[(long long)r * m + k] : 0.f;
+    const float v = (r < m && k < m) ? L[(long long)r * m + k] : 0.f;
     put<MODE>(dst + (r / MT) * tile_bytes, 0, lo_off, r % MT, kk, v);
   }
 }
@@ -205,6 +252,19 @@ __device__ __forceinline__ void stage_right(uint8_t* dst, int slab_bytes, int lo
                                             int m, int ld, int c0, int cols, float sc) {
   constexpr int KA = Fmt<MODE>::katom;
   const int kpad = ((m + KA - 1) / KA) * KA;
+  if (sizeof(TR) == 4 && (ld & 3) == 0 && (c0 & 3) == 0 && (cols & 3) == 0 &&
+      (reinterpret_cast<uintptr_t>(R) & 15) == 0) {
+    for (int e = threadIdx.x; e < kpad * (NP / 4); e += kThreads) {
+      const int k = e / (NP / 4), n = 4 * (e - k * (NP / 4));
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < m && c0 + n < cols) v = *reinterpret_cast<const float4*>(R + (long long)k * ld + c0 + n);
+      put<MODE>(dst, slab_bytes, lo_off, n + 0, k, sc * v.x);
+      put<MODE>(dst, slab_bytes, lo_off, n + 1, k, sc * v.y);
+      put<MODE>(dst, slab_bytes, lo_off, n + 2, k, sc * v.z);
+      put<MODE>(dst, slab_bytes, lo_off, n + 3, k, sc * v.w);
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < kpad * NP; e += kThreads) {
     const int k = e / NP, n = e - k * NP;
     const float v = (k < m && c0 + n < cols) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
@@ -227,11 +287,12 @@ struct Smem {
   static constexpr int total = 1024 /*align*/ + 2 * lbuf_bytes + right_bytes + 64;
 };
 
-// acc(TMEM) = L (m x m) * Rpanel (K-major in `right`): streams L's K-slabs
-// through the two left buffers.  `ph` tracks the two mbarriers' phases.
-// Returns false if a wait expired.
-template <int MODE, typename TL>
-__device__ bool product(const TL* __restrict__ L, int m, int tiles, uint8_t* lbuf0, uint8_t* right,
+// acc(TMEM) = L (m x m, float32) * Rpanel (K-major in `right`).  L's K-slabs
+// stream through the two left buffers: slab s+1 is staged while the MMAs of
+// slab s run.  `ph` tracks the two mbarriers' phases.  Returns false if a
+// wait expired.
+template <int MODE>
+__device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* lbuf0, uint8_t* right,
                         uint64_t* bars, uint32_t (&ph)[2], uint32_t tmem, bool elect) {
   using S = Smem<MODE>;
   constexpr int KA = Fmt<MODE>::katom;
@@ -239,14 +300,11 @@ __device__ bool product(const TL* __restrict__ L, int m, int tiles, uint8_t* lbu
   constexpr uint32_t idesc = make_idesc(MODE == 0 ? 2u : 1u, MT, NP);
   const int nslab = (m + KA - 1) / KA;
   bool ok = true;
+  stage_left<MODE>(lbuf0, L, m, 0, tiles, S::tile_bytes, S::left_lo);
   for (int s = 0; s < nslab; ++s) {
     const int b = s & 1;
     uint8_t* lb = lbuf0 + b * S::lbuf_bytes;
-    if (s >= 2) {  // the MMAs of slab s-2 read this buffer
-      if (!mbar_wait(&bars[b], ph[b])) ok = false;
-      ph[b] ^= 1u;
-    }
-    stage_left<MODE, TL>(lb, L, m, s, tiles, S::tile_bytes, S::left_lo);
+    cp_wait_all();  // slab s (if it was copied asynchronously) has landed
     fence_async_shared();
     if (!__syncthreads_and(ok)) return false;
     tc_fence_after();
@@ -270,7 +328,14 @@ __device__ bool product(const TL* __restrict__ L, int m, int tiles, uint8_t* lbu
       }
       mma_commit(&bars[b]);
     }
-    __syncwarp();
+    if (s + 1 < nslab) {
+      const int nb = (s + 1) & 1;
+      if (s + 1 >= 2) {  // the MMAs of slab s-1 read buffer nb
+        if (!mbar_wait(&bars[nb], ph[nb])) ok = false;
+        ph[nb] ^= 1u;
+      }
+      stage_left<MODE>(lbuf0 + nb * S::lbuf_bytes, L, m, s + 1, tiles, S::tile_bytes, S::left_lo);
+    }
   }
   // drain: wait for the last one or two commits
   for (int s = (nslab >= 2 ? nslab - 2 : 0); s < nslab; ++s) {
@@ -348,9 +413,9 @@ __device__ __forceinline__ int tmem_cols(int tiles) {
 //   1: left spike: Bcal_t[:, J] = G_t A_first[:, J] (t = 0) or G_t (-A_t Bcal_{t-1}[:, J])
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __restrict__ parts, int t, int tiles_n,
-                                                            int type_lo, const double* __restrict__ A,
-                                                            const double* __restrict__ B,
-                                                            const double* __restrict__ C, float* __restrict__ G,
+                                                            int type_lo, const float* __restrict__ A,
+                                                            const float* __restrict__ B,
+                                                            const float* __restrict__ C, float* __restrict__ G,
                                                             float* __restrict__ Acal, float* __restrict__ ZL,
                                                             float* __restrict__ ZR, int* __restrict__ errflag) {
   using S = Smem<MODE>;
@@ -375,10 +440,10 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
   const long long o = p.blk + (long long)t * mm;
   bool ok = true;
   if (type == 0) {
-    stage_right<MODE, double>(right, S::rslab_bytes, S::right_lo, C + o, m, m, c0, m, 1.f);
+    stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, C + o, m, m, c0, m, 1.f);
     fence_async_shared();
     __syncthreads();
-    ok = product<MODE, float>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
     if (ok) {
       float* dst = last ? ZR + o : Acal + o;
       // result to global, and (not last) transposed into `right` for the next product
@@ -396,14 +461,14 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        ok = product<MODE, double>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+        ok = product<MODE>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
         if (ok) {
-          const double* Bn = B + o + mm;
+          const float* Bn = B + o + mm;
           float* Dn = G + o + mm;
           drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
             if (c0 + col < m) {
               const long long e = (long long)row * m + c0 + col;
-              Dn[e] = (float)Bn[e] - v;
+              Dn[e] = Bn[e] - v;
             }
           });
         }
@@ -411,12 +476,12 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
     }
   } else {
     if (t == 0) {
-      stage_right<MODE, double>(right, S::rslab_bytes, S::right_lo, A + o, m, m, c0, m, 1.f);
+      stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, A + o, m, m, c0, m, 1.f);
     } else {
       stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, ZL + o - mm, m, m, c0, m, 1.f);
       fence_async_shared();
       __syncthreads();
-      ok = product<MODE, double>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+      ok = product<MODE>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
       if (ok) {
         tc_fence_before();
         __syncthreads();
@@ -430,7 +495,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (ok) ok = product<MODE, float>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    if (ok) ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
     if (ok) {
       float* dst = ZL + o;
       drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -470,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __r
   stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, Y + mm, m, m, c0, m, 1.f);
   fence_async_shared();
   __syncthreads();
-  bool ok = product<MODE, float>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0);
+  bool ok = product<MODE>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0);
   if (ok) {
     const bool keep = (type == 0);
     drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -498,8 +563,8 @@ void raise_smem_once(K kernel, int bytes, bool* done) {
 bool g_set_fwd[2], g_set_back[2];
 }  // namespace
 
-void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const double* A,
-                          const double* B, const double* C, float* G, float* Acal, float* ZL, float* ZR,
+void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const float* A,
+                          const float* B, const float* C, float* G, float* Acal, float* ZL, float* ZR,
                           int* errflag, cudaStream_t st, int type_lo, int type_hi) {
   if (nparts <= 0 || type_hi <= type_lo) return;
   const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
@@ -531,6 +596,24 @@ void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, i
     raise_smem_once(tc::k_back_factor_tc<1>, bytes, &g_set_back[1]);
     tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag);
   }
+}
+
+namespace {
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; 2 * i + 1 < n; i += stride) {
+    const double2 v = reinterpret_cast<const double2*>(src)[i];
+    reinterpret_cast<float2*>(dst)[i] = make_float2((float)v.x, (float)v.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) dst[n - 1] = (float)src[n - 1];
+}
+}  // namespace
+
+// float32 copy of a float64 array (the blocks the tensor-core sweeps stream).
+void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  int sms = 152;
+  k_to_f32<<<sms * 4, 256, 0, st>>>(src, dst, n);
 }
 
 int tc_smem_bytes(int mode) { return mode == 0 ? tc::Smem<0>::total : tc::Smem<1>::total; }
