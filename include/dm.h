@@ -114,6 +114,31 @@ int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C)
  * relres_out (may be NULL) receives max over columns of ||b - T x||/||b||. */
 int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out);
 
+/* Continuous batching.  dm_submit queues a solve of b on the plan's resident
+ * factors; dm_submit_system queues a factor (of A, B, C) followed by a solve.
+ * Both return at once with a ticket.  A process-wide server runs the queued
+ * requests on `slots` worker streams (default 8, set by dm_serve_slots before
+ * the first submit): a worker takes the oldest request whose plan has nothing
+ * in flight, so requests on different plans run concurrently on the device
+ * and new requests are admitted as slots free up; requests on one plan run in
+ * submission order.  b, x (and A, B, C) must stay valid and unchanged until
+ * dm_poll reports completion, and the plan must not be used directly
+ * meanwhile.  DM_EAGAIN if the queue is full.  dm_destroy waits for a plan's
+ * queued requests.  (Device memory is admitted at dm_plan, which refuses a
+ * plan that does not fit in the free device memory with DM_ENOMEM.) */
+int dm_submit(dm_plan_t plan, const double* b, double* x, uint64_t* ticket);
+int dm_submit_system(dm_plan_t plan, const double* A, const double* B, const double* C,
+                     const double* b, double* x, uint64_t* ticket);
+
+/* Poll a ticket: *status = DM_PENDING while queued or running, else the
+ * request's final status (DM_OK or an error code); relres_out (may be NULL)
+ * receives its relative residual.  A finished ticket is forgotten after the
+ * poll that reports it.  DM_EINVAL for an unknown ticket. */
+int dm_poll(uint64_t ticket, int* status, double* relres_out);
+
+/* Number of serving worker streams (1..64); only before the first submit. */
+int dm_serve_slots(int slots);
+
 /* The decomposition dm_plan would choose for P = 0 / levels = 0 (the tuner's
  * seed: P from Eq. (MAXSpeedP), recursion from the P >= 21 condition after
  * Eq. (SuppMatrM), P2 from Eq. (SuppMatrM)).  Host only: allocates nothing and

@@ -589,6 +589,17 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
   int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
+  {
+    // admission: refuse cleanly, before allocating anything, when the device
+    // lacks the plan's footprint plus a reserve
+    size_t free_b = 0, total_b = 0;
+    DM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t need = top.bytes_needed() + 2 * top.nvec * sizeof(double);
+    const size_t reserve = std::min<size_t>(total_b / 64, size_t(1) << 30);
+    if (need + reserve > free_b)
+      return set_error(DM_ENOMEM, "admission refused: plan needs %zu bytes, %zu free (reserve %zu)", need, free_b,
+                       reserve);
+  }
   DM_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
   stream = own_stream;
   DM_CUDA(cudaStreamCreateWithFlags(&aux.st, cudaStreamNonBlocking));
@@ -802,10 +813,6 @@ int make_spec(int N, int m, int r, int P, int levels, SysSpec* out) {
 // extern "C" entry points
 using namespace dm;
 
-struct dm_plan_s {
-  Plan plan;
-};
-
 extern "C" {
 
 const char* dm_last_error(void) { return g_last_error.c_str(); }
@@ -928,6 +935,10 @@ int dm_profile(dm_plan_t plan, int enable, dm_profile_entry* out, int max_entrie
 
 long long dm_launch_count(dm_plan_t plan) { return plan ? plan->plan.prof.launches : -1; }
 
-void dm_destroy(dm_plan_t plan) { delete plan; }
+void dm_destroy(dm_plan_t plan) {
+  if (!plan) return;
+  serve_drain(plan);  // queued or running serving requests finish first
+  delete plan;
+}
 
 }  // extern "C"

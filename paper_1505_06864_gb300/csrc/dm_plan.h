@@ -147,4 +147,11 @@ void level_flops(const Level& L, double* ffac, double* fsol);
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
+void serve_drain(struct dm_plan_s* plan);
+
 }  // namespace dm
+
+// The opaque handle of the C ABI.
+struct dm_plan_s {
+  dm::Plan plan;
+};

@@ -72,6 +72,10 @@ def lib():
             "dm_profile": (I, [P, I, ctypes.POINTER(dm_profile_entry), I, ctypes.POINTER(I)]),
             "dm_launch_count": (ctypes.c_longlong, [P]),
             "dm_solve_noalloc": (I, [I, I, I, I, P, P, P, P, P, P]),
+            "dm_submit": (I, [P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
+            "dm_submit_system": (I, [P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
+            "dm_poll": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "dm_serve_slots": (I, [I]),
             "dm_destroy": (V, [P]),
             "dm_last_error": (ctypes.c_char_p, []),
         }
@@ -184,6 +188,31 @@ def dm_solve_noalloc(N, m, nrhs, P, A, B, C, b, x, stream=None):
     h = getattr(stream, "cuda_stream", stream)
     return _check(lib().dm_solve_noalloc(int(N), int(m), int(nrhs), int(P), _ptr(A), _ptr(B), _ptr(C),
                                          _ptr(b), _ptr(x, True), ctypes.c_void_p(h) if h else None))
+
+
+def dm_submit(plan, b, x):
+    """Queue a solve of b on the plan's resident factors; returns a ticket."""
+    t = ctypes.c_uint64(0)
+    _check(lib().dm_submit(plan, _ptr(b), _ptr(x, True), ctypes.byref(t)))
+    return t.value
+
+
+def dm_submit_system(plan, A, B, C, b, x):
+    """Queue a factor of (A, B, C) and a solve of b; returns a ticket."""
+    t = ctypes.c_uint64(0)
+    _check(lib().dm_submit_system(plan, _ptr(A), _ptr(B), _ptr(C), _ptr(b), _ptr(x, True), ctypes.byref(t)))
+    return t.value
+
+
+def dm_poll(ticket):
+    """(status, relres): status DM_PENDING while the request runs."""
+    st, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().dm_poll(ctypes.c_uint64(ticket), ctypes.byref(st), ctypes.byref(rel)))
+    return st.value, rel.value
+
+
+def dm_serve_slots(slots):
+    return _check(lib().dm_serve_slots(int(slots)))
 
 
 def dm_destroy(plan):
