@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--N", type=int, default=2048, help="block rows (smaller cases for profiler captures)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"],
                     help="factor precision of the timed path (mixed ones refine in float64)")
+    ap.add_argument("--workload", default="pde", choices=["pde", "precision", "batch", "serve"],
+                    help="pde: the benchmark line (default); precision / batch / serve: the "
+                         "conditioned-block, batched and served workloads, one JSON line each")
+    ap.add_argument("--seconds", type=float, default=2.0, help="serve: length of the arrival stream")
     return ap.parse_args()
 
 
@@ -164,6 +168,8 @@ def main():
     N_ = args.N
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "pde":
+        return {"precision": run_precision, "batch": run_batch, "serve": run_serve}[args.workload](args)
     import torch
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -365,6 +371,208 @@ def mixed_leg(dm, A, B, C, b, stream, x64):
                      "kernels_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
         dm.dm_destroy(plan)
     return out
+
+
+# ---------------------------------------------------------------- other workloads
+def _timed_steps(dm, plan, A, B, C, b, x, steps, warmup, stream, mixed):
+    import torch
+    for _ in range(warmup):
+        dm.dm_factor(plan, A, B, C)
+        dm.dm_solve(plan, b, x, allow_notconv=mixed, count=dm.dm_plan_query(plan)["count"])
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(steps):
+        dm.dm_factor(plan, A, B, C)
+        rel = dm.dm_solve(plan, b, x, allow_notconv=mixed, count=dm.dm_plan_query(plan)["count"])
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / steps, rel
+
+
+def run_precision(args):
+    """Conditioned dense blocks: N=4096, m=128, cond(B_i)=1e4, 8 right-hand
+    sides; float64 DM against float32 / TF32 / split-bf16 factors refined in
+    float64 (tolerance 1e-12 on the refinement step)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_06864_gb300 import dm, workloads as w
+    N, m, r = 4096, 128, 8
+    s = w.conditioned_system(N, m, r, 3, cond=1e4)
+    dev = torch.device("cuda", 0)
+    A, B, C, b = (torch.from_numpy(v).to(dev) for v in (s.A, s.B, s.C, s.b))
+    x = torch.empty_like(b)
+    stream = torch.cuda.Stream()
+    P, lv, P2 = dm.dm_plan_tune(N, m, r)
+    out, x64 = {}, None
+    for prec in ("fp64", "fp32", "tf32", "bf16x3"):
+        plan = dm.dm_plan(N, m, r, P, lv, prec)
+        dm.dm_set_stream(plan, stream)
+        mixed = prec != "fp64"
+        ms, rel = _timed_steps(dm, plan, A, B, C, b, x, args.steps, max(3, args.warmup), stream, mixed)
+        q = dm.dm_plan_query(plan)
+        xh = x.cpu().numpy()
+        if prec == "fp64":
+            x64 = xh
+        out[prec] = {"systems_per_s": 1e3 / ms, "ms": ms, "iters": q["last_iters"], "relres": rel,
+                     "last_correction": q["last_correction"], "converged": (not mixed) or q["last_correction"] <= 1e-12,
+                     "rel_err_vs_xtrue": rel_err(xh, s.x_true), "rel_err_vs_fp64_dm": rel_err(xh, x64),
+                     "tflops": (q["factor_flops"] + q["solve_flops"] * q["last_iters"]) / (ms / 1e3) / 1e12}
+        dm.dm_destroy(plan)
+    ok = {k: v for k, v in out.items() if k != "fp64" and v["converged"] and v["rel_err_vs_fp64_dm"] <= 1e-10}
+    best = max(ok, key=lambda k: ok[k]["systems_per_s"]) if ok else "fp64"
+    line = {"metric": "solved systems/s", "workload": "precision", "value": out[best]["systems_per_s"],
+            "unit": "systems/s", "best_precision": best, "n_gpus": 1, "steps": args.steps,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"conditioned dense blocks N={N} m={m} nrhs={r} cond(B_i)=1e4 seed=3",
+                       "P": P, "levels": lv, "P2": P2}, "results": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """512 independent systems, N ~ U{32..2048}, m ~ U{32,64,96,128},
+    nrhs ~ U{1..16}, dominant generator drawn in device memory; one batch plan,
+    inputs borrowed in place; parity on sampled systems against the oracle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_06864_gb300 import dm, workloads as w
+    from oracle import dm_oracle as o
+    count = args.N if args.N != 2048 else 512
+    shapes = w.batch_shapes(count, 4)
+    Ns, ms_, rs = zip(*shapes)
+    nblk = sum(n * m * m for n, m, _ in shapes)
+    nvec = sum(n * m * r for n, m, r in shapes)
+    dev = torch.device("cuda", 0)
+    A = torch.empty(nblk, dtype=torch.float64, device=dev)
+    B = torch.empty_like(A)
+    C = torch.empty_like(A)
+    b = torch.empty(nvec, dtype=torch.float64, device=dev)
+    ob, ov = [], []
+    pb = pv = 0
+    for i, (n, m, r) in enumerate(shapes):
+        a_, b_, c_, rhs, _ = w.dominant_system_t(n, m, r, 4000 + i, device=dev)
+        A[pb:pb + n * m * m] = a_.reshape(-1)
+        B[pb:pb + n * m * m] = b_.reshape(-1)
+        C[pb:pb + n * m * m] = c_.reshape(-1)
+        b[pv:pv + n * m * r] = rhs.reshape(-1)
+        ob.append(pb)
+        ov.append(pv)
+        pb += n * m * m
+        pv += n * m * r
+        del a_, b_, c_, rhs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    x = torch.empty_like(b)
+    stream = torch.cuda.Stream()
+    out = {}
+    picks = [0, count - 1, int(np.argmax(Ns)), count // 2]
+    for prec in ("bf16x3", "fp64"):
+        try:
+            plan = dm.dm_plan_batch(Ns, ms_, rs, prec)
+        except dm.DMError as e:
+            out[prec] = {"skipped": str(e)}
+            continue
+        dm.dm_set_borrow_inputs(plan)
+        dm.dm_set_stream(plan, stream)
+        mixed = prec != "fp64"
+        ms, rel = _timed_steps(dm, plan, A, B, C, b, x, max(1, args.steps // 3), 3, stream, mixed)
+        q = dm.dm_plan_query(plan)
+        errs = []
+        for i in picks:
+            n, m, r = shapes[i]
+            sl = lambda t, o0, k: t[o0:o0 + k].cpu().numpy()
+            Ai, Bi, Ci = (sl(t, ob[i], n * m * m).reshape(n, m, m) for t in (A, B, C))
+            bi = sl(b, ov[i], n * m * r).reshape(n, m, r)
+            xi = sl(x, ov[i], n * m * r).reshape(n, m, r)
+            P, lv, P2 = dm.dm_plan_tune(n, m, r)
+            errs.append(rel_err(xi, o.dm(Ai, Bi, Ci, bi, P, levels=lv, P2=P2 if P2 > 1 else None)))
+        out[prec] = {"systems_per_s": count * 1e3 / ms, "ms_per_batch": ms, "iters": q["last_iters"],
+                     "max_relres": max(rel) if isinstance(rel, list) else rel,
+                     "tflops": (q["factor_flops"] + q["solve_flops"] * q["last_iters"]) / (ms / 1e3) / 1e12,
+                     "rel_err_vs_oracle_sampled": max(errs), "sampled_systems": picks,
+                     "device_gb": q["device_bytes"] / 1e9}
+        dm.dm_destroy(plan)
+        torch.cuda.empty_cache()
+    line = {"metric": "solved systems/s", "workload": "batch", "value": out.get("bf16x3", {}).get("systems_per_s"),
+            "unit": "systems/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic (drawn on device)",
+            "config": {"workload": f"{count} dominant systems, N~U{{32..2048}}, m~U{{32,64,96,128}}, nrhs~U{{1..16}}, "
+                                   f"seed=4", "blocks_gb": 3 * nblk * 8 / 1e9}, "results": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals (mean 2000 requests/s) of solves on a pool of resident
+    systems (the batching workload's size mix plus 5 % large N=8192, m=256);
+    30 % repeat right-hand sides on resident factors, the rest factor + solve;
+    split-bf16 factors refined in float64.  Latency = done - submit on the
+    library's clock."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_06864_gb300 import dm, workloads as w
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    small = w.batch_shapes(48, 5)
+    large = [(8192, 256, 1)] * 2
+    pool = []
+    for i, (n, m, r) in enumerate(small + large):
+        a_, b_, c_, rhs, _ = w.dominant_system_t(n, m, r, 5000 + i, device=dev)
+        P, lv, _ = dm.dm_plan_tune(n, m, r)
+        plan = dm.dm_plan(n, m, r, P, lv, "bf16x3")
+        dm.dm_set_borrow_inputs(plan)
+        dm.dm_factor(plan, a_, b_, c_)
+        rhs2 = [torch.randn_like(rhs) for _ in range(3)]
+        pool.append(dict(plan=plan, A=a_, B=b_, C=c_, b=rhs, rhs=rhs2, large=i >= len(small)))
+    torch.cuda.synchronize()
+    gaps = rng.exponential(1.0 / 2000.0, size=int(args.seconds * 2000 * 1.2))
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < args.seconds]
+    tickets, keep = [], []
+    refused = 0
+    t0 = time.perf_counter()
+    for ta in arrivals:
+        while time.perf_counter() - t0 < ta:
+            pass
+        is_large = rng.random() < 0.05
+        cand = [p for p in pool if p["large"] == is_large]
+        p = cand[rng.integers(len(cand))]
+        x = torch.empty_like(p["b"])
+        try:
+            if rng.random() < 0.3:
+                t = dm.dm_submit(p["plan"], p["rhs"][rng.integers(3)], x)
+            else:
+                t = dm.dm_submit_system(p["plan"], p["A"], p["B"], p["C"], p["b"], x)
+        except dm.DMError:
+            refused += 1
+            continue
+        tickets.append(t)
+        keep.append(x)
+    lat, done_t, sub_t, bad = [], [], [], 0
+    for t in tickets:
+        while True:
+            st, rel, times = dm.dm_poll_times(t)
+            if st != dm.DM_PENDING:
+                break
+            time.sleep(0.0005)
+        if st != dm.DM_OK:
+            bad += 1
+        lat.append(times[2] - times[0])
+        sub_t.append(times[0])
+        done_t.append(times[2])
+    span = max(done_t) - min(sub_t)
+    for p in pool:
+        dm.dm_destroy(p["plan"])
+    line = {"metric": "solved systems/s", "workload": "serve", "value": len(tickets) / span, "unit": "requests/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic (drawn on device)",
+            "offered_rps": len(arrivals) / args.seconds, "completed": len(tickets), "refused": refused,
+            "failed": bad, "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                          "p99": 1e3 * float(np.percentile(lat, 99))},
+            "config": {"workload": "Poisson 2000 req/s; pool of 48 systems of the batch mix + 2 of N=8192 m=256; "
+                                   "5 % large, 30 % repeat right-hand side; bf16x3 + fp64 refinement",
+                       "seconds": args.seconds, "slots": 8}}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

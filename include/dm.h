@@ -85,8 +85,11 @@ typedef struct dm_plan_info {
  * Section 4.2.1, its subsystem count from Eq. (SuppMatrM)).  P = 0 or
  * levels = 0 asks the built-in tuner to choose (seeded by Eqs. (MAXSpeedP) and
  * (SuppMatrM)).  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
- * device workspace; returns DM_EINVAL or DM_ENOMEM on failure.  *out is set
- * only on success. */
+ * device workspace (factors, sweep vectors, supplementary systems) after an
+ * admission check against the free device memory; returns DM_EINVAL or
+ * DM_ENOMEM on failure.  The plan's copy of A, B, C (3 N m^2 doubles) is
+ * allocated by the first dm_factor that copies (none if the plan borrows its
+ * inputs, see dm_set_borrow_inputs).  *out is set only on success. */
 int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision);
 
 /* Plan `count` independent systems (sizes N[s], m[s], nrhs[s]) that are
@@ -102,7 +105,8 @@ int dm_plan_batch(dm_plan_t* out, int count, const int* N, const int* m, const i
  * (Eq. e231, the W_R right-hand sides), assembly of the supplementary matrix
  * (Eq. e2311) and its float64 factorisation (Eq. e232).  The factors stay on
  * the device until dm_destroy; dm_factor may be called again with new blocks.
- * Returns DM_ESINGULAR if a pivot vanished (dm_last_error names the block row). */
+ * Returns DM_ESINGULAR if a pivot vanished (dm_last_error names the block row),
+ * DM_ENOMEM if the first call cannot allocate the plan's input copies. */
 int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C);
 
 /* Solve T x = b with the resident factors: subsystem sweeps for z^k
@@ -135,6 +139,11 @@ int dm_submit_system(dm_plan_t plan, const double* A, const double* B, const dou
  * receives its relative residual.  A finished ticket is forgotten after the
  * poll that reports it.  DM_EINVAL for an unknown ticket. */
 int dm_poll(uint64_t ticket, int* status, double* relres_out);
+
+/* dm_poll that also reports, for a finished request, when it was submitted,
+ * started on a worker and finished (times[0..2], seconds on a monotonic clock
+ * with an arbitrary origin); times untouched while DM_PENDING. */
+int dm_poll_times(uint64_t ticket, int* status, double* relres_out, double* times);
 
 /* Number of serving worker streams (1..64); only before the first submit. */
 int dm_serve_slots(int slots);
@@ -187,6 +196,14 @@ long long dm_launch_count(dm_plan_t plan);
  * for dm_factor. */
 int dm_solve_noalloc(int N, int m, int nrhs, int P, const double* A, const double* B, const double* C,
                      const double* b, double* x, void* stream);
+
+/* Borrow the inputs instead of copying them: the plan keeps no copy of A, B,
+ * C (3 N m^2 doubles per system; freed if already made) and from then on dm_factor
+ * takes device pointers only and uses them in place; they must stay valid and
+ * unchanged until the next dm_factor or dm_destroy (the residual of every
+ * dm_solve reads them).  For systems that fill a large part of device memory.
+ * Cannot be switched off. */
+int dm_set_borrow_inputs(dm_plan_t plan, int enable);
 
 /* Optional settings and queries. */
 int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */

@@ -259,9 +259,13 @@ int Level::allocate() {
 #define DM_ALLOC(ptr, bytes)                                    \
   if ((rc = alloc(reinterpret_cast<void**>(&(ptr)), (bytes)))) \
     return rc;
-  DM_ALLOC(A, nblk * sizeof(double));
-  DM_ALLOC(B, nblk * sizeof(double));
-  DM_ALLOC(C, nblk * sizeof(double));
+  // the top level's A, B, C copies are allocated at the first copying factor
+  // (ensure_inputs); deeper levels own their assembled blocks from the start
+  if (!lazy_inputs) {
+    DM_ALLOC(A, nblk * sizeof(double));
+    DM_ALLOC(B, nblk * sizeof(double));
+    DM_ALLOC(C, nblk * sizeof(double));
+  }
   DM_ALLOC(G, nblk * es);
   DM_ALLOC(Acal, nblk * es);
   DM_ALLOC(ZL, nblk * es);
@@ -291,6 +295,34 @@ int Level::allocate() {
     DM_CUDA(cudaMemset(supp->C, 0, supp->nblk * sizeof(double)));
   }
   return DM_OK;
+}
+
+int Level::ensure_inputs() {
+  if (A) return DM_OK;
+  void* p[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < 3; ++i) {
+    cudaError_t e = cudaMalloc(&p[i], std::max<size_t>(16, nblk * sizeof(double)));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaFree(p[j]);
+      return set_error(DM_ENOMEM, "cudaMalloc of the %zu-byte input copies failed: %s", nblk * sizeof(double),
+                       cudaGetErrorString(e));
+    }
+  }
+  for (int i = 0; i < 3; ++i) owned.push_back(p[i]);
+  A = static_cast<double*>(p[0]);
+  B = static_cast<double*>(p[1]);
+  C = static_cast<double*>(p[2]);
+  return DM_OK;
+}
+
+void Level::release(void* p) {
+  for (size_t i = 0; i < owned.size(); ++i)
+    if (owned[i] == p) {
+      cudaFree(p);
+      owned.erase(owned.begin() + i);
+      return;
+    }
 }
 
 Level::~Level() {
@@ -587,6 +619,7 @@ int Plan::run(GraphCache& g, F&& body) {
 
 int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
+  top.lazy_inputs = true;
   int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
   {
@@ -594,7 +627,7 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
     // lacks the plan's footprint plus a reserve
     size_t free_b = 0, total_b = 0;
     DM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const size_t need = top.bytes_needed() + 2 * top.nvec * sizeof(double);
+    const size_t need = top.bytes_needed() - 3 * top.nblk * sizeof(double) + 2 * top.nvec * sizeof(double);
     const size_t reserve = std::min<size_t>(total_b / 64, size_t(1) << 30);
     if (need + reserve > free_b)
       return set_error(DM_ENOMEM, "admission refused: plan needs %zu bytes, %zu free (reserve %zu)", need, free_b,
@@ -621,7 +654,7 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   h_nrm.assign((size_t)std::max(1, top.nsys) * 4 * kMaxR, 0.0);
   relres.assign(std::max(1, top.nsys), 0.0);
   level_flops(top, &factor_flops, &solve_flops);
-  device_bytes = top.bytes_needed() + 2 * top.nvec * sizeof(double);
+  device_bytes = top.bytes_needed() - 3 * top.nblk * sizeof(double) + 2 * top.nvec * sizeof(double);
   return DM_OK;
 }
 
@@ -629,20 +662,39 @@ Plan::~Plan() {
   if (R) cudaFree(R);
   if (Dx) cudaFree(Dx);
   if (nrm) cudaFree(nrm);
-  for (GraphCache* g : {&g_factor, &g_solve, &g_iter_first, &g_iter_next})
-    if (g->exec) cudaGraphExecDestroy(g->exec);
+  reset_graphs();
   if (own_stream) cudaStreamDestroy(own_stream);
   if (aux.st) cudaStreamDestroy(aux.st);
   if (aux.ev_main) cudaEventDestroy(aux.ev_main);
   if (aux.ev_aux) cudaEventDestroy(aux.ev_aux);
 }
 
+void Plan::reset_graphs() {
+  for (GraphCache* g : {&g_factor, &g_solve, &g_iter_first, &g_iter_next}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    *g = GraphCache();
+  }
+}
+
 int Plan::factor(const double* A, const double* B, const double* C) {
   cudaStream_t st = stream;
   int rc;
-  if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
-  if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
-  if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
+  if (borrow) {
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))
+      return set_error(DM_EINVAL, "a plan that borrows its inputs needs device pointers for A, B, C");
+    if (A != bA || B != bB || C != bC) {  // captured graphs hold the old addresses
+      reset_graphs();
+      bA = A, bB = B, bC = C;
+    }
+    top.A = const_cast<double*>(A);
+    top.B = const_cast<double*>(B);
+    top.C = const_cast<double*>(C);
+  } else {
+    if ((rc = top.ensure_inputs())) return rc;
+    if ((rc = copy_in(top.A, A, top.nblk * sizeof(double), st))) return rc;
+    if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
+    if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
+  }
   rc = run(g_factor, [&] { factor_level(top, stream, prof, &aux); });
   if (rc) return rc;
   rc = check_status(top, st, 0);
@@ -875,6 +927,22 @@ int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out) {
 int dm_set_stream(dm_plan_t plan, void* cuda_stream) {
   if (!plan) return set_error(DM_EINVAL, "NULL plan");
   plan->plan.stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : plan->plan.own_stream;
+  return DM_OK;
+}
+
+int dm_set_borrow_inputs(dm_plan_t plan, int enable) {
+  if (!plan) return set_error(DM_EINVAL, "NULL plan");
+  Plan& p = plan->plan;
+  if (!enable) return p.borrow ? set_error(DM_ESTATE, "borrowing cannot be switched off") : DM_OK;
+  if (p.borrow) return DM_OK;
+  if (p.top.A) {
+    p.top.release(p.top.A);
+    p.top.release(p.top.B);
+    p.top.release(p.top.C);
+    p.top.A = p.top.B = p.top.C = nullptr;
+  }
+  p.borrow = true;
+  p.factored = false;
   return DM_OK;
 }
 

@@ -949,7 +949,8 @@ std::unordered_map<const void*, size_t> g_smem_granted;
 
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return;
+  // the default limit (48 KB) covers static + dynamic shared memory together
+  if (bytes + 4096 <= 48 * 1024) return;
   const void* key = reinterpret_cast<const void*>(kernel);
   std::lock_guard<std::mutex> lk(g_smem_mu);
   size_t& g = g_smem_granted[key];

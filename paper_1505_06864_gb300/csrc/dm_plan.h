@@ -92,6 +92,9 @@ struct Level {
   std::vector<void*> owned;
 
   int build(const std::vector<SysSpec>& specs, bool fp32_factors, int tensor_mode = -1);
+  void release(void* p);  // free one owned buffer now
+  bool lazy_inputs = false;  // A, B, C copies allocated at the first copying factor
+  int ensure_inputs();
   void compute_costs();
   size_t bytes_needed() const;
   int allocate();
@@ -126,6 +129,9 @@ struct Plan {
   Aux aux;
   bool use_graphs = true;
   GraphCache g_factor, g_solve, g_iter_first, g_iter_next;
+  bool borrow = false;  // use the caller's device A, B, C in place (no copy)
+  const double *bA = nullptr, *bB = nullptr, *bC = nullptr;
+  void reset_graphs();
   template <typename F>
   int run(GraphCache& g, F&& body);
 

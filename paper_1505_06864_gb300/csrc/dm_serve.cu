@@ -38,7 +38,12 @@ struct Outcome {
   bool done = false;
   int status = DM_PENDING;
   double relres = 0.0;
+  double t_submit = 0, t_start = 0, t_done = 0;  // steady clock, seconds
 };
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 class Server {
  public:
@@ -55,13 +60,14 @@ class Server {
     r.ticket = ++next_ticket_;
     queue_.push_back(r);
     outcomes_[r.ticket] = Outcome();
+    outcomes_[r.ticket].t_submit = now_s();
     pending_[r.plan] += 1;
     *ticket = r.ticket;
     cv_.notify_one();
     return DM_OK;
   }
 
-  int poll(uint64_t ticket, int* status, double* relres) {
+  int poll(uint64_t ticket, int* status, double* relres, double* times) {
     std::lock_guard<std::mutex> lk(mu_);
     auto it = outcomes_.find(ticket);
     if (it == outcomes_.end()) return set_error(DM_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
@@ -71,6 +77,11 @@ class Server {
     }
     *status = it->second.status;
     if (relres) *relres = it->second.relres;
+    if (times) {
+      times[0] = it->second.t_submit;
+      times[1] = it->second.t_start;
+      times[2] = it->second.t_done;
+    }
     outcomes_.erase(it);
     return DM_OK;
   }
@@ -111,6 +122,7 @@ class Server {
       {
         std::unique_lock<std::mutex> lk(mu_);
         cv_.wait(lk, [&] { return pick_locked(&r); });
+        outcomes_[r.ticket].t_start = now_s();
       }
       Plan& p = r.plan->plan;
       cudaStream_t keep = p.stream;
@@ -131,6 +143,7 @@ class Server {
         o.done = true;
         o.status = rc;
         o.relres = rel;
+        o.t_done = now_s();
         busy_.erase(r.plan);
         pending_[r.plan] -= 1;
       }
@@ -188,7 +201,12 @@ int dm_submit_system(dm_plan_t plan, const double* A, const double* B, const dou
 
 int dm_poll(uint64_t ticket, int* status, double* relres_out) {
   if (!status) return set_error(DM_EINVAL, "NULL status");
-  return Server::get().poll(ticket, status, relres_out);
+  return Server::get().poll(ticket, status, relres_out, nullptr);
+}
+
+int dm_poll_times(uint64_t ticket, int* status, double* relres_out, double* times) {
+  if (!status || !times) return set_error(DM_EINVAL, "NULL status or times");
+  return Server::get().poll(ticket, status, relres_out, times);
 }
 
 int dm_serve_slots(int slots) { return Server::get().configure(slots); }

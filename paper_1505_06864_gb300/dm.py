@@ -68,6 +68,7 @@ def lib():
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_set_stream": (I, [P, P]),
             "dm_set_refinement": (I, [P, D, I]),
+            "dm_set_borrow_inputs": (I, [P, I]),
             "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
             "dm_profile": (I, [P, I, ctypes.POINTER(dm_profile_entry), I, ctypes.POINTER(I)]),
             "dm_launch_count": (ctypes.c_longlong, [P]),
@@ -75,6 +76,7 @@ def lib():
             "dm_submit": (I, [P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
             "dm_submit_system": (I, [P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
             "dm_poll": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "dm_poll_times": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
             "dm_serve_slots": (I, [I]),
             "dm_destroy": (V, [P]),
             "dm_last_error": (ctypes.c_char_p, []),
@@ -158,6 +160,10 @@ def dm_set_stream(plan, stream):
     return _check(lib().dm_set_stream(plan, ctypes.c_void_p(h) if h else None))
 
 
+def dm_set_borrow_inputs(plan, enable=True):
+    return _check(lib().dm_set_borrow_inputs(plan, 1 if enable else 0))
+
+
 def dm_set_refinement(plan, tol, max_iters):
     return _check(lib().dm_set_refinement(plan, float(tol), int(max_iters)))
 
@@ -209,6 +215,15 @@ def dm_poll(ticket):
     st, rel = ctypes.c_int(0), ctypes.c_double(0.0)
     _check(lib().dm_poll(ctypes.c_uint64(ticket), ctypes.byref(st), ctypes.byref(rel)))
     return st.value, rel.value
+
+
+def dm_poll_times(ticket):
+    """(status, relres, (t_submit, t_start, t_done)) -- times in seconds on the
+    library's monotonic clock, None while DM_PENDING."""
+    st, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    t = (ctypes.c_double * 3)()
+    _check(lib().dm_poll_times(ctypes.c_uint64(ticket), ctypes.byref(st), ctypes.byref(rel), t))
+    return st.value, rel.value, (None if st.value == DM_PENDING else (t[0], t[1], t[2]))
 
 
 def dm_serve_slots(slots):

@@ -207,6 +207,60 @@ def batch_shapes(count: int, seed: int, n_lo=32, n_hi=2048, ms=(32, 64, 96, 128)
     return [(int(n), int(ms[j]), int(r)) for n, j, r in zip(Ns, mi, rs)]
 
 
+# ---------------------------------------------------------------- device copies
+# The same generator written with torch int64 tensors, so that large inputs
+# can be drawn directly in device memory.  Uniform draws are bit-identical to
+# the numpy version (wrapping int64 arithmetic, logical shifts by masking);
+# the dominance shift uses the same summation order; normals and b = T x may
+# differ from the numpy version in the last bits (different log/cos/matmul).
+def _t_u64(torch, seed, stream, count, offset, device):
+    I64 = torch.int64
+    sgn = lambda v: v - (1 << 64) if v >= (1 << 63) else v
+    key = int(_key(seed, stream))
+    k = torch.arange(offset + 1, offset + count + 1, dtype=I64, device=device)
+    z = sgn(key) + k * sgn(int(_G))
+    z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * sgn(int(_M1))
+    z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * sgn(int(_M2))
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def uniform_t(seed, stream, count, lo=0.0, hi=1.0, offset=0, device="cuda"):
+    """torch version of ``uniform`` (bit-identical draws)."""
+    import torch
+    z = _t_u64(torch, seed, stream, count, offset, device)
+    u = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def normal_t(seed, stream, count, device="cuda"):
+    import torch
+    u1 = uniform_t(seed, stream, count, device=device)
+    u2 = uniform_t(seed, stream + 1000, count, device=device)
+    return torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * np.pi * u2)
+
+
+def dominant_system_t(N, m, nrhs, seed, device="cuda"):
+    """``dominant_system`` drawn in device memory: returns torch tensors
+    (A, B, C, b, x_true) with the numpy version's shapes."""
+    import torch
+    A = uniform_t(seed, STREAM_A, N * m * m, -1.0, 1.0, device=device).reshape(N, m, m)
+    B = uniform_t(seed, STREAM_B, N * m * m, -1.0, 1.0, device=device).reshape(N, m, m)
+    C = uniform_t(seed, STREAM_C, N * m * m, -1.0, 1.0, device=device).reshape(N, m, m)
+    A[0] = 0.0
+    C[N - 1] = 0.0
+    sh = torch.zeros((N, m), dtype=torch.float64, device=device)
+    for M in (A, B, C):
+        for j in range(m):
+            sh += torch.abs(M[:, :, j])
+    idx = torch.arange(m, device=device)
+    B[:, idx, idx] += sh + 1.0
+    x = normal_t(seed, STREAM_X, N * m * nrhs, device=device).reshape(N, m, nrhs)
+    b = torch.matmul(B, x)
+    b[1:] += torch.matmul(A[1:], x[:-1])
+    b[:-1] += torch.matmul(C[:-1], x[1:])
+    return A, B, C, b, x
+
+
 def random_rhs(N: int, m: int, nrhs: int, seed: int) -> np.ndarray:
     """A fresh right-hand side ~ N(0, 1) for repeat solves on resident factors."""
     return normal(seed, STREAM_RHS, N * m * nrhs).reshape(N, m, nrhs)

@@ -263,3 +263,33 @@ def test_graph_replay_repeats(dm, prec):
     for x in xs:
         check(x, ref, tol)
     assert len(set(counts)) == 1 and counts[0] > 0
+
+
+def test_borrowed_inputs(dm):
+    """A plan that borrows device inputs gives the copy path's x, also when the
+    borrowed arrays change between calls (captured graphs are rebuilt)."""
+    import torch
+    s1 = w.dominant_system(60, 32, 2, 31)
+    s2 = w.dominant_system(60, 32, 2, 32)
+    T = lambda a: torch.from_numpy(a).cuda()
+    plan = dm.dm_plan(60, 32, 2, 5, 1, "fp64")
+    try:
+        dm.dm_set_borrow_inputs(plan)
+        with pytest.raises(dm.DMError):
+            dm.dm_factor(plan, s1.A, s1.B, s1.C)        # host arrays are refused
+        for s in (s1, s1, s2, s2, s1):
+            A, B, C = T(s.A), T(s.B), T(s.C)
+            dm.dm_factor(plan, A, B, C)
+            x = np.zeros_like(s.b)
+            dm.dm_solve(plan, s.b, x)
+            check(x, o.dm(s.A, s.B, s.C, s.b, 5), TOL64)
+    finally:
+        dm.dm_destroy(plan)
+
+
+def test_residual_wide_rhs_m128(dm):
+    """m = 128 with 9..16 right-hand sides: the float64 residual kernel's shared
+    memory (dynamic + static) goes past the default 48 KB."""
+    s = w.dominant_system(20, 128, 16, 41)
+    x, rel, _ = solve(dm, s, 3, 1, "fp32")
+    check(x, o.dm(s.A, s.B, s.C, s.b, 3), TOLMIX)

@@ -347,3 +347,15 @@ def test_planted_mistakes_are_caught(monkeypatch, kind):
     f = _mutated_dm(monkeypatch, kind)
     x = f(s.A, s.B, s.C, s.b, 3)
     assert o.rel_err(x, xd) > 1e-6
+
+
+def test_device_generator_bit_identical_uniforms():
+    torch = pytest.importorskip("torch")
+    a = w.uniform(7, 3, 1000, -1.0, 1.0, offset=12345)
+    b = w.uniform_t(7, 3, 1000, -1.0, 1.0, offset=12345, device="cpu").numpy()
+    np.testing.assert_array_equal(a, b)
+    s = w.dominant_system(5, 4, 2, 9)
+    A, B, C, bb, x = w.dominant_system_t(5, 4, 2, 9, device="cpu")
+    np.testing.assert_array_equal(s.A, A.numpy())
+    np.testing.assert_array_equal(s.B, B.numpy())     # same draws and same shift summation order
+    np.testing.assert_allclose(s.x_true, x.numpy(), rtol=1e-13)
