@@ -205,6 +205,12 @@ int dm_solve_noalloc(int N, int m, int nrhs, int P, const double* A, const doubl
  * Cannot be switched off. */
 int dm_set_borrow_inputs(dm_plan_t plan, int enable);
 
+/* Factor sweeps: run the left-spike tiles (off the inversion chain) on a
+ * second stream that overlaps the next block inversion (enable = 1) or in
+ * the same launches as the rest (0, the default; on GB300 both run at the
+ * same speed for float64, whose FP64 pipes both stages share). */
+int dm_set_side_stream(dm_plan_t plan, int enable);
+
 /* Optional settings and queries. */
 int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */
 int dm_set_refinement(dm_plan_t plan, double tol, int max_iters); /* default 1e-12, 30 */

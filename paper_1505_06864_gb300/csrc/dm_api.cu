@@ -695,7 +695,7 @@ int Plan::factor(const double* A, const double* B, const double* C) {
     if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
     if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
   }
-  rc = run(g_factor, [&] { factor_level(top, stream, prof, &aux); });
+  rc = run(g_factor, [&] { factor_level(top, stream, prof, overlap ? &aux : nullptr); });
   if (rc) return rc;
   rc = check_status(top, st, 0);
   factored = (rc == DM_OK);
@@ -927,6 +927,13 @@ int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out) {
 int dm_set_stream(dm_plan_t plan, void* cuda_stream) {
   if (!plan) return set_error(DM_EINVAL, "NULL plan");
   plan->plan.stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : plan->plan.own_stream;
+  return DM_OK;
+}
+
+int dm_set_side_stream(dm_plan_t plan, int enable) {
+  if (!plan) return set_error(DM_EINVAL, "NULL plan");
+  if (plan->plan.overlap != (enable != 0)) plan->plan.reset_graphs();
+  plan->plan.overlap = enable != 0;
   return DM_OK;
 }
 

@@ -35,22 +35,43 @@ constexpr int kThreads = 256;  // 16 x 16 thread grid of the panel products
 // Panel product core.  Computes rows r0..r0+63 of L (m x m, row-major, leading
 // dimension m, element type TL) times Rs (m x W in shared memory, row stride
 // W), accumulating into acc.  Thread (ty, tx) owns rows r0 + ty + 16a (a < 4)
-// and columns tx + 16b (b < W/16).  Lc is a 64 x 17 staging tile for L.
+// and columns tx + 16b (b < W/16).  Lc holds two 64 x 17 staging tiles for L.
 template <typename T, typename TL, int W>
 __device__ __forceinline__ void mm_rowblock(T (&acc)[4][W / 16], const TL* __restrict__ L, int m,
                                             int r0, const T* __restrict__ Rs, T* __restrict__ Lc) {
+  // Lc holds two 64 x 17 staging tiles: the chunk being multiplied and the
+  // next one, whose global loads are issued before the current chunk's FMAs.
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  for (int k0 = 0; k0 < m; k0 += 16) {
-    for (int e = tid; e < 64 * 16; e += kThreads) {
+  constexpr int PER = 64 * 16 / kThreads;  // elements per thread per chunk
+  T nxt[PER];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * kThreads;
       const int rr = e >> 4, kk = e & 15, row = r0 + rr, col = k0 + kk;
-      Lc[rr * 17 + kk] = (row < m && col < m) ? (T)L[(long long)row * m + col] : (T)0;
+      nxt[u] = (row < m && col < m) ? (T)L[(long long)row * m + col] : (T)0;
     }
-    __syncthreads();
+  };
+  auto stash = [&](T* buf) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * kThreads;
+      buf[(e >> 4) * 17 + (e & 15)] = nxt[u];
+    }
+  };
+  fetch(0);
+  stash(Lc);
+  __syncthreads();
+  int cur = 0;
+  for (int k0 = 0; k0 < m; k0 += 16) {
+    const bool more = k0 + 16 < m;
+    if (more) fetch(k0 + 16);
+    const T* Lt = Lc + cur * (64 * 17);
     const int kmax = min(16, m - k0);
     for (int kk = 0; kk < kmax; ++kk) {
       T lv[4], rv[W / 16];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) lv[a] = Lc[(ty + 16 * a) * 17 + kk];
+      for (int a = 0; a < 4; ++a) lv[a] = Lt[(ty + 16 * a) * 17 + kk];
 #pragma unroll
       for (int b = 0; b < W / 16; ++b) rv[b] = Rs[(k0 + kk) * W + tx + 16 * b];
 #pragma unroll
@@ -58,7 +79,9 @@ __device__ __forceinline__ void mm_rowblock(T (&acc)[4][W / 16], const TL* __res
 #pragma unroll
         for (int b = 0; b < W / 16; ++b) acc[a][b] = fma(lv[a], rv[b], acc[a][b]);
     }
+    if (more) stash(Lc + (cur ^ 1) * (64 * 17));
     __syncthreads();
+    cur ^= 1;
   }
 }
 
@@ -99,7 +122,7 @@ __device__ __forceinline__ void load_panel(T* Rs, const TS* __restrict__ src, in
 
 template <typename T>
 __host__ __device__ constexpr size_t panel_smem(int m, int W, int npanels) {
-  return sizeof(T) * ((size_t)npanels * m * W + 64 * 17);
+  return sizeof(T) * ((size_t)npanels * m * W + 2 * 64 * 17);
 }
 
 template <int W>

@@ -130,6 +130,7 @@ struct Plan {
   bool use_graphs = true;
   GraphCache g_factor, g_solve, g_iter_first, g_iter_next;
   bool borrow = false;  // use the caller's device A, B, C in place (no copy)
+  bool overlap = false;  // left-spike tiles on the side stream
   const double *bA = nullptr, *bB = nullptr, *bC = nullptr;
   void reset_graphs();
   template <typename F>

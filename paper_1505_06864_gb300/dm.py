@@ -69,6 +69,7 @@ def lib():
             "dm_set_stream": (I, [P, P]),
             "dm_set_refinement": (I, [P, D, I]),
             "dm_set_borrow_inputs": (I, [P, I]),
+            "dm_set_side_stream": (I, [P, I]),
             "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
             "dm_profile": (I, [P, I, ctypes.POINTER(dm_profile_entry), I, ctypes.POINTER(I)]),
             "dm_launch_count": (ctypes.c_longlong, [P]),
@@ -162,6 +163,10 @@ def dm_set_stream(plan, stream):
 
 def dm_set_borrow_inputs(plan, enable=True):
     return _check(lib().dm_set_borrow_inputs(plan, 1 if enable else 0))
+
+
+def dm_set_side_stream(plan, enable=True):
+    return _check(lib().dm_set_side_stream(plan, 1 if enable else 0))
 
 
 def dm_set_refinement(plan, tol, max_iters):
