@@ -222,15 +222,11 @@ def main():
     launches = dm.dm_launch_count(plan) - launches0
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     xh = x.cpu().numpy()
     rel_true = rel_err(xh, s.x_true)
     flops_step = info["factor_flops"] + info["solve_flops"]
-    value = ws * args.steps / (total_ms / 1e3)
+    value = job_value(args.steps, ws, total_ms)
 
     # roofline of the dominant kernel class (largest summed event time)
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -277,6 +273,23 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def max_over_ranks(value, ws, device):
+    """The largest of every rank's value (replicas: the job's time is the
+    slowest rank's); one all_reduce of a scalar, no data-path collective."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, ws, total_ms):
+    """Whole-job throughput: every rank solved `steps` systems in total_ms."""
+    return ws * steps / (total_ms / 1e3)
 
 
 def rel_err(x, xref):
