@@ -82,9 +82,10 @@ typedef struct dm_plan_info {
  * 1 <= P <= (N+1)/2, every subsystem keeps >= 1 row; P = 1 is the block Thomas
  * algorithm of Section 3).  levels >= 1: the supplementary system of Eq. (e232)
  * is solved by block Thomas (levels = 1) or by DM recursively (levels > 1,
- * Section 4.2.1, its subsystem count from Eq. (SuppMatrM)).  P = 0 or
- * levels = 0 asks the built-in tuner to choose (seeded by Eqs. (MAXSpeedP) and
- * (SuppMatrM)).  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
+ * Section 4.2.1, its subsystem count from Eq. (SuppMatrM)).  P = 0 and
+ * levels = 0 take the measured choice of dm_autotune for this shape and
+ * precision if there is one, else (and for P = 0 or levels = 0 alone) the
+ * paper's optimum: Eq. (MAXSpeedP) for P, depth 2 when P >= 21.  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
  * device workspace (factors, sweep vectors, supplementary systems) after an
  * admission check against the free device memory; returns DM_EINVAL or
  * DM_ENOMEM on failure.  The plan's copy of A, B, C (3 N m^2 doubles) is
@@ -117,6 +118,18 @@ int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C)
  * iteration cap; DM_ENOTCONV then, with the best x written.  x may alias b.
  * relres_out (may be NULL) receives max over columns of ||b - T x||/||b||. */
 int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out);
+
+/* Measured tuning: time candidate decompositions -- P from the paper's
+ * optimum (Eq. MAXSpeedP), its half and double, and multiples of half the SM
+ * count; recursion depth 1, 2, 3 -- on a synthetic diagonally dominant system
+ * of this shape (drawn on the device, freed afterwards), for dm_factor +
+ * dm_solve at `precision`, and return the fastest (*ms_out: its time per
+ * factor + solve).  The choice is remembered per (N, m, nrhs, precision) for
+ * the process and, if the environment variable DM_TUNE_CACHE names a file,
+ * in that file; dm_plan with P = 0 and levels = 0 then uses it.  Needs room
+ * for the synthetic system and one plan at a time; a call for a remembered
+ * shape returns at once. */
+int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* levels, double* ms_out);
 
 /* Continuous batching.  dm_submit queues a solve of b on the plan's resident
  * factors; dm_submit_system queues a factor (of A, B, C) followed by a solve.

@@ -875,6 +875,7 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
     return set_error(DM_EINVAL, "unknown precision %d", precision);
   if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)
     return set_error(DM_EINVAL, "tensor-core precisions support m <= %d", kMaxMTensor);
+  if (P == 0 && levels == 0) tuned_lookup(N, m, nrhs, precision, &P, &levels);  // measured choice, if any
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, levels, &s);
   if (rc) return rc;

@@ -155,6 +155,7 @@ int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 void serve_drain(struct dm_plan_s* plan);
+bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels);
 
 }  // namespace dm
 

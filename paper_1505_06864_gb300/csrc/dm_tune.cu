@@ -1,0 +1,206 @@
+// Measured tuner for the decomposition: times candidate (P, levels) pairs on
+// a synthetic system of the requested shape and remembers the fastest.
+//
+// Candidates are seeded by the paper's analytical optimum, Eq. (MAXSpeedP)
+// (P* = sqrt((N+1)/3 (5 + 2/(1 + l/n)))), widened by P*/2 and 2 P* and by
+// the multiples of the SM count that fit (on a GPU the "processors" of the
+// paper's model are the SMs, and every subsystem step is one launch over all
+// subsystems), each with recursion depth 1, 2 and 3 (Section 4.2.1).  The
+// synthetic system has uniform [-1, 1] blocks made diagonally dominant, drawn
+// on the device by a counter-based hash; the timing covers dm_factor +
+// dm_solve as a user would call them.  Results are kept per (N, m, nrhs,
+// precision) in memory and, when the environment variable DM_TUNE_CACHE names
+// a file, in that file (one line per shape).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "../../include/dm.h"
+#include "dm_plan.h"
+
+namespace dm {
+namespace {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double unif(uint64_t key, long long i) {
+  const uint64_t z = mix64(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+  return -1.0 + 2.0 * (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_fill(double* A, double* B, double* C, int N, int m, uint64_t seed) {
+  const long long mm = (long long)m * m, n = (long long)N * mm;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / mm;
+    A[i] = row == 0 ? 0.0 : unif(seed * 3 + 1, i);
+    B[i] = unif(seed * 3 + 2, i);
+    C[i] = row == N - 1 ? 0.0 : unif(seed * 3 + 3, i);
+  }
+}
+
+// diagonal dominance: B[i][r][r] += sum_j |A|+|B|+|C| + 1 (one thread per point row)
+__global__ void k_shift(const double* A, double* B, const double* C, int N, int m) {
+  const long long rows = (long long)N * m;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < rows; q += (long long)gridDim.x * blockDim.x) {
+    const long long i = q / m, r = q - i * m, o = i * m * m + r * m;
+    double s = 1.0;
+    for (int j = 0; j < m; ++j) s += fabs(A[o + j]) + fabs(B[o + j]) + fabs(C[o + j]);
+    B[o + r] += s;
+  }
+}
+
+__global__ void k_fill_vec(double* b, long long n, uint64_t seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = unif(seed, i);
+}
+
+struct Choice {
+  int P, levels;
+  double ms;
+};
+using Key = std::tuple<int, int, int, int>;
+std::mutex g_mu;
+std::map<Key, Choice> g_cache;
+bool g_loaded = false;
+
+void load_cache_locked() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char* path = std::getenv("DM_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int N, m, r, prec, P, lv;
+  double ms;
+  while (std::fscanf(f, "%d %d %d %d %d %d %lf", &N, &m, &r, &prec, &P, &lv, &ms) == 7)
+    g_cache[Key(N, m, r, prec)] = Choice{P, lv, ms};
+  std::fclose(f);
+}
+
+void save_cache_locked() {
+  const char* path = std::getenv("DM_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (auto& kv : g_cache)
+    std::fprintf(f, "%d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                 std::get<3>(kv.first), kv.second.P, kv.second.levels, kv.second.ms);
+  std::fclose(f);
+}
+
+struct DevBuf {
+  double* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t n) {
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return set_error(DM_ENOMEM, "autotune: cannot allocate %zu doubles", n);
+    }
+    return DM_OK;
+  }
+};
+
+}  // namespace
+
+bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  load_cache_locked();
+  auto it = g_cache.find(Key(N, m, r, prec));
+  if (it == g_cache.end()) return false;
+  *P = it->second.P;
+  *levels = it->second.levels;
+  return true;
+}
+
+int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache_locked();
+    auto it = g_cache.find(Key(N, m, r, prec));
+    if (it != g_cache.end()) {
+      *P_out = it->second.P;
+      *lv_out = it->second.levels;
+      if (ms_out) *ms_out = it->second.ms;
+      return DM_OK;
+    }
+  }
+  SysSpec seed;
+  int rc = make_spec(N, m, r, 0, 1, &seed);
+  if (rc) return rc;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  std::set<int> Ps = {seed.P, std::max(1, seed.P / 2), seed.P * 2};
+  for (int k = 1; k <= 4; ++k) Ps.insert(k * sms / 2);
+  std::set<std::tuple<int, int, int>> cand;  // (P, levels, P2) after validation
+  for (int P : Ps) {
+    if (P < 1 || (P > 1 && 2 * P - 1 > N)) continue;
+    for (int lv = 1; lv <= 3; ++lv) {
+      SysSpec s;
+      if (make_spec(N, m, r, P, lv, &s) == DM_OK) cand.insert({s.P, s.levels, s.P2});
+    }
+  }
+  if (cand.empty()) return set_error(DM_EINVAL, "autotune: no valid decomposition for N = %d", N);
+  const long long nb = (long long)N * m * m, nv = (long long)N * m * r;
+  DevBuf A, B, C, b, x;
+  if ((rc = A.alloc(nb)) || (rc = B.alloc(nb)) || (rc = C.alloc(nb)) || (rc = b.alloc(nv)) || (rc = x.alloc(nv)))
+    return rc;
+  k_fill<<<1024, 256>>>(A.p, B.p, C.p, N, m, 12345u);
+  k_shift<<<1024, 256>>>(A.p, B.p, C.p, N, m);
+  k_fill_vec<<<256, 256>>>(b.p, nv, 777u);
+  if (cudaDeviceSynchronize() != cudaSuccess) return set_error(DM_ECUDA, "autotune: input generation failed");
+  Choice best{0, 0, 1e300};
+  for (auto& c : cand) {
+    SysSpec s;
+    if (make_spec(N, m, r, std::get<0>(c), std::get<1>(c), &s) != DM_OK) continue;
+    Plan plan;
+    if (plan.init(std::vector<SysSpec>{s}, prec) != DM_OK) continue;  // e.g. does not fit: skip
+    double ms = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      const auto t0 = std::chrono::steady_clock::now();
+      int e = plan.factor(A.p, B.p, C.p);
+      std::vector<double> rel(1);
+      if (e == DM_OK) e = plan.solve(b.p, x.p, rel.data());
+      const auto t1 = std::chrono::steady_clock::now();
+      if (e != DM_OK && e != DM_ENOTCONV) {
+        ms = 1e300;
+        break;
+      }
+      if (rep == 1) ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+    if (ms < best.ms) best = Choice{s.P, s.levels, ms};
+  }
+  if (best.P == 0) return set_error(DM_ENOMEM, "autotune: no candidate could be timed");
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[Key(N, m, r, prec)] = best;
+    save_cache_locked();
+  }
+  *P_out = best.P;
+  *lv_out = best.levels;
+  if (ms_out) *ms_out = best.ms;
+  return DM_OK;
+}
+
+}  // namespace dm
+
+extern "C" int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* levels, double* ms_out) {
+  if (!P || !levels) return dm::set_error(DM_EINVAL, "NULL argument to dm_autotune");
+  if (precision < DM_FP64 || precision > DM_BF16X3) return dm::set_error(DM_EINVAL, "unknown precision");
+  return dm::autotune(N, m, nrhs, precision, P, levels, ms_out);
+}

@@ -64,6 +64,7 @@ def lib():
             "dm_plan_batch": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I),
                                   ctypes.POINTER(I), I]),
             "dm_plan_tune": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_set_stream": (I, [P, P]),
@@ -140,6 +141,16 @@ def dm_plan_tune(N, m, nrhs, P=0, levels=0):
     p, lv, p2 = ctypes.c_int(P), ctypes.c_int(levels), ctypes.c_int(0)
     _check(lib().dm_plan_tune(int(N), int(m), int(nrhs), ctypes.byref(p), ctypes.byref(lv), ctypes.byref(p2)))
     return p.value, lv.value, p2.value
+
+
+def dm_autotune(N, m, nrhs, precision=DM_FP64):
+    """(P, levels, ms) of the fastest measured decomposition for this shape."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p, lv, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().dm_autotune(int(N), int(m), int(nrhs), int(precision), ctypes.byref(p), ctypes.byref(lv),
+                             ctypes.byref(ms)))
+    return p.value, lv.value, ms.value
 
 
 def dm_factor(plan, A, B, C):

@@ -293,3 +293,20 @@ def test_residual_wide_rhs_m128(dm):
     s = w.dominant_system(20, 128, 16, 41)
     x, rel, _ = solve(dm, s, 3, 1, "fp32")
     check(x, o.dm(s.A, s.B, s.C, s.b, 3), TOLMIX)
+
+
+def test_autotune_choice_used_by_plan(dm):
+    P, lv, ms = dm.dm_autotune(300, 32, 2, "fp64")
+    assert P >= 1 and lv >= 1 and ms > 0
+    assert dm.dm_autotune(300, 32, 2, "fp64")[:2] == (P, lv)      # remembered
+    s = w.dominant_system(300, 32, 2, 61)
+    plan = dm.dm_plan(300, 32, 2, 0, 0, "fp64")
+    try:
+        q = dm.dm_plan_query(plan)
+        assert (q["P"], q["levels"]) == (P, lv)
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        x = np.zeros_like(s.b)
+        dm.dm_solve(plan, s.b, x)
+        check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=q["P2"] if q["P2"] > 1 else None), TOL64)
+    finally:
+        dm.dm_destroy(plan)
