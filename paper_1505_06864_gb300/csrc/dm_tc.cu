@@ -212,6 +212,45 @@ __device__ __forceinline__ void stage_left(uint8_t* dst, const float* __restrict
     cp_commit();
     return;
   }
+  if (MODE == 1 && vec) {
+    // 8 consecutive k per item: two float4 loads, one 16-byte chunk of bf16 hi
+    // and one of bf16 lo (whole-chunk shared stores, no bank conflicts within
+    // a row); U items per thread in flight.
+    constexpr int U = 4;
+    const int n8 = rows * (KA / 8);
+    for (int e0 = threadIdx.x; e0 < n8; e0 += U * kThreads) {
+      float4 v0[U], v1[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kThreads;
+        const int r = e / (KA / 8), k = k0 + 8 * (e - r * (KA / 8));
+        const bool ok = e < n8 && r < m && k < m;
+        const float* src = L + (long long)r * m + k;
+        v0[u] = ok ? *reinterpret_cast<const float4*>(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v1[u] = ok ? *reinterpret_cast<const float4*>(src + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= n8) break;
+        const int r = e / (KA / 8), c = e - r * (KA / 8);
+        const float f[8] = {v0[u].x, v0[u].y, v0[u].z, v0[u].w, v1[u].x, v1[u].y, v1[u].z, v1[u].w};
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]), h1 = __float2bfloat16_rn(f[2 * q + 1]);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
+          hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        uint8_t* t = dst + (r / MT) * tile_bytes + sw128_off(r % MT, c * 16);
+        *reinterpret_cast<uint4*>(t) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(t + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+    return;
+  }
   if (vec) {
     constexpr int U = 4;  // independent vector loads in flight per thread
     const int n4 = rows * (KA / 4);
@@ -246,29 +285,42 @@ __device__ __forceinline__ void stage_left(uint8_t* dst, const float* __restrict
 }
 
 // Right operand: the m x NP panel R[k][c0 + n] (row stride ld, columns past
-// `cols` zero, scaled by `sc`) stored transposed: row n, K index k.
+// `cols` zero, scaled by `sc`) stored transposed: row n, K index k.  A thread
+// builds whole 16-byte chunks (4 TF32 values, or 8 bf16 hi + 8 bf16 lo) from
+// coalesced reads of consecutive columns n across the warp.
 template <int MODE, typename TR>
 __device__ __forceinline__ void stage_right(uint8_t* dst, int slab_bytes, int lo_off, const TR* __restrict__ R,
                                             int m, int ld, int c0, int cols, float sc) {
   constexpr int KA = Fmt<MODE>::katom;
+  constexpr int G = MODE == 0 ? 4 : 8;  // K values per 16-byte chunk
   const int kpad = ((m + KA - 1) / KA) * KA;
-  if (sizeof(TR) == 4 && (ld & 3) == 0 && (c0 & 3) == 0 && (cols & 3) == 0 &&
-      (reinterpret_cast<uintptr_t>(R) & 15) == 0) {
-    for (int e = threadIdx.x; e < kpad * (NP / 4); e += kThreads) {
-      const int k = e / (NP / 4), n = 4 * (e - k * (NP / 4));
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k < m && c0 + n < cols) v = *reinterpret_cast<const float4*>(R + (long long)k * ld + c0 + n);
-      put<MODE>(dst, slab_bytes, lo_off, n + 0, k, sc * v.x);
-      put<MODE>(dst, slab_bytes, lo_off, n + 1, k, sc * v.y);
-      put<MODE>(dst, slab_bytes, lo_off, n + 2, k, sc * v.z);
-      put<MODE>(dst, slab_bytes, lo_off, n + 3, k, sc * v.w);
+  for (int e = threadIdx.x; e < (kpad / G) * NP; e += kThreads) {
+    const int kg = e / NP, n = e - kg * NP, k0 = kg * G;
+    const bool col_ok = c0 + n < cols;
+    float v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = k0 + i;
+      v[i] = (col_ok && k < m) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
     }
-    return;
-  }
-  for (int e = threadIdx.x; e < kpad * NP; e += kThreads) {
-    const int k = e / NP, n = e - k * NP;
-    const float v = (k < m && c0 + n < cols) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
-    put<MODE>(dst, slab_bytes, lo_off, n, k, v);
+    const int slab = k0 / KA, kk = k0 - slab * KA;
+    uint8_t* p = dst + (size_t)slab * slab_bytes + sw128_off(n, kk * Fmt<MODE>::esz);
+    if (MODE == 0) {
+      *reinterpret_cast<uint4*>(p) = make_uint4(__float_as_uint(to_tf32(v[0])), __float_as_uint(to_tf32(v[1])),
+                                                __float_as_uint(to_tf32(v[2])), __float_as_uint(to_tf32(v[3])));
+    } else {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+        hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      *reinterpret_cast<uint4*>(p) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
   }
 }
 
