@@ -282,6 +282,11 @@ int Level::allocate() {
     DM_ALLOC(A32, nblk * sizeof(float));
     DM_ALLOC(B32, nblk * sizeof(float));
     DM_ALLOC(C32, nblk * sizeof(float));
+    // TF32 sweeps stream G, A32, Acal by TMA when every system has the same m
+    bool uniform = true;
+    for (const SysSpec& sp : spec) uniform = uniform && sp.m == max_m;
+    if (tc_mode == 0 && uniform && tma_maps_bytes() <= (int)sizeof(tmaps))
+      has_tma = make_tma_maps(static_cast<float*>(G), A32, static_cast<float*>(Acal), nblk / max_m, max_m, tmaps);
   }
 #undef DM_ALLOC
   if (!parts.empty()) DM_CUDA(cudaMemcpy(d_parts, parts.data(), parts.size() * sizeof(PartDesc), cudaMemcpyHostToDevice));
@@ -423,7 +428,7 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
     if constexpr (std::is_same<T, float>::value) {
       if (L.tc_mode >= 0) {
         launch_fwd_factor_tc(L.tc_mode, L.d_parts, np, t, L.max_m, L.A32, L.B32, L.C32, G, Ac, ZL, ZR, L.d_err, s,
-                             lo, hi);
+                             lo, hi, L.has_tma ? L.tmaps : nullptr);
         return;
       }
     }
@@ -432,7 +437,8 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   auto back = [&](int np, int s) {
     if constexpr (std::is_same<T, float>::value) {
       if (L.tc_mode >= 0) {
-        launch_back_factor_tc(L.tc_mode, L.d_parts, np, s, L.max_m, Ac, ZL, ZR, L.d_err, st);
+        launch_back_factor_tc(L.tc_mode, L.d_parts, np, s, L.max_m, Ac, ZL, ZR, L.d_err, st,
+                              L.has_tma ? L.tmaps : nullptr);
         return;
       }
     }

@@ -84,12 +84,15 @@ void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int ma
 
 // tcgen05 block products of the float32 factor sweeps (dm_tc.cu); mode 0 =
 // TF32, 1 = split bf16 (three products).  m <= 256.
+// tmaps: host copy of the level's tensor maps (make_tma_maps) or nullptr.
 void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const float* A,
                           const float* B, const float* C, float* G, float* Acal, float* ZL, float* ZR,
-                          int* errflag, cudaStream_t st, int type_lo, int type_hi);
+                          int* errflag, cudaStream_t st, int type_lo, int type_hi, const void* tmaps);
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, int max_m, const float* Acal,
-                           float* ZL, float* ZR, int* errflag, cudaStream_t st);
+                           float* ZL, float* ZR, int* errflag, cudaStream_t st, const void* tmaps);
+bool make_tma_maps(const float* G, const float* A32, const float* Acal, long long rows, int m, void* out);
+int tma_maps_bytes();
 constexpr int kMaxMTensor = 256;
 
 constexpr int kMaxM = 512;

@@ -304,32 +304,34 @@ __global__ void __launch_bounds__(256) k_inv_cluster(const PartDesc* __restrict_
   }
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  // Pivot search over rows k..m-1 of local column kl (ties to the lowest row)
+  // by one warp, then publication of the column as it reads after exchanging
+  // rows k and p, into pub[k & 1] / pubp[k & 1].
+  auto search_publish = [&](int k, int kl) {
+    T best = (T)-1;
+    int bi = k;
+    for (int i = k + lane; i < m; i += 32) {
+      const T v = fabs(a[i * lda + kl]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    const T akk = a[k * lda + kl], apk = a[bi * lda + kl];
+    T* pb = pub + (k & 1) * kMaxM;
+    for (int i = lane; i < m; i += 32) pb[i] = (i == k) ? apk : (i == bi ? akk : a[i * lda + kl]);
+    if (lane == 0) pubp[k & 1] = bi;
+  };
+  if (rank == 0 && warp == 0) search_publish(0, 0);  // step 0's column is owned by CTA 0
   for (int k = 0; k < m; ++k) {
     const int owner = k / w, kl = k - owner * w;
     const int buf = k & 1;
     const bool own = (rank == owner);
-    if (own && warp == 0) {
-      // pivot search over rows k..m-1 of column k (ties to the lowest row),
-      // then publish the column as it reads after exchanging rows k and p
-      T best = (T)-1;
-      int bi = k;
-      for (int i = k + lane; i < m; i += 32) {
-        const T v = fabs(a[i * lda + kl]);
-        if (v > best) { best = v; bi = i; }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const T ob = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      bi = __shfl_sync(0xffffffffu, bi, 0);
-      const T akk = a[k * lda + kl], apk = a[bi * lda + kl];
-      T* pb = pub + buf * kMaxM;
-      for (int i = lane; i < m; i += 32) pb[i] = (i == k) ? apk : (i == bi ? akk : a[i * lda + kl]);
-      if (lane == 0) pubp[buf] = bi;
-    }
-    cl.sync();
+    cl.sync();  // step k's pivot column is published
     const T* rb = cl.map_shared_rank(pub + buf * kMaxM, owner);
     const int pr = *cl.map_shared_rank(&pubp[buf], owner);
     const T piv = rb[k];
@@ -349,20 +351,37 @@ __global__ void __launch_bounds__(256) k_inv_cluster(const PartDesc* __restrict_
     }
     if (tid == 0) perm[k] = pr;
     __syncthreads();
-    // rank-1 update of every local column; rowk stays in registers
-    for (int jl = lane; jl < wc; jl += 32) {
-      const T rj = rowk[jl];
-      int i = warp;
-      for (; i + 3 * nwarp < m; i += 4 * nwarp) {
-        const int i1 = i + nwarp, i2 = i + 2 * nwarp, i3 = i + 3 * nwarp;
-        const T c0v = colk[i], c1v = colk[i1], c2v = colk[i2], c3v = colk[i3];
-        const T a0 = a[i * lda + jl], a1 = a[i1 * lda + jl], a2 = a[i2 * lda + jl], a3 = a[i3 * lda + jl];
-        a[i * lda + jl] = (i == k) ? rj : fma(-c0v, rj, a0);
-        a[i1 * lda + jl] = (i1 == k) ? rj : fma(-c1v, rj, a1);
-        a[i2 * lda + jl] = (i2 == k) ? rj : fma(-c2v, rj, a2);
-        a[i3 * lda + jl] = (i3 == k) ? rj : fma(-c3v, rj, a3);
+    // lookahead: the owner of column k+1 updates that column first, and its
+    // warp 0 searches and publishes step k+1's pivot column while the other
+    // warps apply the rest of step k's update
+    const int k1 = k + 1, owner1 = k1 < m ? k1 / w : -1, kl1 = k1 - owner1 * w;
+    const bool next_here = (rank == owner1);
+    if (next_here) {
+      const T rj = rowk[kl1];
+      for (int i = tid; i < m; i += nthr)
+        a[i * lda + kl1] = (i == k) ? rj : fma(-colk[i], rj, a[i * lda + kl1]);
+      __syncthreads();
+    }
+    const bool searcher = next_here && warp == 0;
+    if (searcher) search_publish(k1, kl1);
+    // rank-1 update of the local columns (column k+1 done above); rowk in registers
+    const int w0 = next_here ? 1 : 0, nw = nwarp - w0;
+    if (!searcher) {
+      for (int jl = lane; jl < wc; jl += 32) {
+        if (next_here && jl == kl1) continue;
+        const T rj = rowk[jl];
+        int i = warp - w0;
+        for (; i + 3 * nw < m; i += 4 * nw) {
+          const int i1 = i + nw, i2 = i + 2 * nw, i3 = i + 3 * nw;
+          const T c0v = colk[i], c1v = colk[i1], c2v = colk[i2], c3v = colk[i3];
+          const T a0 = a[i * lda + jl], a1 = a[i1 * lda + jl], a2 = a[i2 * lda + jl], a3 = a[i3 * lda + jl];
+          a[i * lda + jl] = (i == k) ? rj : fma(-c0v, rj, a0);
+          a[i1 * lda + jl] = (i1 == k) ? rj : fma(-c1v, rj, a1);
+          a[i2 * lda + jl] = (i2 == k) ? rj : fma(-c2v, rj, a2);
+          a[i3 * lda + jl] = (i3 == k) ? rj : fma(-c3v, rj, a3);
+        }
+        for (; i < m; i += nw) a[i * lda + jl] = (i == k) ? rj : fma(-colk[i], rj, a[i * lda + jl]);
       }
-      for (; i < m; i += nwarp) a[i * lda + jl] = (i == k) ? rj : fma(-colk[i], rj, a[i * lda + jl]);
     }
     __syncthreads();
     // column k itself becomes the k-th column of the running inverse

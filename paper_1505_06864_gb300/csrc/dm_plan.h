@@ -68,6 +68,8 @@ struct Level {
   int tc_mode = -1;   // float32 factors: -1 CUDA cores, 0 tcgen05 TF32, 1 tcgen05 split bf16
   int* d_err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
   float *A32 = nullptr, *B32 = nullptr, *C32 = nullptr;  // float32 copies streamed by the tensor-core sweeps
+  alignas(64) unsigned char tmaps[3 * 128];  // TMA tensor maps of G, A32, Acal (TF32 level, one block size)
+  bool has_tma = false;
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0

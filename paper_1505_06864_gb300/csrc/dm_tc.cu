@@ -26,10 +26,12 @@
 // chunk index XOR-ed with the row index within the atom.  Every wait on an
 // mbarrier is bounded; on expiry the kernel records an error flag, stops
 // issuing, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "dm_internal.cuh"
 
@@ -189,6 +191,21 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, uint32
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// TMA: the byte count the next phase of `bar` waits for, and one 2-D tile
+// load (box 32 x 128 float32 = one M-tile of one K-slab, 128-byte swizzle)
+// that completes on `bar`.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Left-operand K-slab `slab` of the m x m row-major float32 block L (rows
 // padded to MT * tiles, columns past m zero) into buffer `dst` (M-tile t at
 // t * tile_bytes).  TF32 with m % 4 == 0: 16-byte cp.async copies straight
@@ -293,33 +310,46 @@ __device__ __forceinline__ void stage_right(uint8_t* dst, int slab_bytes, int lo
                                             int m, int ld, int c0, int cols, float sc) {
   constexpr int KA = Fmt<MODE>::katom;
   constexpr int G = MODE == 0 ? 4 : 8;  // K values per 16-byte chunk
+  constexpr int U = 4;                  // chunks per thread with their loads in flight together
   const int kpad = ((m + KA - 1) / KA) * KA;
-  for (int e = threadIdx.x; e < (kpad / G) * NP; e += kThreads) {
-    const int kg = e / NP, n = e - kg * NP, k0 = kg * G;
-    const bool col_ok = c0 + n < cols;
-    float v[G];
+  const int items = (kpad / G) * NP;
+  for (int e0 = threadIdx.x; e0 < items; e0 += U * kThreads) {
+    float v[U][G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
-      const int k = k0 + i;
-      v[i] = (col_ok && k < m) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
-    }
-    const int slab = k0 / KA, kk = k0 - slab * KA;
-    uint8_t* p = dst + (size_t)slab * slab_bytes + sw128_off(n, kk * Fmt<MODE>::esz);
-    if (MODE == 0) {
-      *reinterpret_cast<uint4*>(p) = make_uint4(__float_as_uint(to_tf32(v[0])), __float_as_uint(to_tf32(v[1])),
-                                                __float_as_uint(to_tf32(v[2])), __float_as_uint(to_tf32(v[3])));
-    } else {
-      uint32_t hi[4], lo[4];
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kThreads;
+      const int kg = e / NP, n = e - kg * NP, k0 = kg * G;
+      const bool col_ok = e < items && c0 + n < cols;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-        hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      for (int i = 0; i < G; ++i) {
+        const int k = k0 + i;
+        v[u][i] = (col_ok && k < m) ? sc * (float)R[(long long)k * ld + c0 + n] : 0.f;
       }
-      *reinterpret_cast<uint4*>(p) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e >= items) break;
+      const int kg = e / NP, n = e - kg * NP, k0 = kg * G;
+      const int slab = k0 / KA, kk = k0 - slab * KA;
+      uint8_t* p = dst + (size_t)slab * slab_bytes + sw128_off(n, kk * Fmt<MODE>::esz);
+      if (MODE == 0) {
+        *reinterpret_cast<uint4*>(p) =
+            make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
+                       __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
+      } else {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(v[u][2 * q]), h1 = __float2bfloat16_rn(v[u][2 * q + 1]);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(v[u][2 * q] - __bfloat162float(h0));
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(v[u][2 * q + 1] - __bfloat162float(h1));
+          hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint4*>(p) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
     }
   }
 }
@@ -345,19 +375,41 @@ struct Smem {
 // wait expired.
 template <int MODE>
 __device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* lbuf0, uint8_t* right,
-                        uint64_t* bars, uint32_t (&ph)[2], uint32_t tmem, bool elect) {
+                        uint64_t* bars, uint32_t (&ph)[2], uint32_t tmem, bool elect, const CUtensorMap* tm,
+                        long long row0, uint64_t* lbars, uint32_t (&lph)[2]) {
   using S = Smem<MODE>;
   constexpr int KA = Fmt<MODE>::katom;
   constexpr int KS = Fmt<MODE>::kstep;
   constexpr uint32_t idesc = make_idesc(MODE == 0 ? 2u : 1u, MT, NP);
   const int nslab = (m + KA - 1) / KA;
+  const bool tma = (MODE == 0) && tm != nullptr;
   bool ok = true;
-  stage_left<MODE>(lbuf0, L, m, 0, tiles, S::tile_bytes, S::left_lo);
+  // stage K-slab `slab` of L into left buffer `buf`: TMA tiles (rows of the
+  // next block row past m only feed output rows that are never stored;
+  // columns past m are zero-filled) or cp.async / register copies
+  auto stage = [&](int slab, int buf) {
+    uint8_t* dstb = lbuf0 + buf * S::lbuf_bytes;
+    if (tma) {
+      if (elect) {
+        mbar_expect_tx(&lbars[buf], (uint32_t)(tiles * MT * 128));
+        for (int t = 0; t < tiles; ++t)
+          tma_load_2d(smem_u32(dstb + t * S::tile_bytes), tm, slab * KA, (int)(row0 + t * MT), &lbars[buf]);
+      }
+    } else {
+      stage_left<MODE>(dstb, L, m, slab, tiles, S::tile_bytes, S::left_lo);
+    }
+  };
+  stage(0, 0);
   for (int s = 0; s < nslab; ++s) {
     const int b = s & 1;
     uint8_t* lb = lbuf0 + b * S::lbuf_bytes;
-    cp_wait_all();  // slab s (if it was copied asynchronously) has landed
-    fence_async_shared();
+    if (tma) {
+      if (!mbar_wait(&lbars[b], lph[b])) ok = false;
+      lph[b] ^= 1u;
+    } else {
+      cp_wait_all();  // slab s (if it was copied asynchronously) has landed
+      fence_async_shared();
+    }
     if (!__syncthreads_and(ok)) return false;
     tc_fence_after();
     if (elect) {
@@ -386,7 +438,7 @@ __device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* 
         if (!mbar_wait(&bars[nb], ph[nb])) ok = false;
         ph[nb] ^= 1u;
       }
-      stage_left<MODE>(lbuf0 + nb * S::lbuf_bytes, L, m, s + 1, tiles, S::tile_bytes, S::left_lo);
+      stage(s + 1, nb);
     }
   }
   // drain: wait for the last one or two commits
@@ -418,9 +470,15 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, int tiles, int m, F&& f
 }
 
 struct TcState {
-  uint64_t bars[2];
+  uint64_t bars[2];   // MMA completion per left buffer
+  uint64_t lbars[2];  // TMA completion per left buffer
   uint32_t tmem;
   int err;
+};
+
+// Tensor maps of a level's float32 arrays (one 2-D view [rows][m] each).
+struct __align__(64) TmaMaps {
+  CUtensorMap G, A, Acal;
 };
 
 template <int MODE>
@@ -437,6 +495,8 @@ __device__ __forceinline__ void tc_setup(TcState* st, int ncols) {
   if (threadIdx.x == 0) {
     mbar_init(&st->bars[0], 1);
     mbar_init(&st->bars[1], 1);
+    mbar_init(&st->lbars[0], 1);
+    mbar_init(&st->lbars[1], 1);
     st->err = 0;
     fence_mbar_init();
   }
@@ -469,7 +529,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
                                                             const float* __restrict__ B,
                                                             const float* __restrict__ C, float* __restrict__ G,
                                                             float* __restrict__ Acal, float* __restrict__ ZL,
-                                                            float* __restrict__ ZR, int* __restrict__ errflag) {
+                                                            float* __restrict__ ZR, int* __restrict__ errflag,
+                                                            const __grid_constant__ TmaMaps tmaps, int use_tma) {
   using S = Smem<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ TcState st;
@@ -486,16 +547,18 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
   const int tiles = (m + MT - 1) / MT;
   const int ncols = tmem_cols(tiles);
   tc_setup(&st, ncols);
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t ph[2] = {0u, 0u}, lph[2] = {0u, 0u};
   const bool elect = threadIdx.x == 0;
   const long long mm = (long long)m * m;
   const long long o = p.blk + (long long)t * mm;
+  const CUtensorMap* tG = use_tma ? &tmaps.G : nullptr;
+  const CUtensorMap* tA = use_tma ? &tmaps.A : nullptr;
   bool ok = true;
   if (type == 0) {
     stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, C + o, m, m, c0, m, 1.f);
     fence_async_shared();
     __syncthreads();
-    ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph);
     if (ok) {
       float* dst = last ? ZR + o : Acal + o;
       // result to global, and (not last) transposed into `right` for the next product
@@ -513,7 +576,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        ok = product<MODE>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+        ok = product<MODE>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tA, (o + mm) / m,
+                           st.lbars, lph);
         if (ok) {
           const float* Bn = B + o + mm;
           float* Dn = G + o + mm;
@@ -533,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
       stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, ZL + o - mm, m, m, c0, m, 1.f);
       fence_async_shared();
       __syncthreads();
-      ok = product<MODE>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+      ok = product<MODE>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tA, o / m, st.lbars, lph);
       if (ok) {
         tc_fence_before();
         __syncthreads();
@@ -547,7 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (ok) ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect);
+    if (ok) ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph);
     if (ok) {
       float* dst = ZL + o;
       drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -563,7 +627,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __restrict__ parts, int s, int tiles_n,
                                                              const float* __restrict__ Acal, float* __restrict__ ZL,
-                                                             float* __restrict__ ZR, int* __restrict__ errflag) {
+                                                             float* __restrict__ ZR, int* __restrict__ errflag,
+                                                             const __grid_constant__ TmaMaps tmaps, int use_tma) {
   using S = Smem<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ TcState st;
@@ -580,14 +645,15 @@ __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __r
   const int tiles = (m + MT - 1) / MT;
   const int ncols = tmem_cols(tiles);
   tc_setup(&st, ncols);
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t ph[2] = {0u, 0u}, lph[2] = {0u, 0u};
   const long long mm = (long long)m * m;
   const long long o = p.blk + (long long)t * mm;
   float* Y = (type == 0 ? ZL : ZR) + o;
   stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, Y + mm, m, m, c0, m, 1.f);
   fence_async_shared();
   __syncthreads();
-  bool ok = product<MODE>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0);
+  bool ok = product<MODE>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0,
+                         use_tma ? &tmaps.Acal : nullptr, o / m, st.lbars, lph);
   if (ok) {
     const bool keep = (type == 0);
     drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -617,36 +683,44 @@ bool g_set_fwd[2], g_set_back[2];
 
 void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const float* A,
                           const float* B, const float* C, float* G, float* Acal, float* ZL, float* ZR,
-                          int* errflag, cudaStream_t st, int type_lo, int type_hi) {
+                          int* errflag, cudaStream_t st, int type_lo, int type_hi, const void* tmaps) {
   if (nparts <= 0 || type_hi <= type_lo) return;
+  tc::TmaMaps tm;
+  std::memset(&tm, 0, sizeof tm);
+  if (tmaps) std::memcpy(&tm, tmaps, sizeof tm);
+  const int use_tma = (tmaps != nullptr && mode == 0) ? 1 : 0;
   const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
   const dim3 grid((type_hi - type_lo) * tiles_n, nparts);
   if (mode == 0) {
     const int bytes = tc::Smem<0>::total;
     raise_smem_once(tc::k_fwd_factor_tc<0>, bytes, &g_set_fwd[0]);
     tc::k_fwd_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
-                                                              errflag);
+                                                              errflag, tm, use_tma);
   } else {
     const int bytes = tc::Smem<1>::total;
     raise_smem_once(tc::k_fwd_factor_tc<1>, bytes, &g_set_fwd[1]);
     tc::k_fwd_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
-                                                              errflag);
+                                                              errflag, tm, 0);
   }
 }
 
 void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, int max_m, const float* Acal,
-                           float* ZL, float* ZR, int* errflag, cudaStream_t st) {
+                           float* ZL, float* ZR, int* errflag, cudaStream_t st, const void* tmaps) {
   if (nparts <= 0) return;
+  tc::TmaMaps tm;
+  std::memset(&tm, 0, sizeof tm);
+  if (tmaps) std::memcpy(&tm, tmaps, sizeof tm);
+  const int use_tma = (tmaps != nullptr && mode == 0) ? 1 : 0;
   const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
   const dim3 grid(2 * tiles_n, nparts);
   if (mode == 0) {
     const int bytes = tc::Smem<0>::total;
     raise_smem_once(tc::k_back_factor_tc<0>, bytes, &g_set_back[0]);
-    tc::k_back_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag);
+    tc::k_back_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, use_tma);
   } else {
     const int bytes = tc::Smem<1>::total;
     raise_smem_once(tc::k_back_factor_tc<1>, bytes, &g_set_back[1]);
-    tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag);
+    tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, 0);
   }
 }
 
@@ -667,6 +741,45 @@ void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) 
   int sms = 152;
   k_to_f32<<<sms * 4, 256, 0, st>>>(src, dst, n);
 }
+
+// 2-D tensor maps ([rows][m] float32, box 32 x 128, 128-byte swizzle, zero
+// fill past the extent) of the three arrays the TF32 sweeps stream as left
+// operands.  Returns false when the driver entry point is unavailable or m is
+// not a multiple of 4 (row pitch must be a multiple of 16 bytes).
+bool make_tma_maps(const float* G, const float* A32, const float* Acal, long long rows, int m, void* out) {
+  if (m % 4 != 0 || rows <= 0) return false;
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    enc = reinterpret_cast<Encode>(fn);
+  }
+  tc::TmaMaps tm;
+  std::memset(&tm, 0, sizeof tm);
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)m * sizeof(float)};
+  const cuuint32_t box[2] = {32, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const float* src[3] = {G, A32, Acal};
+  CUtensorMap* dst[3] = {&tm.G, &tm.A, &tm.Acal};
+  for (int i = 0; i < 3; ++i)
+    if (enc(dst[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(src[i]), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  std::memcpy(out, &tm, sizeof tm);
+  return true;
+}
+
+int tma_maps_bytes() { return (int)sizeof(tc::TmaMaps); }
 
 int tc_smem_bytes(int mode) { return mode == 0 ? tc::Smem<0>::total : tc::Smem<1>::total; }
 
