@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--N", type=int, default=2048, help="block rows (smaller cases for profiler captures)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"],
                     help="factor precision of the timed path (mixed ones refine in float64)")
-    ap.add_argument("--workload", default="pde", choices=["pde", "precision", "batch", "serve"],
+    ap.add_argument("--workload", default="pde", choices=["pde", "precision", "batch", "serve", "paper"],
                     help="pde: the benchmark line (default); precision / batch / serve: the "
                          "conditioned-block, batched and served workloads, one JSON line each")
     ap.add_argument("--seconds", type=float, default=2.0, help="serve: length of the arrival stream")
@@ -169,7 +169,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "pde":
-        return {"precision": run_precision, "batch": run_batch, "serve": run_serve}[args.workload](args)
+        return {"precision": run_precision, "batch": run_batch, "serve": run_serve,
+                "paper": run_paper}[args.workload](args)
     import torch
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -585,6 +586,47 @@ def run_serve(args):
             "config": {"workload": "Poisson 2000 req/s; pool of 48 systems of the batch mix + 2 of N=8192 m=256; "
                                    "5 % large, 30 % repeat right-hand side; bf16x3 + fp64 refinement",
                        "seconds": args.seconds, "slots": 8}}
+    print(json.dumps(line), flush=True)
+
+
+def run_paper(args):
+    """The paper's validation shape (Section 6): N = 3071 blocks, n = 100 and
+    400, one right-hand side, Laplace blocks with small random fill, float64.
+    Measured speedup of DM over block Thomas (P = 1) on the GPU against the
+    analytical speedup of Eq. (SpeedupMP) for the same P."""
+    import math
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_06864_gb300 import dm, workloads as w
+    N = 3071
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    out = {}
+    for m in (100, 400):
+        s = w.laplace_fill_system(N, m, 1, 6)
+        A, B, C, b = (torch.from_numpy(v).to(dev) for v in (s.A, s.B, s.C, s.b))
+        x = torch.empty_like(b)
+        rows = []
+        t1 = None
+        for P in (1, 4, 16, 32, 48, 64, 85, 128):
+            plan = dm.dm_plan(N, m, 1, P, 1, "fp64")
+            dm.dm_set_stream(plan, stream)
+            ms, rel = _timed_steps(dm, plan, A, B, C, b, x, 1, 1, stream, False)
+            dm.dm_destroy(plan)
+            if P == 1:
+                t1 = ms
+            c = 5.0 + 2.0 / (1.0 + 1.0 / m)
+            s_model = (3 * N - 2) / (3 * P - 5 + c * (N - P + 1) / P) if P > 1 else 1.0
+            rows.append({"P": P, "ms": ms, "speedup_vs_ta": t1 / ms, "speedup_model": s_model, "relres": rel,
+                         "rel_err_vs_xtrue": rel_err(x.cpu().numpy(), s.x_true)})
+        out[f"n={m}"] = rows
+        del A, B, C, b, x
+        torch.cuda.empty_cache()
+    line = {"metric": "speedup of DM over block Thomas", "workload": "paper", "unit": "x", "n_gpus": 1,
+            "data": "synthetic", "config": {"workload": "Laplace blocks with random fill (eps 1e-2), N=3071, "
+                                                        "n in {100, 400}, l=1, float64, levels=1"},
+            "results": out}
     print(json.dumps(line), flush=True)
 
 

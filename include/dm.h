@@ -93,6 +93,19 @@ typedef struct dm_plan_info {
  * inputs, see dm_set_borrow_inputs).  *out is set only on success. */
 int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision);
 
+/* dm_plan with flags.  DM_PLAN_EQUAL_TIME sizes the subsystems for equal
+ * operation counts (Section 5.1, second case; sizes from Table 2): the first
+ * and last subsystems longer than the middle ones (about 7/4 and 7/6 of them
+ * for nrhs << m).  On the GPU every step of all subsystems is one launch, so
+ * the longest subsystem sets the step count: equal sizes (flags = 0) are
+ * normally faster there. */
+#define DM_PLAN_EQUAL_TIME 1
+int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags);
+
+/* Subsystem sizes (rows, in order) a plan with these arguments uses; host
+ * only.  `lengths` receives P values (P = the effective P: 0 = the tuner's). */
+int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths);
+
 /* Plan `count` independent systems (sizes N[s], m[s], nrhs[s]) that are
  * factored and solved together, every stage of all systems in the same
  * launches.  Partition counts and recursion depth are chosen per system by

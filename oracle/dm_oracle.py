@@ -24,6 +24,7 @@ paper's multiplicative-operation counts exactly.
 
 Functions and the passages they follow:
     partition_plan   Section 2 (choice of the M-1 separator block-rows)
+    partition_lengths_equal_time   Section 5.1 (equal execution time, Table 2)
     ta_factor/ta_solve/thomas   Section 3 (Thomas algorithm, forward and backward sweeps)
     dm               Section 2, Eqs. (e220)-(endSolution); recursion on the
                      supplementary system as in Section 4.2.1
@@ -158,6 +159,52 @@ def partition_plan(N: int, P: int):
     return starts, lengths, seps
 
 
+def partition_lengths_equal_time(N: int, P: int, n: int, l: int):
+    """Subsystem sizes with equal operation counts (Section 5.1, second case):
+    from Table 2, a middle subsystem of N_k rows costs N_k (7n^3 + 5n^2 l), the
+    first (4N_1 - 1)(n^3 + n^2 l) and the last (6N_M - 3)n^3 + (4N_M - 1)n^2 l.
+    Equating them gives N_1 = a1 N_k + b1 and N_M = a2 N_k + b2; the size
+    constraint N_1 + N_M + (P - 2) N_k = N - P + 1 fixes N_k.  Rounding
+    (reading): N_1 and N_M to the nearest integer (halves up), the middle
+    subsystems share the remaining rows equally, remainder to the lowest ones;
+    equal sizes when a subsystem would be left empty."""
+    if P < 1 or (P > 1 and 2 * P - 1 > N):
+        raise ValueError(f"invalid partition: N={N}, P={P}")
+    if P == 1:
+        return [N]
+    rows = N - P + 1
+    c = 7.0 * n ** 3 + 5.0 * n ** 2 * l
+    a1, b1 = c / (4.0 * n ** 3 + 4.0 * n ** 2 * l), 0.25
+    a2 = c / (6.0 * n ** 3 + 4.0 * n ** 2 * l)
+    b2 = (3.0 * n ** 3 + n ** 2 * l) / (6.0 * n ** 3 + 4.0 * n ** 2 * l)
+    nk = (rows - b1 - b2) / (a1 + a2 + P - 2)
+    n1 = int(math.floor(a1 * nk + b1 + 0.5))
+    nm = int(math.floor(a2 * nk + b2 + 0.5))
+    mid = rows - n1 - nm
+    if n1 < 1 or nm < 1 or (P > 2 and mid < P - 2) or (P == 2 and mid != 0):
+        if P == 2 and n1 >= 1 and rows - n1 >= 1:
+            return [n1, rows - n1]
+        _, L, _ = partition_plan(N, P)
+        return L
+    if P == 2:
+        return [n1, nm]
+    base, extra = divmod(mid, P - 2)
+    return [n1] + [base + (1 if k < extra else 0) for k in range(P - 2)] + [nm]
+
+
+def plan_from_lengths(lengths):
+    """(starts, lengths, seps) for subsystems of the given sizes, separator k
+    right after subsystem k."""
+    starts, seps, r = [], [], 0
+    for k, L in enumerate(lengths):
+        starts.append(r)
+        r += L
+        if k < len(lengths) - 1:
+            seps.append(r)
+            r += 1
+    return starts, list(lengths), seps
+
+
 # --------------------------------------------------------------------------
 # Thomas algorithm (Section 3)
 # --------------------------------------------------------------------------
@@ -225,7 +272,7 @@ def supp_partitions(Ms: int, P: int, l: int, m: int):
     return max(p2, 1)
 
 
-def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False):
+def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=None):
     """Solve A_i X_{i-1} + B_i X_i + C_i X_{i+1} = F_i by the decomposition
     method with P subsystems (Section 2).
 
@@ -239,7 +286,11 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False):
     if P == 1:
         with ctr.stage("ta"):
             return thomas(A, B, C, F, ctr)
-    starts, lengths, seps = partition_plan(N, P)
+    if lengths is None:
+        starts, lengths, seps = partition_plan(N, P)
+    else:
+        assert len(lengths) == P and sum(lengths) == N - P + 1 and min(lengths) >= 1
+        starts, lengths, seps = plan_from_lengths(lengths)
 
     # Eq. (e231): S^k Z^k = W_R^k and S^k z^k = F_s^k for every subsystem.
     # S^k is the block-tridiagonal matrix of subsystem k's rows with the

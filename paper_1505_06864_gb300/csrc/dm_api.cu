@@ -108,7 +108,15 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     sd.pad = 0;
     sysd.push_back(sd);
     std::vector<int> starts, lens, sepr;
-    partition_plan(sp.N, sp.P, starts, lens, sepr);
+    partition_lengths(sp.N, sp.P, sp.m, sp.r, sp.flags, lens);
+    {
+      int r0 = 0;
+      for (int k = 0; k < sp.P; ++k) {
+        starts.push_back(r0);
+        r0 += lens[k];
+        if (k < sp.P - 1) sepr.push_back(r0++);
+      }
+    }
     const long long mm = (long long)sp.m * sp.m, mr = (long long)sp.m * sp.r;
     for (int k = 0; k < sp.P; ++k) {
       PartDesc pd;
@@ -823,6 +831,34 @@ void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& le
   }
 }
 
+// Subsystem sizes: equal (remainder to the lowest subsystems), or with
+// DM_PLAN_EQUAL_TIME equal operation counts per subsystem (Section 5.1, from
+// Table 2: first N_1 = a1 N_k + 1/4, last N_M = a2 N_k + b2, middle N_k).
+void partition_lengths(int N, int P, int m, int r, int flags, std::vector<int>& lens) {
+  std::vector<int> st, sp;
+  partition_plan(N, P, st, lens, sp);
+  if (!(flags & DM_PLAN_EQUAL_TIME) || P < 2) return;
+  const double n3 = (double)m * m * m, n2l = (double)m * m * r;
+  const double c = 7.0 * n3 + 5.0 * n2l;
+  const double a1 = c / (4.0 * n3 + 4.0 * n2l), b1 = 0.25;
+  const double a2 = c / (6.0 * n3 + 4.0 * n2l), b2 = (3.0 * n3 + n2l) / (6.0 * n3 + 4.0 * n2l);
+  const int rows = N - P + 1;
+  const double nk = (rows - b1 - b2) / (a1 + a2 + P - 2);
+  const int n1 = (int)std::floor(a1 * nk + b1 + 0.5), nm = (int)std::floor(a2 * nk + b2 + 0.5);
+  const int mid = rows - n1 - nm;
+  if (n1 < 1 || nm < 1 || (P > 2 && mid < P - 2) || (P == 2 && mid != 0)) {
+    if (P == 2 && n1 >= 1 && rows - n1 >= 1) lens = {n1, rows - n1};
+    return;  // else keep equal sizes
+  }
+  lens.assign(P, 0);
+  lens[0] = n1;
+  lens[P - 1] = nm;
+  if (P > 2) {
+    const int base = mid / (P - 2), extra = mid % (P - 2);
+    for (int k = 0; k < P - 2; ++k) lens[1 + k] = base + (k < extra ? 1 : 0);
+  }
+}
+
 // Eq. (MAXSpeedP): P* = sqrt((N+1)/3 (5 + 2/(1 + l/n))), clamped to 1..(N+1)/2.
 int tuner_seed_p(int N, int m, int r) {
   const double c = 5.0 + 2.0 / (1.0 + (double)r / m);
@@ -876,7 +912,24 @@ extern "C" {
 const char* dm_last_error(void) { return g_last_error.c_str(); }
 
 int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision) {
+  return dm_plan_ex(out, N, m, nrhs, P, levels, precision, 0);
+}
+
+int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths) {
+  if (!lengths) return set_error(DM_EINVAL, "NULL lengths");
+  if (flags & ~DM_PLAN_EQUAL_TIME) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
+  SysSpec s;
+  int rc = make_spec(N, m, nrhs, P, 1, &s);
+  if (rc) return rc;
+  std::vector<int> L;
+  partition_lengths(N, s.P, m, nrhs, flags, L);
+  for (int k = 0; k < s.P; ++k) lengths[k] = L[k];
+  return DM_OK;
+}
+
+int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags) {
   if (!out) return set_error(DM_EINVAL, "out is NULL");
+  if (flags & ~DM_PLAN_EQUAL_TIME) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
   if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
     return set_error(DM_EINVAL, "unknown precision %d", precision);
   if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)
@@ -885,6 +938,7 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, levels, &s);
   if (rc) return rc;
+  s.flags = flags;
   std::unique_ptr<dm_plan_s> p(new dm_plan_s());
   rc = p->plan.init(std::vector<SysSpec>{s}, precision);
   if (rc) return rc;

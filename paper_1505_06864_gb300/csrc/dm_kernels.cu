@@ -717,20 +717,27 @@ __device__ __forceinline__ void narrow_mm(int m, const TL1* __restrict__ L1, con
     T acc[RM];
 #pragma unroll
     for (int c = 0; c < RM; ++c) acc[c] = (T)0;
-    const TL1* l1 = L1 + (long long)i * m;
-    for (int k = lane; k < m; k += 32) {
-      const T lv = (T)l1[k];
+    // 4 independent loads of the row in flight per lane before their FMAs
+    auto row_dot = [&](const auto* __restrict__ l, const T* __restrict__ R) {
+      int k = lane;
+      for (; k + 96 < m; k += 128) {
+        const T l0 = (T)l[k], l1 = (T)l[k + 32], l2 = (T)l[k + 64], l3 = (T)l[k + 96];
 #pragma unroll
-      for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R1[k * RM + c], acc[c]);
-    }
-    if (L2 != nullptr) {
-      const TL2* l2 = L2 + (long long)i * m;
-      for (int k = lane; k < m; k += 32) {
-        const T lv = (T)l2[k];
-#pragma unroll
-        for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R2[k * RM + c], acc[c]);
+        for (int c = 0; c < RM; ++c) {
+          acc[c] = fma(l0, R[k * RM + c], acc[c]);
+          acc[c] = fma(l1, R[(k + 32) * RM + c], acc[c]);
+          acc[c] = fma(l2, R[(k + 64) * RM + c], acc[c]);
+          acc[c] = fma(l3, R[(k + 96) * RM + c], acc[c]);
+        }
       }
-    }
+      for (; k < m; k += 32) {
+        const T lv = (T)l[k];
+#pragma unroll
+        for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R[k * RM + c], acc[c]);
+      }
+    };
+    row_dot(L1 + (long long)i * m, R1);
+    if (L2 != nullptr) row_dot(L2 + (long long)i * m, R2);
 #pragma unroll
     for (int c = 0; c < RM; ++c) {
       T v = acc[c];
@@ -1027,15 +1034,52 @@ bool narrow_dispatch(int max_r, F&& f) {
 }
 
 template <typename T>
+size_t inv_cluster_smem(int max_m, int cs) {
+  const int w = (max_m + cs - 1) / cs;
+  return sizeof(T) * (3 * (size_t)kMaxM + 128 + (size_t)max_m * (w + 1)) + 3 * kMaxM * sizeof(int);
+}
+
+template <typename T>
 int inv_cluster_size(int max_m) {
-  // float64: ~32 columns per CTA so the FP64 pipes of cs SMs share a block;
+  // float64: ~32 columns per CTA so the FP64 pipes of cs SMs share a block
+  // (up to 64 columns when that keeps the cluster at the portable 8 CTAs);
   // float32: one CTA up to m = 128, else 64 columns per CTA (the update is
-// cheap, barriers dominate).
+  // cheap, barriers dominate).
   if (sizeof(T) == 4 && max_m <= 128) return 1;
   const int per = sizeof(T) == 8 ? 32 : 64;
   int cs = 1;
   while (cs * per < max_m) cs *= 2;
+  if (cs > 8 && inv_cluster_smem<T>(max_m, 8) <= 227 * 1024 && (max_m + 7) / 8 <= 128) cs = 8;
   return cs;
+}
+
+// Whether a cluster of cs CTAs with `bytes` of shared memory each can run.
+template <typename T>
+bool inv_cluster_ok(int cs, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<long long, bool> known;
+  const long long key = (long long)cs * (1ll << 32) + (long long)bytes;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find(key);
+  if (it != known.end()) return it->second;
+  if (cs > 8) cudaFuncSetAttribute(k_inv_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  allow_smem(k_inv_cluster<T>, bytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_inv_cluster<T>, &cfg) == cudaSuccess && nclusters > 0;
+  cudaGetLastError();
+  known[key] = ok;
+  return ok;
 }
 
 template <typename T>
@@ -1043,9 +1087,8 @@ void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G,
                 int max_m, cudaStream_t st) {
   if (nparts <= 0) return;
   const int cs = inv_cluster_size<T>(max_m);
-  if (cs <= 8) {
-    const int w = (max_m + cs - 1) / cs;
-    const size_t bytes = sizeof(T) * (3 * (size_t)kMaxM + 128 + (size_t)max_m * (w + 1)) + 3 * kMaxM * sizeof(int);
+  const size_t bytes = inv_cluster_smem<T>(max_m, cs);
+  if (cs <= 16 && bytes <= 227 * 1024 && (cs <= 8 || inv_cluster_ok<T>(cs, bytes))) {
     allow_smem(k_inv_cluster<T>, bytes);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nparts * cs);
@@ -1062,15 +1105,15 @@ void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G,
     cudaLaunchKernelEx(&cfg, k_inv_cluster<T>, parts, t, B, G, status, cs);
     return;
   }
-  // float64 blocks above m = 256: one CTA per block, working matrix in global memory
+  // no cluster fits: one CTA per block, working matrix in global memory
   const int smax = inv_smem_max_m<T>();
   const size_t base = 2 * kMaxM * sizeof(int) + 2 * kMaxM * sizeof(T);
-  const size_t bytes = base + (max_m <= smax ? (size_t)max_m * (max_m + 1) * sizeof(T) : 0);
-  allow_smem(k_inv<T>, bytes);
+  const size_t gbytes = base + (max_m <= smax ? (size_t)max_m * (max_m + 1) * sizeof(T) : 0);
+  allow_smem(k_inv<T>, gbytes);
   const int thr = max_m >= 128 ? 512 : (max_m >= 48 ? 256 : 128);
   // capacity actually allocated: every block up to max_m fits, or none does
   const int cap = max_m <= smax ? max_m : 0;
-  k_inv<T><<<nparts, thr, bytes, st>>>(parts, t, B, G, status, cap);
+  k_inv<T><<<nparts, thr, gbytes, st>>>(parts, t, B, G, status, cap);
 }
 
 template <typename T>

@@ -59,6 +59,7 @@ struct SysSpec {
   int P = 1;       // subsystems (the paper's M)
   int levels = 1;  // 1: supplementary system by block Thomas; L > 1: by DM, L-1 levels
   int P2 = 1;      // subsystems of the supplementary system when levels > 1
+  int flags = 0;   // DM_PLAN_* (subsystem sizing)
 };
 
 // One level of the recursion: a set of independent systems, each split into
@@ -147,6 +148,7 @@ struct Plan {
 
 int set_error(int code, const char* fmt, ...);
 void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps);
+void partition_lengths(int N, int P, int m, int r, int flags, std::vector<int>& lens);
 int tuner_seed_p(int N, int m, int r);
 int supp_partitions(int Ms, int P, int r, int m);
 int make_spec(int N, int m, int r, int P, int levels, SysSpec* out);

@@ -64,6 +64,8 @@ def lib():
             "dm_plan_batch": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I),
                                   ctypes.POINTER(I), I]),
             "dm_plan_tune": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "dm_plan_ex": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I]),
+            "dm_partition_sizes": (I, [I, I, I, I, I, ctypes.POINTER(I)]),
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
@@ -124,6 +126,26 @@ def dm_plan(N, m, nrhs, P=0, levels=0, precision=DM_FP64):
     h = ctypes.c_void_p()
     _check(lib().dm_plan(ctypes.byref(h), int(N), int(m), int(nrhs), int(P), int(levels), int(precision)))
     return h
+
+
+DM_PLAN_EQUAL_TIME = 1
+
+
+def dm_plan_ex(N, m, nrhs, P=0, levels=0, precision=DM_FP64, flags=0):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = ctypes.c_void_p()
+    _check(lib().dm_plan_ex(ctypes.byref(h), int(N), int(m), int(nrhs), int(P), int(levels), int(precision),
+                            int(flags)))
+    return h
+
+
+def dm_partition_sizes(N, m, nrhs, P, flags=0):
+    """Subsystem sizes the planner uses (host only)."""
+    Pe = dm_plan_tune(N, m, nrhs, P, 1)[0]
+    out = (ctypes.c_int * Pe)()
+    _check(lib().dm_partition_sizes(int(N), int(m), int(nrhs), int(P), int(flags), out))
+    return list(out)
 
 
 def dm_plan_batch(Ns, ms, rs, precision=DM_FP64):

@@ -32,6 +32,9 @@ Workload recipes (one function each):
   B_i = U_i diag(sigma) V_i^T with U_i, V_i orthogonal (QR of Gaussian
   matrices) and sigma log-spaced in [1, cond]; A_i, C_i uniform in [-1, 1],
   each scaled to Frobenius norm 0.25 so ||A_i||_2 + ||C_i||_2 <= 0.5 sigma_min.
+* ``laplace_fill_system`` -- the 5-point 2-D Laplace operator (blocks
+  tridiag(-1, 4, -1) and -I) with its zero entries filled by small uniform
+  values, the shape of the paper's validation matrices.
 * ``batch_shapes`` -- shapes of a batch of independent systems: N uniform in
   [n_lo, n_hi], m drawn from a set, nrhs uniform in [r_lo, r_hi].
 """
@@ -172,6 +175,27 @@ def pde_banded_system(N: int, m: int, nrhs: int, seed: int, hb: int = 3) -> Syst
     x = normal(seed, STREAM_X, N * m * nrhs).reshape(N, m, nrhs)
     return System(A, B, C, manufacture_rhs(A, B, C, x), x,
                   f"pde-banded N={N} m={m} nrhs={nrhs} hb={hb} seed={seed}")
+
+
+def laplace_fill_system(N: int, m: int, nrhs: int, seed: int, eps: float = 1e-2) -> System:
+    """Five-point 2-D Laplace operator on an N x m grid (blocks: B_i =
+    tridiag(-1, 4, -1), A_i = C_i = -I), every block's zero entries filled
+    with uniform [-eps, eps] values -- the shape of the paper's validation
+    matrices (Laplace discretisation with small random fill)."""
+    A = eps * uniform(seed, STREAM_A, N * m * m, -1.0, 1.0).reshape(N, m, m)
+    B = eps * uniform(seed, STREAM_B, N * m * m, -1.0, 1.0).reshape(N, m, m)
+    C = eps * uniform(seed, STREAM_C, N * m * m, -1.0, 1.0).reshape(N, m, m)
+    idx = np.arange(m)
+    A[:, idx, idx] = -1.0
+    C[:, idx, idx] = -1.0
+    B[:, idx, idx] = 4.0
+    B[:, idx[1:], idx[:-1]] = -1.0
+    B[:, idx[:-1], idx[1:]] = -1.0
+    A[0] = 0.0
+    C[N - 1] = 0.0
+    x = normal(seed, STREAM_X, N * m * nrhs).reshape(N, m, nrhs)
+    return System(A, B, C, manufacture_rhs(A, B, C, x), x,
+                  f"laplace-fill N={N} m={m} nrhs={nrhs} eps={eps:g} seed={seed}")
 
 
 def conditioned_system(N: int, m: int, nrhs: int, seed: int, cond: float = 1e4) -> System:

@@ -70,3 +70,12 @@ def test_tuner_seed_is_paper_optimum(dm):
 def o_supp(P, r, m):
     from oracle import dm_oracle as o
     return o.supp_partitions(P - 1, P, r, m)
+
+
+def test_partition_sizes_match_oracle(dm):
+    from oracle import dm_oracle as o
+    for N, P, m, r in [(2048, 64, 256, 1), (3071, 64, 400, 1), (100, 5, 8, 1), (20, 9, 4, 2), (10, 2, 3, 1),
+                       (40, 13, 5, 5), (1, 1, 4, 1)]:
+        assert dm.dm_partition_sizes(N, m, r, P) == o.partition_plan(N, P)[1]
+        assert dm.dm_partition_sizes(N, m, r, P, dm.DM_PLAN_EQUAL_TIME) == \
+            o.partition_lengths_equal_time(N, P, m, r)

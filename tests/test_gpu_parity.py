@@ -310,3 +310,26 @@ def test_autotune_choice_used_by_plan(dm):
         check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=q["P2"] if q["P2"] > 1 else None), TOL64)
     finally:
         dm.dm_destroy(plan)
+
+
+def test_equal_time_partitions(dm):
+    s = w.dominant_system(200, 24, 2, 71)
+    L = o.partition_lengths_equal_time(200, 9, 24, 2)
+    assert L[0] > L[1]
+    plan = dm.dm_plan_ex(200, 24, 2, 9, 1, "fp64", dm.DM_PLAN_EQUAL_TIME)
+    try:
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        x = np.zeros_like(s.b)
+        dm.dm_solve(plan, s.b, x)
+        assert dm.dm_plan_query(plan)["max_rows"] == max(L)
+    finally:
+        dm.dm_destroy(plan)
+    check(x, o.dm(s.A, s.B, s.C, s.b, 9, lengths=L), TOL64)
+
+
+def test_laplace_fill_paper_shape_small(dm):
+    """The paper's validation matrices (2-D Laplace blocks with small random
+    fill), m above the tensor-core limit, float64."""
+    s = w.laplace_fill_system(40, 300, 1, 3)
+    x, rel, _ = solve(dm, s, 6, 1)
+    check(x, o.dm(s.A, s.B, s.C, s.b, 6), TOL64)

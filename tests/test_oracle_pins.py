@@ -359,3 +359,35 @@ def test_device_generator_bit_identical_uniforms():
     np.testing.assert_array_equal(s.A, A.numpy())
     np.testing.assert_array_equal(s.B, B.numpy())     # same draws and same shift summation order
     np.testing.assert_allclose(s.x_true, x.numpy(), rtol=1e-13)
+
+
+# ---------------------------------------------------------------- equal-time subsystems (Section 5.1)
+def _per_subsystem_counts(Ls, n, l):
+    M = len(Ls)
+    return [o.mo_dm_solve(k + 1, M, Ls[k], n, l) + o.mo_dm_wing(k + 1, M, n, l) + o.mo_dm_back(k + 1, M, Ls[k], n, l)
+            for k in range(M)]
+
+
+@pytest.mark.parametrize("N,P,n,l", [(2048, 64, 256, 1), (3071, 64, 400, 1), (3071, 16, 100, 1), (500, 7, 50, 50)])
+def test_equal_time_sizes_balance_table2(N, P, n, l):
+    L = o.partition_lengths_equal_time(N, P, n, l)
+    assert len(L) == P and sum(L) == N - P + 1 and min(L) >= 1
+    c = _per_subsystem_counts(L, n, l)
+    ce = _per_subsystem_counts(o.partition_plan(N, P)[1], n, l)
+    row = 7 * n ** 3 + 5 * n ** 2 * l          # one middle row's count
+    assert max(c) - min(c) <= 2 * row           # balanced to within rounding of a row or two
+    assert max(ce) - min(ce) > max(c) - min(c)  # better balanced than equal sizes
+    # the enlargement of the first and last subsystems approaches 7/4 and 7/6 (Section 5.1)
+    if l * 100 < n:
+        mid = L[P // 2]
+        assert abs(L[0] / mid - 7 / 4) < 0.15 and abs(L[-1] / mid - 7 / 6) < 0.15
+
+
+def test_dm_with_equal_time_sizes_matches_dense():
+    s = w.dominant_system(40, 3, 2, 31)
+    L = o.partition_lengths_equal_time(40, 5, 3, 2)
+    xd = o.dense_ge(o.dense_from_blocks(s.A, s.B, s.C), s.b.reshape(-1, 2)).reshape(40, 3, 2)
+    assert o.rel_err(o.dm(s.A, s.B, s.C, s.b, 5, lengths=L), xd) < 1e-13
+    ctr = o.OpCounter()
+    o.dm(s.A, s.B, s.C, s.b, 5, lengths=L, ctr=ctr)
+    assert ctr.total() == o.mo_dm_total(L, 3, 2)
