@@ -174,6 +174,14 @@ int dm_poll_times(uint64_t ticket, int* status, double* relres_out, double* time
 /* Number of serving worker streams (1..64); only before the first submit. */
 int dm_serve_slots(int slots);
 
+/* The application case of the paper's Section 7: the right-hand side is zero
+ * except its last block row b_N ([m][nrhs]) and only x_N ([m][nrhs]) is
+ * wanted.  Every subsystem's z vanishes except the last one's, whose forward
+ * sweep is a single step; only the last separator's supplementary right-hand
+ * side is non-zero; x_N = z_N - Z_L h (Eqs. e2311, endSolution).  Float64
+ * single-system plans only (DM_EINVAL otherwise); no residual is computed. */
+int dm_solve_last(dm_plan_t plan, const double* b_last, double* x_last);
+
 /* The decomposition dm_plan would choose for P = 0 / levels = 0 (the tuner's
  * seed: P from Eq. (MAXSpeedP), recursion from the P >= 21 condition after
  * Eq. (SuppMatrM), P2 from Eq. (SuppMatrM)).  Host only: allocates nothing and

@@ -160,6 +160,9 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
                    [](const PartDesc& a, const PartDesc& b) { return a.L > b.L; });
   nparts = (int)parts.size();
   nseps = (int)seps.size();
+  last_part.assign(nsys, -1);
+  for (int i = 0; i < nparts; ++i)
+    if (!(parts[i].flags & HAS_RIGHT)) last_part[parts[i].sys] = i;
   Lmax = nparts ? parts[0].L : 0;
   active_fwd.assign(std::max(Lmax, 1), 0);
   for (int t = 0; t < Lmax; ++t) {
@@ -813,6 +816,46 @@ int Plan::solve(const double* b, double* x, double* relres_out) {
   return rc;
 }
 
+// Last block row only (the application case: b is zero except its last block
+// row, only x_N is wanted).  Every z^k vanishes but the last subsystem's,
+// whose forward sweep is one step (z_{L-1} = G_{L-1} b_N); its backward sweep
+// gives z^{P}[first] for the one non-zero supplementary right-hand side
+// fh_{P-1} = -C_q z^{P}[first] (Eq. e2311); after the supplementary solve,
+// x_N = z_{L-1} - ZL_{L-1} h_{P-1} (Eq. endSolution).
+int Plan::solve_last(const double* b_last, double* x_last) {
+  if (!factored) return set_error(DM_ESTATE, "dm_solve_last before a successful dm_factor");
+  if (precision != DM_FP64) return set_error(DM_EINVAL, "dm_solve_last needs a float64 plan (no refinement)");
+  if (top.nsys != 1) return set_error(DM_EINVAL, "dm_solve_last needs a single-system plan");
+  cudaStream_t st = stream;
+  const SysSpec& sp = top.spec[0];
+  const long long mr = (long long)sp.m * sp.r;
+  const int li = top.last_part[0];
+  const PartDesc& lp = top.parts[li];
+  const PartDesc* dlp = top.d_parts + li;
+  DM_CUDA(cudaMemsetAsync(top.F, 0, top.nvec * sizeof(double), st));
+  DM_CUDA(cudaMemsetAsync(top.z, 0, top.nvec * sizeof(double), st));
+  int rc = copy_in(top.F + (long long)(sp.N - 1) * mr, b_last, mr * sizeof(double), st);
+  if (rc) return rc;
+  double* z = static_cast<double*>(top.z);
+  launch_fwd_solve<double>(dlp, 1, lp.L - 1, top.max_m, top.max_r, top.A, static_cast<const double*>(top.G),
+                           top.F, z, st);
+  for (int s = 0; s + 1 < lp.L; ++s)
+    launch_back_solve<double>(dlp, 1, s, top.max_m, top.max_r, static_cast<const double*>(top.Acal), z, st);
+  if (top.supp) {
+    Level& S = *top.supp;
+    DM_CUDA(cudaMemsetAsync(S.F, 0, S.nvec * sizeof(double), st));
+    launch_assemble_f<double>(top.d_seps + (top.nseps - 1), 1, top.max_m, top.max_r, top.A, top.C, top.F, z, S.F, st);
+    solve_level(S, S.F, S.X, st, prof);
+  }
+  launch_backsub<double>(dlp, 1, lp.L, top.max_m, top.max_r, static_cast<const double*>(top.ZL),
+                         static_cast<const double*>(top.ZR), z, top.supp ? top.supp->X : nullptr, top.X, st);
+  DM_CUDA(cudaGetLastError());
+  rc = copy_out(x_last, top.X + (long long)(sp.N - 1) * mr, mr * sizeof(double), st);
+  if (rc) return rc;
+  DM_CUDA(cudaStreamSynchronize(st));
+  return DM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // partition plan and tuner seeds (Section 2, Section 5)
 void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps) {
@@ -983,6 +1026,11 @@ int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C)
 int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out) {
   if (!plan || !b || !x) return set_error(DM_EINVAL, "NULL argument to dm_solve");
   return plan->plan.solve(b, x, relres_out);
+}
+
+int dm_solve_last(dm_plan_t plan, const double* b_last, double* x_last) {
+  if (!plan || !b_last || !x_last) return set_error(DM_EINVAL, "NULL argument to dm_solve_last");
+  return plan->plan.solve_last(b_last, x_last);
 }
 
 int dm_set_stream(dm_plan_t plan, void* cuda_stream) {

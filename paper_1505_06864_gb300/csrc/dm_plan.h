@@ -83,6 +83,7 @@ struct Level {
   // per-step launch costs
   std::vector<Cost> c_inv, c_fwd, c_back, c_fwds, c_backs;
   std::vector<double> fwd_chain_frac;  // share of c_fwd[t] in the type-0 (chain) tiles
+  std::vector<int> last_part;           // per system: index in parts of its last subsystem
   Cost c_asm_h, c_asm_f, c_backsub, c_resid, c_axpy, c_sepcopy;
   PartDesc* d_parts = nullptr;
   SepDesc* d_seps = nullptr;
@@ -140,6 +141,7 @@ struct Plan {
   int run(GraphCache& g, F&& body);
 
   int init(const std::vector<SysSpec>& specs, int precision);
+  int solve_last(const double* b_last, double* x_last);
   int factor(const double* A, const double* B, const double* C);
   int solve(const double* b, double* x, double* relres_out);
   int solve_device(const double* b_dev, double* x_dev);

@@ -69,6 +69,7 @@ def lib():
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
+            "dm_solve_last": (I, [P, P, P]),
             "dm_set_stream": (I, [P, P]),
             "dm_set_refinement": (I, [P, D, I]),
             "dm_set_borrow_inputs": (I, [P, I]),
@@ -186,6 +187,11 @@ def dm_solve(plan, b, x, count=1, allow_notconv=False):
     rc = lib().dm_solve(plan, _ptr(b), _ptr(x, True), rel)
     _check(rc, (DM_OK, DM_ENOTCONV) if allow_notconv else (DM_OK,))
     return rel[0] if count == 1 else list(rel)
+
+
+def dm_solve_last(plan, b_last, x_last):
+    """x_N for a right-hand side that is zero except its last block row b_last."""
+    return _check(lib().dm_solve_last(plan, _ptr(b_last), _ptr(x_last, True)))
 
 
 def dm_set_stream(plan, stream):

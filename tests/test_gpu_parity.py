@@ -333,3 +333,30 @@ def test_laplace_fill_paper_shape_small(dm):
     s = w.laplace_fill_system(40, 300, 1, 3)
     x, rel, _ = solve(dm, s, 6, 1)
     check(x, o.dm(s.A, s.B, s.C, s.b, 6), TOL64)
+
+
+@pytest.mark.parametrize("N,m,r,P,levels", [(64, 16, 1, 4, 1), (97, 40, 3, 7, 2), (30, 8, 2, 1, 1), (3, 5, 1, 2, 1),
+                                            (200, 24, 2, 30, 2)])
+def test_solve_last_row_only(dm, N, m, r, P, levels):
+    """b zero except its last block row; only x_N is computed (the paper's
+    application case)."""
+    s = w.dominant_system(N, m, r, 90 + N)
+    b = np.zeros_like(s.b)
+    b[-1] = w.random_rhs(1, m, r, 5)[0]
+    plan = dm.dm_plan(N, m, r, P, levels, "fp64")
+    try:
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        xl = np.zeros((m, r))
+        dm.dm_solve_last(plan, np.ascontiguousarray(b[-1]), xl)
+        P2 = dm.dm_plan_query(plan)["P2"]
+        with pytest.raises(dm.DMError):
+            q = dm.dm_plan(N, m, r, P, levels, "fp32")
+            try:
+                dm.dm_factor(q, s.A, s.B, s.C)
+                dm.dm_solve_last(q, np.ascontiguousarray(b[-1]), xl.copy())
+            finally:
+                dm.dm_destroy(q)
+    finally:
+        dm.dm_destroy(plan)
+    xo = o.dm(s.A, s.B, s.C, b, P, levels=levels, P2=P2 if P2 > 1 else None)
+    check(xl[None], xo[-1:], TOL64)
