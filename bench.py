@@ -404,6 +404,14 @@ def _timed_steps(dm, plan, A, B, C, b, x, steps, warmup, stream, mixed):
     return ev[0].elapsed_time(ev[1]) / steps, rel
 
 
+def _profile_pass(dm, plan, A, B, C, b, x, mixed):
+    """One extra factor + solve with per-launch CUDA events (not timed above)."""
+    dm.dm_profile(plan, True)
+    dm.dm_factor(plan, A, B, C)
+    dm.dm_solve(plan, b, x, allow_notconv=mixed, count=dm.dm_plan_query(plan)["count"])
+    return {k: round(v["ms"], 2) for k, v in dm.dm_profile(plan, False).items()}
+
+
 def run_precision(args):
     """Conditioned dense blocks: N=4096, m=128, cond(B_i)=1e4, 8 right-hand
     sides; float64 DM against float32 / TF32 / split-bf16 factors refined in
@@ -426,13 +434,15 @@ def run_precision(args):
         mixed = prec != "fp64"
         ms, rel = _timed_steps(dm, plan, A, B, C, b, x, args.steps, max(3, args.warmup), stream, mixed)
         q = dm.dm_plan_query(plan)
+        kern = _profile_pass(dm, plan, A, B, C, b, x, mixed)
         xh = x.cpu().numpy()
         if prec == "fp64":
             x64 = xh
         out[prec] = {"systems_per_s": 1e3 / ms, "ms": ms, "iters": q["last_iters"], "relres": rel,
                      "last_correction": q["last_correction"], "converged": (not mixed) or q["last_correction"] <= 1e-12,
                      "rel_err_vs_xtrue": rel_err(xh, s.x_true), "rel_err_vs_fp64_dm": rel_err(xh, x64),
-                     "tflops": (q["factor_flops"] + q["solve_flops"] * q["last_iters"]) / (ms / 1e3) / 1e12}
+                     "tflops": (q["factor_flops"] + q["solve_flops"] * q["last_iters"]) / (ms / 1e3) / 1e12,
+                     "kernels_ms": kern}
         dm.dm_destroy(plan)
     ok = {k: v for k, v in out.items() if k != "fp64" and v["converged"] and v["rel_err_vs_fp64_dm"] <= 1e-10}
     best = max(ok, key=lambda k: ok[k]["systems_per_s"]) if ok else "fp64"
@@ -493,6 +503,7 @@ def run_batch(args):
         mixed = prec != "fp64"
         ms, rel = _timed_steps(dm, plan, A, B, C, b, x, max(1, args.steps // 3), 3, stream, mixed)
         q = dm.dm_plan_query(plan)
+        kern = _profile_pass(dm, plan, A, B, C, b, x, mixed)
         errs = []
         for i in picks:
             n, m, r = shapes[i]
@@ -505,7 +516,7 @@ def run_batch(args):
         out[prec] = {"systems_per_s": count * 1e3 / ms, "ms_per_batch": ms, "iters": q["last_iters"],
                      "max_relres": max(rel) if isinstance(rel, list) else rel,
                      "tflops": (q["factor_flops"] + q["solve_flops"] * q["last_iters"]) / (ms / 1e3) / 1e12,
-                     "rel_err_vs_oracle_sampled": max(errs), "sampled_systems": picks,
+                     "rel_err_vs_oracle_sampled": max(errs), "sampled_systems": picks, "kernels_ms": kern,
                      "device_gb": q["device_bytes"] / 1e9}
         dm.dm_destroy(plan)
         torch.cuda.empty_cache()

@@ -94,6 +94,7 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     if (rc) return rc;
   }
   // subsystem and separator tables
+  nrows = 0;
   parts.clear();
   seps.clear();
   sysd.clear();
@@ -105,7 +106,8 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     sd.N = sp.N;
     sd.m = sp.m;
     sd.r = sp.r;
-    sd.pad = 0;
+    sd.row0 = nrows;
+    nrows += sp.N;
     sysd.push_back(sd);
     std::vector<int> starts, lens, sepr;
     partition_lengths(sp.N, sp.P, sp.m, sp.r, sp.flags, lens);
@@ -739,7 +741,7 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
       solve_level(top, b_dev, x_dev, stream, prof);
       cudaMemsetAsync(nrm, 0, nb, stream);
       DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
-                launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
                                 b_dev, R, nrm, stream));
     };
     int rc0 = (b_dev == top.F && x_dev == top.X) ? run(g_solve, body) : (body(), DM_OK);
@@ -764,9 +766,9 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
       solve_level(top, rhs, Dx, stream, prof);
       cudaMemsetAsync(nrm, 0, nb, stream);
       DM_LAUNCH(prof, stream, K_AXPY, top.c_axpy, top.nsys,
-                launch_axpy_norms(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, Dx, x_dev, nrm, stream));
+                launch_axpy_norms(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, Dx, x_dev, nrm, stream));
       DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
-                launch_residual(top.d_sys, top.nsys, top.Nmax, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
                                 b_dev, R, nrm, stream));
     };
     int rc0 = (b_dev == top.F && x_dev == top.X) ? run(it == 1 ? g_iter_first : g_iter_next, body) : (body(), DM_OK);

@@ -39,7 +39,8 @@ struct SepDesc {
 // One system of a level (for row-parallel kernels such as the residual).
 struct SysDesc {
   long long blk, vec;  // offsets of row 0
-  int N, m, r, pad;
+  int N, m, r;
+  int row0;            // first row of the system when the rows of all systems are numbered consecutively
 };
 
 // ---- launchers (dm_kernels.cu); T = double or float (factor storage type)
@@ -75,11 +76,11 @@ void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const
                      double* x, cudaStream_t st);
 // r = b - T x (float64), per-system column norms: nrm[s*4*64 + 0*64 + c] = ||r_c||^2,
 // [1] = ||b_c||^2 (both accumulated by atomics; zeroed by the caller).
-void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* A,
+void launch_residual(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* A,
                      const double* B, const double* C, const double* x, const double* b, double* r,
                      double* nrm, cudaStream_t st);
 // x += d, nrm[2] += ||d_c||^2, nrm[3] += ||x_c||^2 (after the update)
-void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
+void launch_axpy_norms(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* d,
                        double* x, double* nrm, cudaStream_t st);
 
 // tcgen05 block products of the float32 factor sweeps (dm_tc.cu); mode 0 =

@@ -704,60 +704,59 @@ __global__ void __launch_bounds__(kThreads) k_backsub(const PartDesc* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Narrow products for right-hand sides with r <= RM <= 16 columns: a warp per
-// output row, lanes striding over k (coalesced reads of the m x m block), RM
-// partial sums per lane reduced with shuffles.  R panels live in shared memory
-// as [m][RM], zero past column r.  No multiply-add is spent on padding beyond
-// the bucket RM in {1, 2, 4, 8, 16}.
-template <typename T, typename TL1, typename TL2, int RM, typename Epi>
-__device__ __forceinline__ void narrow_mm(int m, const TL1* __restrict__ L1, const T* __restrict__ R1,
-                                          const TL2* __restrict__ L2, const T* __restrict__ R2, Epi epi) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x >> 5; i < m; i += nw) {
-    T acc[RM];
+// Narrow products for right-hand sides (r <= 16 columns): one output row per
+// thread.  Each thread streams its row of the m x m block from global memory
+// (every load brings a whole line into L1, so a warp keeps 32 lines in flight
+// and the following k hit L1) against the panel R ([m][RB] in shared memory,
+// read as broadcasts); no cross-lane reduction.  RB is the CTA's own column
+// bucket (1, 2, 4, 8 or 16 >= its r), so a batch with mixed right-hand-side
+// counts spends no multiply-add on another system's padding.
+__host__ __device__ constexpr int rbucket(int r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : 16; }
+
+// f(integral_constant<RB>) with RB = rbucket(r), instantiated only for RB <= RM
+template <int RM, typename F>
+__device__ __forceinline__ void with_rb(int r, F&& f) {
+  const int rb = rbucket(r);
+  if (rb == 1) { f(std::integral_constant<int, 1>()); return; }
+  if constexpr (RM >= 2) if (rb == 2) { f(std::integral_constant<int, 2>()); return; }
+  if constexpr (RM >= 4) if (rb == 4) { f(std::integral_constant<int, 4>()); return; }
+  if constexpr (RM >= 8) if (rb == 8) { f(std::integral_constant<int, 8>()); return; }
+  if constexpr (RM >= 16) f(std::integral_constant<int, 16>());
+}
+
+template <typename T, typename TL1, typename TL2, int RB, typename Epi>
+__device__ __forceinline__ void rows_mm(int m, const TL1* __restrict__ L1, const T* __restrict__ R1,
+                                        const TL2* __restrict__ L2, const T* __restrict__ R2, Epi epi) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    T acc[RB];
 #pragma unroll
-    for (int c = 0; c < RM; ++c) acc[c] = (T)0;
-    // 4 independent loads of the row in flight per lane before their FMAs
-    auto row_dot = [&](const auto* __restrict__ l, const T* __restrict__ R) {
-      int k = lane;
-      for (; k + 96 < m; k += 128) {
-        const T l0 = (T)l[k], l1 = (T)l[k + 32], l2 = (T)l[k + 64], l3 = (T)l[k + 96];
+    for (int c = 0; c < RB; ++c) acc[c] = (T)0;
+    const TL1* l1 = L1 + (long long)i * m;
+#pragma unroll 4
+    for (int k = 0; k < m; ++k) {
+      const T lv = (T)l1[k];
 #pragma unroll
-        for (int c = 0; c < RM; ++c) {
-          acc[c] = fma(l0, R[k * RM + c], acc[c]);
-          acc[c] = fma(l1, R[(k + 32) * RM + c], acc[c]);
-          acc[c] = fma(l2, R[(k + 64) * RM + c], acc[c]);
-          acc[c] = fma(l3, R[(k + 96) * RM + c], acc[c]);
-        }
-      }
-      for (; k < m; k += 32) {
-        const T lv = (T)l[k];
-#pragma unroll
-        for (int c = 0; c < RM; ++c) acc[c] = fma(lv, R[k * RM + c], acc[c]);
-      }
-    };
-    row_dot(L1 + (long long)i * m, R1);
-    if (L2 != nullptr) row_dot(L2 + (long long)i * m, R2);
-#pragma unroll
-    for (int c = 0; c < RM; ++c) {
-      T v = acc[c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      acc[c] = v;
+      for (int c = 0; c < RB; ++c) acc[c] = fma(lv, R1[k * RB + c], acc[c]);
     }
-    T mine = (T)0;
+    if (L2 != nullptr) {
+      const TL2* l2 = L2 + (long long)i * m;
+#pragma unroll 4
+      for (int k = 0; k < m; ++k) {
+        const T lv = (T)l2[k];
 #pragma unroll
-    for (int c = 0; c < RM; ++c)
-      if (c == lane) mine = acc[c];
-    if (lane < RM) epi(i, lane, mine);
+        for (int c = 0; c < RB; ++c) acc[c] = fma(lv, R2[k * RB + c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < RB; ++c) epi(i, c, acc[c]);
   }
 }
 
-// Rs[k][c] = src[k * r + c] for c < r, zero up to RM.
-template <typename T, typename TS, int RM>
+// Rs[k][c] = src[k * r + c] for c < r, zero up to RB.
+template <typename T, typename TS, int RB>
 __device__ __forceinline__ void load_narrow(T* Rs, const TS* __restrict__ src, int m, int r) {
-  for (int e = threadIdx.x; e < m * RM; e += blockDim.x) {
-    const int k = e / RM, c = e - k * RM;
+  for (int e = threadIdx.x; e < m * RB; e += blockDim.x) {
+    const int k = e / RB, c = e - k * RB;
     Rs[e] = c < r ? (T)src[(long long)k * r + c] : (T)0;
   }
 }
@@ -770,25 +769,28 @@ __global__ void __launch_bounds__(256) k_fwd_solve_n(const PartDesc* __restrict_
   const PartDesc p = parts[blockIdx.x];
   if (t >= p.L) return;
   const int m = p.m, r = p.r;
-  T* Rs = reinterpret_cast<T*>(smem_raw);
-  T* Xs = Rs + m * RM;
-  const long long mm = (long long)m * m, mr = (long long)m * r;
-  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
-  const double* Ft = F + v;
-  if (t == 0) {
-    load_narrow<T, double, RM>(Rs, Ft, m, r);
-  } else {
-    load_narrow<T, T, RM>(Xs, z + v - mr, m, r);
-    __syncthreads();
-    narrow_mm<T, double, double, RM>(m, A + o, Xs, (const double*)nullptr, (const T*)nullptr,
+  with_rb<RM>(r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    T* Rs = reinterpret_cast<T*>(smem_raw);
+    T* Xs = Rs + m * RB;
+    const long long mm = (long long)m * m, mr = (long long)m * r;
+    const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+    const double* Ft = F + v;
+    if (t == 0) {
+      load_narrow<T, double, RB>(Rs, Ft, m, r);
+    } else {
+      load_narrow<T, T, RB>(Xs, z + v - mr, m, r);
+      __syncthreads();
+      rows_mm<T, double, double, RB>(m, A + o, Xs, (const double*)nullptr, (const T*)nullptr,
                                      [&](int row, int col, T val) {
-                                       Rs[row * RM + col] = col < r ? (T)Ft[(long long)row * r + col] - val : (T)0;
+                                       Rs[row * RB + col] = col < r ? (T)Ft[(long long)row * r + col] - val : (T)0;
                                      });
-  }
-  __syncthreads();
-  T* dst = z + v;
-  narrow_mm<T, T, T, RM>(m, G + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
-    if (col < r) dst[(long long)row * r + col] = val;
+    }
+    __syncthreads();
+    T* dst = z + v;
+    rows_mm<T, T, T, RB>(m, G + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
+      if (col < r) dst[(long long)row * r + col] = val;
+    });
   });
 }
 
@@ -800,17 +802,20 @@ __global__ void __launch_bounds__(256) k_back_solve_n(const PartDesc* __restrict
   const int t = p.L - 2 - s;
   if (t < 0) return;
   const int m = p.m, r = p.r;
-  T* Rs = reinterpret_cast<T*>(smem_raw);
-  const long long mm = (long long)m * m, mr = (long long)m * r;
-  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
-  T* Y = z + v;
-  load_narrow<T, T, RM>(Rs, Y + mr, m, r);
-  __syncthreads();
-  narrow_mm<T, T, T, RM>(m, Acal + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
-    if (col < r) {
-      const long long e = (long long)row * r + col;
-      Y[e] = Y[e] - val;
-    }
+  with_rb<RM>(r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    T* Rs = reinterpret_cast<T*>(smem_raw);
+    const long long mm = (long long)m * m, mr = (long long)m * r;
+    const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+    T* Y = z + v;
+    load_narrow<T, T, RB>(Rs, Y + mr, m, r);
+    __syncthreads();
+    rows_mm<T, T, T, RB>(m, Acal + o, Rs, (const T*)nullptr, (const T*)nullptr, [&](int row, int col, T val) {
+      if (col < r) {
+        const long long e = (long long)row * r + col;
+        Y[e] = Y[e] - val;
+      }
+    });
   });
 }
 
@@ -823,22 +828,27 @@ __global__ void __launch_bounds__(256) k_assemble_f_n(const SepDesc* __restrict_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SepDesc sp = seps[blockIdx.x];
   const int m = sp.m, r = sp.r;
-  double* R1 = reinterpret_cast<double*>(smem_raw);
-  double* R2 = R1 + m * RM;
-  load_narrow<double, T, RM>(R1, z + sp.vec_prev, m, r);
-  load_narrow<double, T, RM>(R2, z + sp.vec_next, m, r);
-  __syncthreads();
-  const double* Fq = F + sp.vec_q;
-  double* dst = fh + sp.hvec;
-  narrow_mm<double, double, double, RM>(m, A + sp.blk_q, R1, C + sp.blk_q, R2, [&](int row, int col, double v) {
-    if (col < r) {
-      const long long e = (long long)row * r + col;
-      dst[e] = Fq[e] - v;
-    }
+  with_rb<RM>(r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    double* R1 = reinterpret_cast<double*>(smem_raw);
+    double* R2 = R1 + m * RB;
+    load_narrow<double, T, RB>(R1, z + sp.vec_prev, m, r);
+    load_narrow<double, T, RB>(R2, z + sp.vec_next, m, r);
+    __syncthreads();
+    const double* Fq = F + sp.vec_q;
+    double* dst = fh + sp.hvec;
+    rows_mm<double, double, double, RB>(m, A + sp.blk_q, R1, C + sp.blk_q, R2, [&](int row, int col, double v) {
+      if (col < r) {
+        const long long e = (long long)row * r + col;
+        dst[e] = Fq[e] - v;
+      }
+    });
   });
 }
 
-// Back-substitution for row t = blockIdx.x of subsystem blockIdx.y.
+// Back-substitution for row t = blockIdx.x of subsystem blockIdx.y, in the
+// level's arithmetic (float32 levels: the spikes are float32, the products
+// too; x is written in float64).
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_backsub_n(const PartDesc* __restrict__ parts,
                                                    const T* __restrict__ ZL, const T* __restrict__ ZR,
@@ -849,31 +859,34 @@ __global__ void __launch_bounds__(256) k_backsub_n(const PartDesc* __restrict__ 
   const int t = blockIdx.x;
   if (t >= p.L) return;
   const int m = p.m, r = p.r;
-  double* R1 = reinterpret_cast<double*>(smem_raw);
-  double* R2 = R1 + m * RM;
-  const long long mm = (long long)m * m, mr = (long long)m * r;
-  const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
-  const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
-  if (hl) load_narrow<double, double, RM>(R1, h + p.hprev, m, r);
-  if (hr) load_narrow<double, double, RM>(R2, h + p.hnext, m, r);
-  __syncthreads();
-  const T* zt = z + v;
-  double* xt = x + v;
-  auto epi = [&](int row, int col, double val) {
-    if (col < r) {
-      const long long e = (long long)row * r + col;
-      xt[e] = (double)zt[e] - val;
+  with_rb<RM>(r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    T* R1 = reinterpret_cast<T*>(smem_raw);
+    T* R2 = R1 + m * RB;
+    const long long mm = (long long)m * m, mr = (long long)m * r;
+    const long long o = p.blk + (long long)t * mm, v = p.vec + (long long)t * mr;
+    const bool hl = p.flags & HAS_LEFT, hr = p.flags & HAS_RIGHT;
+    if (hl) load_narrow<T, double, RB>(R1, h + p.hprev, m, r);
+    if (hr) load_narrow<T, double, RB>(R2, h + p.hnext, m, r);
+    __syncthreads();
+    const T* zt = z + v;
+    double* xt = x + v;
+    auto epi = [&](int row, int col, T val) {
+      if (col < r) {
+        const long long e = (long long)row * r + col;
+        xt[e] = (double)zt[e] - (double)val;
+      }
+    };
+    if (hl && hr) {
+      rows_mm<T, T, T, RB>(m, ZL + o, R1, ZR + o, R2, epi);
+    } else if (hl) {
+      rows_mm<T, T, T, RB>(m, ZL + o, R1, (const T*)nullptr, (const T*)nullptr, epi);
+    } else if (hr) {
+      rows_mm<T, T, T, RB>(m, ZR + o, R2, (const T*)nullptr, (const T*)nullptr, epi);
+    } else {
+      for (long long e = threadIdx.x; e < mr; e += blockDim.x) xt[e] = (double)zt[e];
     }
-  };
-  if (hl && hr) {
-    narrow_mm<double, T, T, RM>(m, ZL + o, R1, ZR + o, R2, epi);
-  } else if (hl) {
-    narrow_mm<double, T, T, RM>(m, ZL + o, R1, (const T*)nullptr, (const double*)nullptr, epi);
-  } else if (hr) {
-    narrow_mm<double, T, T, RM>(m, ZR + o, R2, (const T*)nullptr, (const double*)nullptr, epi);
-  } else {
-    for (int e = threadIdx.x; e < mr; e += blockDim.x) xt[e] = (double)zt[e];
-  }
+  });
 }
 
 __global__ void k_sep_copy(const SepDesc* __restrict__ seps, const double* __restrict__ h,
@@ -884,14 +897,23 @@ __global__ void k_sep_copy(const SepDesc* __restrict__ seps, const double* __res
 }
 
 // ---------------------------------------------------------------------------
-// Residual r_i = b_i - A_i x_{i-1} - B_i x_i - C_i x_{i+1} in float64.  One CTA
-// per block row; a warp per output row reads A/B/C rows coalesced and reduces
-// with shuffles; x_{i-1}, x_i, x_{i+1} are staged in shared memory RM columns
-// at a time (RM in {1, 2, 4, 8, 16}, the smallest bucket >= nrhs, so no
-// multiply-add is spent on padding columns).  Column sums of r^2 and b^2 go
-// to nrm by atomics.
+// Residual r_i = b_i - A_i x_{i-1} - B_i x_i - C_i x_{i+1} in float64, one CTA
+// per block row of any system (rows of all systems numbered consecutively;
+// the CTA finds its system by binary search over their first rows).  One
+// output row per thread streaming the three block rows; x_{i-1}, x_i, x_{i+1}
+// staged in shared memory RB columns at a time (RB = the system's bucket).
+// Column sums of r^2 and b^2 go to nrm by atomics.
+__device__ __forceinline__ int find_sys(const SysDesc* __restrict__ sys, int nsys, int row) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sys[mid].row0 <= row) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int RM>
-__global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sys,
+__global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sys, int nsys,
                                                   const double* __restrict__ A,
                                                   const double* __restrict__ B,
                                                   const double* __restrict__ C,
@@ -901,76 +923,74 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
                                                   double* __restrict__ nrm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2 * kMaxR];
-  const SysDesc sd = sys[blockIdx.y];
-  const int i = blockIdx.x;
-  if (i >= sd.N) return;
+  const int si = find_sys(sys, nsys, blockIdx.x);
+  const SysDesc sd = sys[si];
+  const int i = blockIdx.x - sd.row0;
   const int m = sd.m, r = sd.r;
   const long long mm = (long long)m * m, mr = (long long)m * r;
   const long long o = sd.blk + i * mm, v = sd.vec + i * mr;
-  double* xs = reinterpret_cast<double*>(smem_raw);  // [3][m][RM]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   for (int e = tid; e < 2 * r; e += blockDim.x) red[e] = 0.0;
   const bool hasA = i > 0, hasC = i < sd.N - 1;
-  for (int c0 = 0; c0 < r; c0 += RM) {
-    const int nc = min(RM, r - c0);
-    __syncthreads();
-    for (int e = tid; e < 3 * m * RM; e += blockDim.x) {
-      const int which = e / (m * RM), rem = e - which * m * RM, k = rem / RM, c = rem - k * RM;
-      const int row = i - 1 + which;
-      xs[e] = (row >= 0 && row < sd.N && c < nc) ? x[sd.vec + row * mr + (long long)k * r + c0 + c] : 0.0;
-    }
-    __syncthreads();
-    for (int row = warp; row < m; row += 8) {
-      double acc[RM];
-#pragma unroll
-      for (int c = 0; c < RM; ++c) acc[c] = 0.0;
-      for (int k = lane; k < m; k += 32) {
-        const double a = hasA ? A[o + (long long)row * m + k] : 0.0;
-        const double bb = B[o + (long long)row * m + k];
-        const double cc = hasC ? C[o + (long long)row * m + k] : 0.0;
-        const double* xm = xs + k * RM;
-        const double* x0 = xm + m * RM;
-        const double* xp = x0 + m * RM;
-#pragma unroll
-        for (int c = 0; c < RM; ++c) acc[c] = fma(a, xm[c], fma(bb, x0[c], fma(cc, xp[c], acc[c])));
+  with_rb<RM>(r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    double* xs = reinterpret_cast<double*>(smem_raw);  // [3][m][RB]
+    for (int c0 = 0; c0 < r; c0 += RB) {
+      const int nc = min(RB, r - c0);
+      __syncthreads();
+      for (int e = tid; e < 3 * m * RB; e += blockDim.x) {
+        const int which = e / (m * RB), rem = e - which * m * RB, k = rem / RB, c = rem - k * RB;
+        const int row = i - 1 + which;
+        xs[e] = (row >= 0 && row < sd.N && c < nc) ? x[sd.vec + row * mr + (long long)k * r + c0 + c] : 0.0;
       }
+      __syncthreads();
+      for (int row = tid; row < m; row += blockDim.x) {
+        double acc[RB];
 #pragma unroll
-      for (int c = 0; c < RM; ++c) {
-        double s = acc[c];
+        for (int c = 0; c < RB; ++c) acc[c] = 0.0;
+        const double* ar = A + o + (long long)row * m;
+        const double* br = B + o + (long long)row * m;
+        const double* cr = C + o + (long long)row * m;
+#pragma unroll 2
+        for (int k = 0; k < m; ++k) {
+          const double av = hasA ? ar[k] : 0.0, bv = br[k], cv = hasC ? cr[k] : 0.0;
+          const double* xm = xs + k * RB;
+          const double* x0 = xm + m * RB;
+          const double* xp = x0 + m * RB;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        acc[c] = s;
-      }
-      if (lane < nc) {
-        double s = 0.0;
+          for (int c = 0; c < RB; ++c) acc[c] = fma(av, xm[c], fma(bv, x0[c], fma(cv, xp[c], acc[c])));
+        }
 #pragma unroll
-        for (int c = 0; c < RM; ++c)
-          if (c == lane) s = acc[c];
-        const long long e = v + (long long)row * r + c0 + lane;
-        const double bv = b[e];
-        const double rv = bv - s;
-        rout[e] = rv;
-        atomicAdd(&red[c0 + lane], rv * rv);
-        atomicAdd(&red[r + c0 + lane], bv * bv);
+        for (int c = 0; c < RB; ++c) {
+          if (c < nc) {
+            const long long e = v + (long long)row * r + c0 + c;
+            const double bb = b[e];
+            const double rv = bb - acc[c];
+            rout[e] = rv;
+            atomicAdd(&red[c0 + c], rv * rv);
+            atomicAdd(&red[r + c0 + c], bb * bb);
+          }
+        }
       }
     }
-  }
+  });
   __syncthreads();
   for (int c = tid; c < r; c += blockDim.x) {
-    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + c], red[c]);
-    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + kMaxR + c], red[r + c]);
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + c], red[c]);
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + kMaxR + c], red[r + c]);
   }
 }
 
-// x += d per block row, with column sums of d^2 and (updated) x^2.
-__global__ void __launch_bounds__(256) k_axpy_norms(const SysDesc* __restrict__ sys,
+// x += d per block row (rows of all systems numbered consecutively), with
+// column sums of d^2 and (updated) x^2.
+__global__ void __launch_bounds__(256) k_axpy_norms(const SysDesc* __restrict__ sys, int nsys,
                                                     const double* __restrict__ d,
                                                     double* __restrict__ x,
                                                     double* __restrict__ nrm) {
   __shared__ double red[2 * kMaxR];
-  const SysDesc sd = sys[blockIdx.y];
-  const int i = blockIdx.x;
-  if (i >= sd.N) return;
+  const int si = find_sys(sys, nsys, blockIdx.x);
+  const SysDesc sd = sys[si];
+  const int i = blockIdx.x - sd.row0;
   const int r = sd.r;
   const long long mr = (long long)sd.m * r, v = sd.vec + i * mr;
   for (int e = threadIdx.x; e < 2 * r; e += blockDim.x) red[e] = 0.0;
@@ -985,8 +1005,8 @@ __global__ void __launch_bounds__(256) k_axpy_norms(const SysDesc* __restrict__ 
   }
   __syncthreads();
   for (int c = threadIdx.x; c < r; c += blockDim.x) {
-    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + 2 * kMaxR + c], red[c]);
-    atomicAdd(&nrm[(long long)blockIdx.y * 4 * kMaxR + 3 * kMaxR + c], red[r + c]);
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + 2 * kMaxR + c], red[c]);
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + 3 * kMaxR + c], red[r + c]);
   }
 }
 
@@ -1256,7 +1276,7 @@ void launch_backsub(const PartDesc* parts, int nparts, int Lmax, int max_m, int 
   if (nparts <= 0 || Lmax <= 0) return;
   if (narrow_dispatch(max_r, [&](auto rm) {
         constexpr int RM = decltype(rm)::value;
-        const size_t bytes = sizeof(double) * 2 * (size_t)max_m * RM;
+        const size_t bytes = sizeof(T) * 2 * (size_t)max_m * RM;
         allow_smem(k_backsub_n<T, RM>, bytes);
         k_backsub_n<T, RM><<<dim3(Lmax, nparts), 256, bytes, st>>>(parts, ZL, ZR, z, h, x);
       }))
@@ -1282,23 +1302,23 @@ void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const
   k_sep_copy<<<nseps, 256, 0, st>>>(seps, h, x);
 }
 
-void launch_residual(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* A,
+void launch_residual(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* A,
                      const double* B, const double* C, const double* x, const double* b, double* r,
                      double* nrm, cudaStream_t st) {
-  if (nsys <= 0 || Nmax <= 0) return;
+  if (nsys <= 0 || nrows <= 0) return;
   auto go = [&](auto rm) {
     constexpr int RM = decltype(rm)::value;
     const size_t bytes = sizeof(double) * 3 * (size_t)max_m * RM;
     allow_smem(k_residual<RM>, bytes);
-    k_residual<RM><<<dim3(Nmax, nsys), 256, bytes, st>>>(sys, A, B, C, x, b, r, nrm);
+    k_residual<RM><<<nrows, 256, bytes, st>>>(sys, nsys, A, B, C, x, b, r, nrm);
   };
   if (!narrow_dispatch(max_r, go)) go(std::integral_constant<int, 16>());
 }
 
-void launch_axpy_norms(const SysDesc* sys, int nsys, int Nmax, int max_m, int max_r, const double* d,
+void launch_axpy_norms(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* d,
                        double* x, double* nrm, cudaStream_t st) {
-  if (nsys <= 0 || Nmax <= 0) return;
-  k_axpy_norms<<<dim3(Nmax, nsys), 256, 0, st>>>(sys, d, x, nrm);
+  if (nsys <= 0 || nrows <= 0) return;
+  k_axpy_norms<<<nrows, 256, 0, st>>>(sys, nsys, d, x, nrm);
 }
 
 #define DM_INST(T)                                                                                  \

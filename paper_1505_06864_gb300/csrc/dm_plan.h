@@ -76,6 +76,7 @@ struct Level {
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0
   long long nblk = 0, nvec = 0;       // elements of the [rows][m][m] and [rows][m][r] arrays
   int max_m = 1, max_r = 1, Nmax = 0, Lmax = 0, nparts = 0, nseps = 0;
+  int nrows = 0;  // block rows of all systems
   std::vector<PartDesc> parts;
   std::vector<SepDesc> seps;
   std::vector<SysDesc> sysd;
