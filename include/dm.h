@@ -194,7 +194,9 @@ int dm_plan_tune(int N, int m, int nrhs, int* P, int* levels, int* P2);
  * fwd_solve, back_solve, assemble_f, backsub, sep_copy, residual,
  * axpy_norms).  With profiling enabled each launch is bracketed by a pair of
  * CUDA events recorded on the plan's stream.  dm_profile first writes (when
- * out != NULL) one entry per class seen since the previous call -- launches,
+ * out != NULL) one entry per class and recursion depth seen since the
+ * previous call (name "fwd_factor" for the top level, "fwd_factor@1" for its
+ * supplementary system, "@2" one level further, "@3" for all deeper) -- launches,
  * summed event time in ms, and the launches' algorithmic flops (2 per
  * multiply-add) and bytes (operands read once, results written once) --
  * then clears the sums and switches profiling on (enable = 1) or off. */

@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -90,6 +91,7 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
   }
   if (!sub.empty()) {
     supp.reset(new Level());
+    supp->depth = depth + 1;
     int rc = supp->build(sub, false);
     if (rc) return rc;
   }
@@ -177,6 +179,15 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     int c = 0;
     while (c < nparts && parts[c].L >= s + 2) ++c;
     active_back[s] = c;
+  }
+  // Both z sweeps in one persistent launch when every subsystem's cluster is
+  // resident at once (a second wave would serialise whole sweeps); with many
+  // subsystems the per-step launches keep the GPU busier.  DM_SOLVE_SWEEP=0
+  // keeps the per-step kernels (for comparisons).
+  {
+    const char* e = std::getenv("DM_SOLVE_SWEEP");
+    sweep_cs = (e && e[0] == '0') ? 0 : sweep_cluster_choice(f32 ? 4 : 8, max_m, max_r, nparts);
+    sweep = sweep_cs > 0;
   }
   compute_costs();
   return DM_OK;
@@ -351,7 +362,7 @@ Level::~Level() {
 // Profiler
 const char* const kClassNames[K_NCLASS] = {
     "inv", "fwd_factor", "back_factor", "assemble_h", "fwd_solve", "back_solve", "assemble_f",
-    "backsub", "sep_copy", "residual", "axpy_norms"};
+    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve"};
 
 cudaEvent_t Prof::take() {
   if (!pool.empty()) {
@@ -380,7 +391,7 @@ void Prof::end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, b
   }
   cudaEvent_t e1 = take();
   cudaEventRecord(e1, st);
-  recs.push_back(Rec{cls, e0, e1, fl, by});
+  recs.push_back(Rec{cls + K_NCLASS * std::min(depth, kDepths - 1), e0, e1, fl, by});
 }
 
 int Prof::collect() {
@@ -403,7 +414,7 @@ int Prof::collect() {
 
 void Prof::reset() {
   collect();
-  for (int i = 0; i < K_NCLASS; ++i) n[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
+  for (int i = 0; i < K_NCLASS * kDepths; ++i) n[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
 }
 
 Prof::~Prof() {
@@ -493,11 +504,13 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
 void factor_level(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   cudaMemsetAsync(L.status, 0x7f, std::max(1, L.nsys) * sizeof(int), st);
   cudaMemsetAsync(L.d_err, 0, sizeof(int), st);
+  pf.depth = L.depth;
   if (L.f32)
     factor_level_t<float>(L, st, pf, aux);
   else
     factor_level_t<double>(L, st, pf, aux);
   if (L.supp) factor_level(*L.supp, st, pf, aux);
+  pf.depth = L.depth;
 }
 
 // Solve with resident factors: F -> X for every system of the level.
@@ -506,16 +519,25 @@ static void solve_level_t(Level& L, const double* F, double* X, cudaStream_t st,
   T* z = static_cast<T*>(L.z);
   const T* G = static_cast<const T*>(L.G);
   const T* Ac = static_cast<const T*>(L.Acal);
-  for (int t = 0; t < L.Lmax; ++t)
-    DM_LAUNCH(pf, st, K_FWD_SOLVE, L.c_fwds[t], L.active_fwd[t],
-              launch_fwd_solve<T>(L.d_parts, L.active_fwd[t], t, L.max_m, L.max_r, L.A, G, F, z, st));
-  for (int s = 0; s + 1 < L.Lmax; ++s)
-    DM_LAUNCH(pf, st, K_BACK_SOLVE, L.c_backs[s], L.active_back[s],
-              launch_back_solve<T>(L.d_parts, L.active_back[s], s, L.max_m, L.max_r, Ac, z, st));
+  if (L.sweep) {
+    Cost c;
+    for (int t = 0; t < L.Lmax; ++t) c.flops += L.c_fwds[t].flops + L.c_backs[t].flops,
+                                     c.bytes += L.c_fwds[t].bytes + L.c_backs[t].bytes;
+    DM_LAUNCH(pf, st, K_SWEEP_SOLVE, c, L.nparts,
+              launch_sweep_solve<T>(L.d_parts, L.nparts, L.sweep_cs, L.max_m, L.max_r, L.A, G, Ac, F, z, st));
+  } else {
+    for (int t = 0; t < L.Lmax; ++t)
+      DM_LAUNCH(pf, st, K_FWD_SOLVE, L.c_fwds[t], L.active_fwd[t],
+                launch_fwd_solve<T>(L.d_parts, L.active_fwd[t], t, L.max_m, L.max_r, L.A, G, F, z, st));
+    for (int s = 0; s + 1 < L.Lmax; ++s)
+      DM_LAUNCH(pf, st, K_BACK_SOLVE, L.c_backs[s], L.active_back[s],
+                launch_back_solve<T>(L.d_parts, L.active_back[s], s, L.max_m, L.max_r, Ac, z, st));
+  }
   if (L.supp) {
     DM_LAUNCH(pf, st, K_ASSEMBLE_F, L.c_asm_f, L.nseps,
               launch_assemble_f<T>(L.d_seps, L.nseps, L.max_m, L.max_r, L.A, L.C, F, z, L.supp->F, st));
     solve_level(*L.supp, L.supp->F, L.supp->X, st, pf);
+    pf.depth = L.depth;
   }
   DM_LAUNCH(pf, st, K_BACKSUB, L.c_backsub, L.nparts,
             launch_backsub<T>(L.d_parts, L.nparts, L.Lmax, L.max_m, L.max_r, static_cast<const T*>(L.ZL),
@@ -526,6 +548,7 @@ static void solve_level_t(Level& L, const double* F, double* X, cudaStream_t st,
 }
 
 void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf) {
+  pf.depth = L.depth;
   if (L.f32)
     solve_level_t<float>(L, F, X, st, pf);
   else
@@ -1100,11 +1123,15 @@ int dm_profile(dm_plan_t plan, int enable, dm_profile_entry* out, int max_entrie
   if (out && max_entries > 0) {
     pf.collect();
     int k = 0;
-    for (int c = 0; c < K_NCLASS && k < max_entries; ++c) {
+    for (int c = 0; c < K_NCLASS * Prof::kDepths && k < max_entries; ++c) {
       if (pf.n[c] == 0) continue;
       dm_profile_entry& e = out[k++];
       std::memset(e.name, 0, sizeof e.name);
-      std::strncpy(e.name, kClassNames[c], sizeof e.name - 1);
+      const int d = c / K_NCLASS;
+      if (d == 0)
+        std::snprintf(e.name, sizeof e.name, "%s", kClassNames[c % K_NCLASS]);
+      else
+        std::snprintf(e.name, sizeof e.name, "%s@%d", kClassNames[c % K_NCLASS], d);
       e.launches = pf.n[c];
       e.ms = pf.ms[c];
       e.flops = pf.flops[c];

@@ -59,6 +59,15 @@ void launch_back_factor(const PartDesc* parts, int nparts, int s, int max_m, con
 template <typename T>
 void launch_fwd_solve(const PartDesc* parts, int nparts, int t, int max_m, int max_r,
                       const double* A, const T* G, const double* F, T* z, cudaStream_t st);
+// Both right-hand-side sweeps of a level in one persistent launch (one
+// cluster per subsystem); false when the level's shape needs the per-step
+// kernels (more than 16 right-hand sides or panels beyond shared memory).
+// Cluster size for the persistent solve sweep of `nparts` subsystems (0: use
+// the per-step kernels).
+int sweep_cluster_choice(int elem_bytes, int max_m, int max_r, int nparts);
+template <typename T>
+void launch_sweep_solve(const PartDesc* parts, int nparts, int cs, int max_m, int max_r, const double* A,
+                        const T* G, const T* Acal, const double* F, T* z, cudaStream_t st);
 template <typename T>
 void launch_back_solve(const PartDesc* parts, int nparts, int s, int max_m, int max_r,
                        const T* Acal, T* z, cudaStream_t st);

@@ -761,6 +761,173 @@ __device__ __forceinline__ void load_narrow(T* Rs, const TS* __restrict__ src, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Both right-hand-side sweeps of a level in one launch (Section 3 applied to
+// the subsystems: z_t = G_t (F_t - A_t z_{t-1}) for t = 0..L-1, then
+// z_t -= Acal_t z_{t+1} for t = L-2..0), one thread-block cluster of CS CTAs
+// per subsystem.  CTA `rank` owns rows [rank*rpc, (rank+1)*rpc) of every
+// block; each of its rows is a dot product over LPR lanes (coalesced loads of
+// the block row, many in flight per lane, xor-shuffle reduction), against the
+// full m x RB panel that every CTA holds in shared memory, column-major
+// ([c][k], conflict-free).  A CTA pushes the rows it computes into the panel
+// of every CTA of its cluster (distributed shared memory) and the cluster
+// barrier publishes them, so a step costs two cluster barriers forward and
+// one backward instead of a kernel launch.  All loop bounds are uniform over
+// a cluster (the subsystem's L and m), so every CTA passes every barrier.
+constexpr int kSweepThreads = 256;
+
+// Lanes per row: the largest power of two <= 32 with lpr * rows <= threads
+// (at least 4; a CTA with more rows than groups loops over them).
+__host__ __device__ constexpr int sweep_lpr(int rows) {
+  return rows <= 8 ? 32 : rows <= 16 ? 16 : rows <= 32 ? 8 : rows <= 64 ? 4 : rows <= 128 ? 2 : 1;
+}
+
+// acc[c] = sum_k Lrow[k] X[c * ld + k] over the LPR lanes of a group
+// (result in every lane of the group).  `valid` false contributes zeros but
+// still takes part in the shuffles (the whole warp executes them).
+template <typename T, typename TL, int RB, int LPR>
+__device__ __forceinline__ void group_dot(bool valid, const TL* __restrict__ Lrow, const T* X, int ld, int m,
+                                          int lane, T (&acc)[RB]) {
+#pragma unroll
+  for (int c = 0; c < RB; ++c) acc[c] = (T)0;
+  if (valid) {
+    constexpr int U = (sizeof(T) == 8 && RB >= 16) ? 4 : 8;  // loads in flight per lane
+    int k = lane;
+    for (; k + LPR * (U - 1) < m; k += LPR * U) {
+      TL v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = Lrow[k + u * LPR];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < RB; ++c) acc[c] = fma((T)v[u], X[c * ld + k + u * LPR], acc[c]);
+    }
+    for (; k < m; k += LPR) {
+      const T v = (T)Lrow[k];
+#pragma unroll
+      for (int c = 0; c < RB; ++c) acc[c] = fma(v, X[c * ld + k], acc[c]);
+    }
+  }
+  if constexpr (LPR > 1) {
+#pragma unroll
+    for (int off = LPR / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int c = 0; c < RB; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, LPR);
+  }
+}
+
+namespace cg = cooperative_groups;
+
+template <typename T, int RB, int LPR>
+__device__ void sweep_body(const PartDesc& p, int rank, int cs, const double* __restrict__ A,
+                           const T* __restrict__ G, const T* __restrict__ Acal, const double* __restrict__ F,
+                           T* __restrict__ z, T* Zp0, T* Zp1, T* Rs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int m = p.m, r = p.r, L = p.L;
+  const int rpc = (m + cs - 1) / cs;
+  const int r0 = min(m, rank * rpc), r1 = min(m, r0 + rpc);
+  constexpr int GROUPS = kSweepThreads / LPR;
+  const int g = threadIdx.x / LPR, lane = threadIdx.x % LPR;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  // the rows this CTA computes go into the panel `dst` of every CTA
+  auto push = [&](T* dst, int row, int c, T v) {
+    for (int q = 0; q < cs; ++q) *cl.map_shared_rank(dst + c * m + row, q) = v;
+  };
+  // forward sweep
+  for (int t = 0; t < L; ++t) {
+    const long long o = p.blk + t * mm, v = p.vec + t * mr;
+    const double* Ft = F + v;
+    if (t == 0) {
+      for (int e = threadIdx.x; e < m * RB; e += blockDim.x) {
+        const int c = e / m, k = e - c * m;
+        Rs[e] = c < r ? (T)Ft[(long long)k * r + c] : (T)0;
+      }
+      __syncthreads();
+    } else {
+      for (int i0 = r0; i0 < r1; i0 += GROUPS) {
+        const int row = i0 + g;
+        const bool ok = row < r1;
+        T acc[RB];
+        group_dot<T, double, RB, LPR>(ok, A + o + (long long)row * m, Zp0, m, m, lane, acc);
+#pragma unroll
+        for (int c = 0; c < RB; ++c)
+          if (ok && c % LPR == lane) push(Rs, row, c, c < r ? (T)Ft[(long long)row * r + c] - acc[c] : (T)0);
+      }
+      cl.sync();
+    }
+    T* zt = z + v;
+    for (int i0 = r0; i0 < r1; i0 += GROUPS) {
+      const int row = i0 + g;
+      const bool ok = row < r1;
+      T acc[RB];
+      group_dot<T, T, RB, LPR>(ok, G + o + (long long)row * m, Rs, m, m, lane, acc);
+#pragma unroll
+      for (int c = 0; c < RB; ++c)
+        if (ok && c % LPR == lane) {
+          if (c < r) zt[(long long)row * r + c] = acc[c];
+          push(Zp0, row, c, c < r ? acc[c] : (T)0);
+        }
+    }
+    cl.sync();
+  }
+  // backward sweep: Zp0 holds z_{L-1}; panels alternate between Zp0 and Zp1
+  T* cur = Zp0;
+  T* nxt = Zp1;
+  for (int t = L - 2; t >= 0; --t) {
+    const long long o = p.blk + t * mm, v = p.vec + t * mr;
+    T* zt = z + v;
+    for (int i0 = r0; i0 < r1; i0 += GROUPS) {
+      const int row = i0 + g;
+      const bool ok = row < r1;
+      T acc[RB];
+      group_dot<T, T, RB, LPR>(ok, Acal + o + (long long)row * m, cur, m, m, lane, acc);
+#pragma unroll
+      for (int c = 0; c < RB; ++c)
+        if (ok && c % LPR == lane) {
+          T val = (T)0;
+          if (c < r) {
+            const long long e = (long long)row * r + c;
+            val = zt[e] - acc[c];
+            zt[e] = val;
+          }
+          push(nxt, row, c, val);
+        }
+    }
+    cl.sync();
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_solve_n(const PartDesc* __restrict__ parts, int cs,
+                                                                 const double* __restrict__ A,
+                                                                 const T* __restrict__ G,
+                                                                 const T* __restrict__ Acal,
+                                                                 const double* __restrict__ F, T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const PartDesc p = parts[blockIdx.x / cs];
+  const int m = p.m;
+  // panels laid out for this subsystem's m (at most the launch's max_m)
+  T* Zp0 = reinterpret_cast<T*>(smem_raw);
+  T* Zp1 = Zp0 + m * RM;
+  T* Rs = Zp1 + m * RM;
+  const int rpc = (m + cs - 1) / cs;
+  const int lpr = sweep_lpr(rpc);
+  with_rb<RM>(p.r, [&](auto rbc) {
+    constexpr int RB = decltype(rbc)::value;
+    switch (lpr) {
+      case 32: sweep_body<T, RB, 32>(p, rank, cs, A, G, Acal, F, z, Zp0, Zp1, Rs); break;
+      case 16: sweep_body<T, RB, 16>(p, rank, cs, A, G, Acal, F, z, Zp0, Zp1, Rs); break;
+      case 8: sweep_body<T, RB, 8>(p, rank, cs, A, G, Acal, F, z, Zp0, Zp1, Rs); break;
+      default: sweep_body<T, RB, 4>(p, rank, cs, A, G, Acal, F, z, Zp0, Zp1, Rs); break;  // rows looped
+    }
+  });
+}
+
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_fwd_solve_n(const PartDesc* __restrict__ parts, int t,
                                                      const double* __restrict__ A, const T* __restrict__ G,
@@ -1226,6 +1393,65 @@ void launch_back_solve(const PartDesc* parts, int nparts, int s, int max_m, int 
   }
 }
 
+template <typename T, int RM>
+cudaLaunchConfig_t sweep_config(int nparts, int cs, int max_m, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nparts * cs);
+  cfg.blockDim = dim3(kSweepThreads);
+  cfg.dynamicSmemBytes = sizeof(T) * 3 * (size_t)max_m * RM;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Largest cluster size (about 16 rows per CTA, at most the portable 8) at
+// which all nparts clusters are resident together; 0 if none.
+template <typename T>
+int sweep_choice_t(int max_m, int max_r, int nparts) {
+  if (max_r > 16 || sizeof(T) * 3 * (size_t)max_m * (size_t)rbucket(max_r) > 227 * 1024) return 0;
+  if (nparts <= 0) return 0;
+  int cs = 1;
+  while (cs < 8 && cs * 16 < max_m) cs *= 2;
+  int chosen = 0;
+  narrow_dispatch(max_r, [&](auto rm) {
+    constexpr int RM = decltype(rm)::value;
+    allow_smem(k_sweep_solve_n<T, RM>, sizeof(T) * 3 * (size_t)max_m * RM);
+    for (int c = cs; c >= 1 && !chosen; c /= 2) {
+      cudaLaunchAttribute attr[1];
+      cudaLaunchConfig_t cfg = sweep_config<T, RM>(nparts, c, max_m, nullptr, attr);
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_sweep_solve_n<T, RM>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      if (nclusters >= nparts) chosen = c;
+    }
+  });
+  return chosen;
+}
+
+int sweep_cluster_choice(int elem_bytes, int max_m, int max_r, int nparts) {
+  return elem_bytes == 4 ? sweep_choice_t<float>(max_m, max_r, nparts) : sweep_choice_t<double>(max_m, max_r, nparts);
+}
+
+template <typename T>
+void launch_sweep_solve(const PartDesc* parts, int nparts, int cs, int max_m, int max_r, const double* A,
+                        const T* G, const T* Acal, const double* F, T* z, cudaStream_t st) {
+  if (nparts <= 0 || cs <= 0) return;
+  narrow_dispatch(max_r, [&](auto rm) {
+    constexpr int RM = decltype(rm)::value;
+    allow_smem(k_sweep_solve_n<T, RM>, sizeof(T) * 3 * (size_t)max_m * RM);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = sweep_config<T, RM>(nparts, cs, max_m, st, attr);
+    cudaLaunchKernelEx(&cfg, k_sweep_solve_n<T, RM>, parts, cs, A, G, Acal, F, z);
+  });
+}
+
 template <typename T>
 void launch_assemble_h(const SepDesc* seps, int nseps, int max_m, const double* A, const double* B,
                        const double* C, const T* ZL, const T* ZR, double* HA, double* HB,
@@ -1329,6 +1555,8 @@ void launch_axpy_norms(const SysDesc* sys, int nsys, int nrows, int max_m, int m
   template void launch_fwd_solve<T>(const PartDesc*, int, int, int, int, const double*, const T*,   \
                                     const double*, T*, cudaStream_t);                               \
   template void launch_back_solve<T>(const PartDesc*, int, int, int, int, const T*, T*, cudaStream_t); \
+  template void launch_sweep_solve<T>(const PartDesc*, int, int, int, int, const double*, const T*,   \
+                                      const T*, const double*, T*, cudaStream_t);                    \
   template void launch_assemble_h<T>(const SepDesc*, int, int, const double*, const double*,        \
                                      const double*, const T*, const T*, double*, double*, double*,  \
                                      cudaStream_t);                                                 \

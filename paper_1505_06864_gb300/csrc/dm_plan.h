@@ -15,7 +15,7 @@ namespace dm {
 // Kernel classes of the profiler (one per launcher).
 enum KClass {
   K_INV, K_FWD_FACTOR, K_BACK_FACTOR, K_ASSEMBLE_H, K_FWD_SOLVE, K_BACK_SOLVE, K_ASSEMBLE_F,
-  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_NCLASS
+  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_NCLASS
 };
 extern const char* const kClassNames[K_NCLASS];
 
@@ -30,8 +30,12 @@ struct Prof {
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  long long n[K_NCLASS] = {};
-  double ms[K_NCLASS] = {}, flops[K_NCLASS] = {}, bytes[K_NCLASS] = {};
+  // sums per class and recursion depth (0 = the top level; deeper levels
+  // share the last slot)
+  static constexpr int kDepths = 4;
+  int depth = 0;  // depth of the level whose kernels are being launched
+  long long n[K_NCLASS * kDepths] = {};
+  double ms[K_NCLASS * kDepths] = {}, flops[K_NCLASS * kDepths] = {}, bytes[K_NCLASS * kDepths] = {};
   cudaEvent_t take();
   void begin(cudaStream_t st, cudaEvent_t* e0);
   void end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, bool launched);
@@ -94,6 +98,9 @@ struct Level {
   void *G = nullptr, *Acal = nullptr, *ZL = nullptr, *ZR = nullptr, *z = nullptr;
   double *F = nullptr, *X = nullptr;  // right-hand sides and solutions (supplementary: fh and h)
   std::unique_ptr<Level> supp;
+  bool sweep = false;  // both z sweeps in one persistent cluster launch
+  int sweep_cs = 0;    // its cluster size
+  int depth = 0;  // 0 = the top level, 1 = its supplementary system, ...
   std::vector<void*> owned;
 
   int build(const std::vector<SysSpec>& specs, bool fp32_factors, int tensor_mode = -1);

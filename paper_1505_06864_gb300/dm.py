@@ -219,11 +219,13 @@ def dm_plan_query(plan) -> dict:
 
 
 def dm_profile(plan, enable=True):
-    """Per-kernel-class sums since the last call (launches, ms, flops, bytes);
-    then clears them and switches event timing on or off."""
-    buf = (dm_profile_entry * 32)()
+    """Per-kernel-class sums since the last call (launches, ms, flops, bytes),
+    keyed by class name ("fwd_factor") for the top level and "name@d" for the
+    supplementary system at recursion depth d; then clears them and switches
+    event timing on or off."""
+    buf = (dm_profile_entry * 64)()
     n = ctypes.c_int(0)
-    _check(lib().dm_profile(plan, 1 if enable else 0, buf, 32, ctypes.byref(n)))
+    _check(lib().dm_profile(plan, 1 if enable else 0, buf, 64, ctypes.byref(n)))
     return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
                                        bytes=buf[i].bytes) for i in range(n.value)}
 

@@ -360,3 +360,27 @@ def test_solve_last_row_only(dm, N, m, r, P, levels):
         dm.dm_destroy(plan)
     xo = o.dm(s.A, s.B, s.C, b, P, levels=levels, P2=P2 if P2 > 1 else None)
     check(xl[None], xo[-1:], TOL64)
+
+
+@pytest.mark.parametrize("N,m,r,P,levels,prec", [(64, 16, 1, 4, 1, "fp64"), (97, 40, 3, 7, 2, "fp64"),
+                                                 (130, 100, 5, 9, 2, "fp64"), (40, 200, 16, 6, 1, "fp64"),
+                                                 (33, 512, 2, 4, 1, "fp64"), (97, 40, 9, 7, 2, "fp32"),
+                                                 (70, 128, 8, 8, 2, "fp32"), (3, 5, 1, 2, 1, "fp64")])
+def test_solve_sweep_and_per_step_kernels(dm, monkeypatch, N, m, r, P, levels, prec):
+    """The persistent cluster sweep (default for <= 16 right-hand sides) and
+    the per-step solve kernels (DM_SOLVE_SWEEP=0) against the oracle, on
+    ragged rows per CTA (m = 5, 40, 100, 200), the largest block (m = 512)
+    and the column buckets 1..16."""
+    s = w.dominant_system(N, m, r, 11)
+    tol = TOL64 if prec == "fp64" else TOLMIX
+    out, xref = {}, None
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DM_SOLVE_SWEEP", flag)
+        x, rel, info = solve(dm, s, P, levels, prec)
+        if xref is None:
+            xref = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
+        check(x, xref, tol)
+        assert rel < (1e-13 if prec == "fp64" else 1e-12)
+        out[flag] = x
+    monkeypatch.delenv("DM_SOLVE_SWEEP")
+    check(out["1"], out["0"], tol)
