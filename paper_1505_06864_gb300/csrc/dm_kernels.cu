@@ -17,7 +17,11 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 #include <type_traits>
 #include <unordered_map>
 
@@ -404,6 +408,432 @@ __global__ void __launch_bounds__(256) k_inv_cluster(const PartDesc* __restrict_
   for (int e = tid; e < m * wc; e += nthr) {
     const int i = e / wc, jl = e - i * wc;
     g[(long long)i * m + inv_idx[c0 + jl]] = a[i * lda + jl];
+  }
+  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Blocked form of the same Gauss-Jordan inverse (partial pivoting inside the
+// block, column unscramble at the end): the columns are processed in panels
+// of NB.  The CTA that owns a panel's columns eliminates the panel alone (one
+// warp, warp-synchronous: pivot search by shuffles, row exchange, scaling and
+// elimination restricted to the panel), which leaves the panel holding the
+// NB non-trivial columns of the panel's composed elimination matrix
+// M = I + X.  After one cluster barrier every CTA copies the panel and its
+// pivots (distributed shared memory), applies the exchanges to its own
+// columns, keeps the NB pivot rows Y, and applies the rank-NB update
+//   a[i][j] <- (i a pivot row of the panel ? 0 : a[i][j]) + sum_l M[i][l] Y[l][j]
+// to its other columns.  Lookahead: the owner of the next panel updates that
+// panel's columns first, and its warp 0 eliminates the next panel while the
+// other warps finish the update, so a panel costs one cluster barrier and the
+// elimination of the next panel is hidden behind the update.  All loop bounds
+// are uniform over the cluster; a final barrier keeps every CTA's shared
+// memory alive until the last remote read.
+struct InvPanel {
+  int owner, kl0, nbk, k0;
+};
+
+__host__ __device__ __forceinline__ size_t up16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename T, int NB>
+__host__ __device__ size_t inv_blocked_layout(int m, int w, size_t* off_pan, size_t* off_y, size_t* off_perm) {
+  const size_t a = up16(sizeof(T) * (size_t)m * (w + 1));
+  const size_t pan = up16(sizeof(T) * (size_t)m * NB);
+  const size_t y = up16(sizeof(T) * (size_t)NB * w);
+  if (off_pan) *off_pan = a;
+  if (off_y) *off_y = a + pan;
+  if (off_perm) *off_perm = a + pan + y;
+  return a + pan + y + 3 * sizeof(int) * (size_t)m;
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_inv_blocked(const PartDesc* __restrict__ parts, int t,
+                                                     const double* __restrict__ B, T* __restrict__ G,
+                                                     int* __restrict__ status, int cs) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const PartDesc p = parts[blockIdx.x / cs];
+  if (t >= p.L) return;  // the same for every CTA of the cluster
+  const int m = p.m;
+  const int w = (m + cs - 1) / cs, c0 = rank * w, wc = max(0, min(w, m - c0));
+  const int lda = w + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  size_t op, oy, oq;
+  inv_blocked_layout<T, NB>(m, w, &op, &oy, &oq);
+  T* a = reinterpret_cast<T*>(smem_raw);           // [m][lda]: this CTA's columns
+  T* pan = reinterpret_cast<T*>(smem_raw + op);    // [m][NB]: the current panel
+  T* Y = reinterpret_cast<T*>(smem_raw + oy);      // [NB][w]: pivot rows of the own columns
+  int* perm = reinterpret_cast<int*>(smem_raw + oq);
+  int* idx = perm + m;
+  int* inv_idx = idx + m;
+  __shared__ int s_bad;
+  const long long o = p.blk + (long long)t * m * m;
+  T* g = G + o;
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < m * wc; e += blockDim.x) {
+    const int i = e / wc, jl = e - i * wc;
+    a[i * lda + jl] = (t == 0) ? (T)B[o + (long long)i * m + c0 + jl] : g[(long long)i * m + c0 + jl];
+  }
+  __syncthreads();
+
+  // panels in column order: owner r, local columns [kl0, kl0 + nbk)
+  auto owner_cols = [&](int r) { return max(0, min(w, m - r * w)); };
+  auto first_panel = [&]() { return InvPanel{0, 0, min(NB, owner_cols(0)), 0}; };
+  auto next_panel = [&](InvPanel q) {
+    q.kl0 += NB;
+    if (q.kl0 >= owner_cols(q.owner)) {
+      q.owner += 1;
+      q.kl0 = 0;
+    }
+    q.nbk = q.owner < cs ? min(NB, owner_cols(q.owner) - q.kl0) : 0;
+    q.k0 = q.owner * w + q.kl0;
+    return q;
+  };
+
+  // Elimination of a panel by one warp (columns kl0.. of this CTA, rows 0..m-1).
+  auto eliminate = [&](const InvPanel& q) {
+    for (int j = 0; j < q.nbk; ++j) {
+      const int k = q.k0 + j, kl = q.kl0 + j;
+      T best = (T)-1;
+      int bi = k;
+      for (int i = k + lane; i < m; i += 32) {
+        const T v = fabs(a[i * lda + kl]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      bi = __shfl_sync(0xffffffffu, bi, 0);
+      if (bi != k && lane < q.nbk) {
+        T* rk = a + k * lda + q.kl0 + lane;
+        T* rp = a + bi * lda + q.kl0 + lane;
+        const T tmp = *rk;
+        *rk = *rp;
+        *rp = tmp;
+      }
+      if (lane == 0) perm[k] = bi;
+      __syncwarp();
+      const T piv = a[k * lda + kl];
+      T inv = (T)1 / piv;
+      if (!(fabs(piv) > (T)0) || !isfinite(inv)) {
+        inv = (T)0;
+        if (lane == 0) s_bad = 1;
+      }
+      T rk[NB];
+#pragma unroll
+      for (int l = 0; l < NB; ++l) rk[l] = l < q.nbk ? a[k * lda + q.kl0 + l] * inv : (T)0;
+      __syncwarp();
+      for (int i = lane; i < m; i += 32) {
+        T* ai = a + i * lda + q.kl0;
+        if (i == k) {
+#pragma unroll
+          for (int l = 0; l < NB; ++l)
+            if (l < q.nbk) ai[l] = (l == j) ? inv : rk[l];
+        } else {
+          const T cik = ai[j];
+#pragma unroll
+          for (int l = 0; l < NB; ++l)
+            if (l < q.nbk) ai[l] = (l == j) ? -cik * inv : fma(-cik, rk[l], ai[l]);
+        }
+      }
+      __syncwarp();
+    }
+  };
+
+  // Rank-NB update of local columns jl in [lo, hi) except [x0, x1) and
+  // [y0, y1), by warps wf .. wf + nw - 1 (lanes over columns, warps over rows).
+  auto update = [&](const InvPanel& q, int lo, int hi, int x0, int x1, int y0, int y1, int wf, int nw) {
+    const int wi = warp - wf;
+    if (wi < 0 || wi >= nw) return;
+    for (int jl = lo + lane; jl < hi; jl += 32) {
+      if ((jl >= x0 && jl < x1) || (jl >= y0 && jl < y1)) continue;
+      T yc[NB];
+#pragma unroll
+      for (int l = 0; l < NB; ++l) yc[l] = Y[l * w + jl];
+      for (int i = wi; i < m; i += nw) {
+        const T* pi = pan + i * NB;
+        T acc = (i >= q.k0 && i < q.k0 + q.nbk) ? (T)0 : a[i * lda + jl];
+#pragma unroll
+        for (int l = 0; l < NB; ++l) acc = fma(pi[l], yc[l], acc);
+        a[i * lda + jl] = acc;
+      }
+    }
+  };
+
+  InvPanel q = first_panel();
+  if (rank == q.owner && warp == 0) eliminate(q);
+  while (q.owner < cs && q.nbk > 0) {
+    cl.sync();  // panel q eliminated by its owner
+    const bool own = rank == q.owner;
+    const T* ra = cl.map_shared_rank(a, q.owner);
+    const int* rperm = cl.map_shared_rank(perm, q.owner);
+    for (int e = tid; e < m * NB; e += blockDim.x) {
+      const int i = e / NB, l = e - i * NB;
+      pan[e] = l < q.nbk ? ra[i * lda + q.kl0 + l] : (T)0;
+    }
+    if (tid < q.nbk) perm[q.k0 + tid] = rperm[q.k0 + tid];
+    __syncthreads();
+    // exchanges and pivot rows of the own columns (the owner's panel excluded)
+    const int x0 = own ? q.kl0 : 0, x1 = own ? q.kl0 + q.nbk : 0;
+    for (int jl = tid; jl < wc; jl += blockDim.x) {
+      if (jl >= x0 && jl < x1) continue;
+      for (int l = 0; l < q.nbk; ++l) {
+        const int k = q.k0 + l, pr = perm[k];
+        if (pr != k) {
+          const T tmp = a[k * lda + jl];
+          a[k * lda + jl] = a[pr * lda + jl];
+          a[pr * lda + jl] = tmp;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < NB; ++l) Y[l * w + jl] = l < q.nbk ? a[(q.k0 + l) * lda + jl] : (T)0;
+    }
+    __syncthreads();
+    const InvPanel q1 = next_panel(q);
+    const bool next_here = q1.owner < cs && q1.nbk > 0 && rank == q1.owner;
+    if (next_here) {
+      update(q, q1.kl0, q1.kl0 + q1.nbk, x0, x1, 0, 0, 0, 8);
+      __syncthreads();
+      if (warp == 0)
+        eliminate(q1);
+      else
+        update(q, 0, wc, x0, x1, q1.kl0, q1.kl0 + q1.nbk, 1, 7);
+    } else {
+      update(q, 0, wc, x0, x1, 0, 0, 0, 8);
+    }
+    q = q1;
+  }
+  cl.sync();  // every remote read of this CTA's columns is done
+  if (tid == 0) {
+    for (int c = 0; c < m; ++c) idx[c] = c;
+    for (int k = m - 1; k >= 0; --k) {
+      const int r = perm[k];
+      const int tmp = idx[k];
+      idx[k] = idx[r];
+      idx[r] = tmp;
+    }
+    for (int c = 0; c < m; ++c) inv_idx[idx[c]] = c;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * wc; e += blockDim.x) {
+    const int i = e / wc, jl = e - i * wc;
+    g[(long long)i * m + inv_idx[c0 + jl]] = a[i * lda + jl];
+  }
+  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident Gauss-Jordan inverse (Section 3's explicit block inverse;
+// partial pivoting inside the block), columns split over a cluster of cs CTAs
+// (cs = 1: one CTA).  Each CTA holds the m x w slab of its columns in
+// registers: a 32 x 32 thread grid, thread (ty = lane, tx = warp) owning rows
+// ty + 32a (a < RT) and local columns tx + 32b (b < CT), so a warp holds whole
+// columns.  Pivoting is implicit: rows are never exchanged; step k takes the
+// unused row p_k with the largest |a[i][k]| as its pivot row, and the working
+// matrix ends as W[p_r][c] = inv(D)[r][p_c], written out in that order.
+// Step k (one barrier):
+//   * the warp owning column k (in the owner CTA) has published the column,
+//     p_k and 1 / pivot (its pivot search ran at the end of step k-1:
+//     warp-wide max of |a| then min of the row index among the maxima);
+//   * every thread reads the column for its rows (distributed shared memory
+//     in a cluster), takes row p_k of its columns from lane p_k mod 32 of its
+//     own warp by a shuffle, and applies the rank-1 update in registers,
+//     fixing up row p_k and column k;
+//   * the warp owning column k+1 searches and publishes its pivot.
+// The slab is staged through shared memory on entry and exit (coalesced
+// global traffic).  Loop bounds are uniform over the cluster; a final barrier
+// keeps every CTA's shared memory alive until the last remote read.
+constexpr int kInvRegThreads = 1024;
+
+template <typename T>
+__host__ __device__ size_t inv_reg_smem(int m, int w) {
+  // slab [m][w+1] + published columns [2][m] + published reciprocals [2] (T),
+  // then pivot row per step [m] and published pivot rows [2] (int)
+  return sizeof(T) * ((size_t)m * (w + 1) + 2 * (size_t)m + 2) + sizeof(int) * ((size_t)m + 2);
+}
+
+// f(integral_constant<I>) for the I in [0, N) equal to v (uniform v: one
+// branch taken, the others skipped), so register arrays stay statically
+// indexed.
+template <int N, int I = 0, typename F>
+__device__ __forceinline__ void dispatch_index(int v, F&& f) {
+  if constexpr (I < N) {
+    if (v == I)
+      f(std::integral_constant<int, I>());
+    else
+      dispatch_index<N, I + 1>(v, f);
+  }
+}
+
+// Warp-wide argmax of v >= 0 (lowest index among equal maxima; lanes
+// without a candidate pass idx = m).
+__device__ __forceinline__ int warp_argmax(float v, int idx) {
+  const unsigned bits = idx < INT_MAX ? __float_as_uint(v) : 0u;
+  const unsigned vmax = __reduce_max_sync(0xffffffffu, bits);
+  return (int)__reduce_min_sync(0xffffffffu, bits == vmax ? (unsigned)idx : 0xffffffffu);
+}
+__device__ __forceinline__ int warp_argmax(double v, int idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  return idx;
+}
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
+template <typename T, int RT, int CT>
+__global__ void __launch_bounds__(kInvRegThreads) k_inv_reg(const PartDesc* __restrict__ parts, int t,
+                                                            const double* __restrict__ B, T* __restrict__ G,
+                                                            int* __restrict__ status, int cs) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const PartDesc p = parts[blockIdx.x / cs];
+  if (t >= p.L) return;  // the same for every CTA of the cluster
+  const int m = p.m;
+  const int w = (m + cs - 1) / cs, c0 = rank * w, wc = max(0, min(w, m - c0));
+  const int lds = w + 1;
+  const int tid = threadIdx.x;
+  const int ty = tid & 31, tx = tid >> 5;
+  T* slab = reinterpret_cast<T*>(smem_raw);  // [m][lds]
+  T* pubc = slab + (size_t)m * lds;          // [2][m]: published column k
+  T* pubinv = pubc + 2 * (size_t)m;          // [2]: published 1 / pivot
+  int* pivrow = reinterpret_cast<int*>(pubinv + 2);  // [m]: pivot row of step k
+  int* pubp = pivrow + m;                            // [2]: published pivot row
+  __shared__ int s_bad;
+  const long long o = p.blk + (long long)t * m * m;
+  T* g = G + o;
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < m * wc; e += blockDim.x) {
+    const int i = e / wc, jl = e - i * wc;
+    slab[i * lds + jl] = (t == 0) ? (T)B[o + (long long)i * m + c0 + jl] : g[(long long)i * m + c0 + jl];
+  }
+  __syncthreads();
+  T A[RT][CT];
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < CT; ++b) {
+      const int i = ty + 32 * a, jl = tx + 32 * b;
+      A[a][b] = (i < m && jl < wc) ? slab[i * lds + jl] : (T)0;
+    }
+  unsigned used = 0;  // bit a: row ty + 32a has been a pivot row
+
+  // Pivot search of column k by the warp owning it (NaN counted as 0) and
+  // publication of the column, the pivot row and the pivot's reciprocal (0
+  // for a zero or non-finite pivot, which also flags the block).
+  auto search = [&](int k) {
+    T* pc = pubc + (k & 1) * m;
+    dispatch_index<CT>((k - c0) >> 5, [&](auto bc) {
+      constexpr int BK = decltype(bc)::value;
+      T best = (T)0;
+      int bi = INT_MAX;
+#pragma unroll
+      for (int a = 0; a < RT; ++a) {
+        const int i = ty + 32 * a;
+        const T x = A[a][BK];
+        if (i < m) {
+          pc[i] = x;
+          T v = fabs(x);
+          if (!(v >= (T)0)) v = (T)0;
+          if (!((used >> a) & 1u) && (bi == INT_MAX || v > best)) { best = v; bi = i; }
+        }
+      }
+      const int pk = warp_argmax(best, bi);
+      __syncwarp();
+      if (ty == 0) {
+        const int q = min(max(pk, 0), m - 1);
+        const T piv = pc[q];
+        T inv = recip(piv);
+        if (!(fabs(piv) > (T)0) || !isfinite(inv)) {
+          inv = (T)0;
+          s_bad = 1;
+        }
+        pubp[k & 1] = q;
+        pubinv[k & 1] = inv;
+      }
+    });
+  };
+
+  auto owner_of = [&](int k) { return k / w; };
+  if (rank == 0 && tx == 0) search(0);
+  for (int k = 0; k < m; ++k) {
+    const int ok = owner_of(k), jk = k - ok * w;
+    if (cs > 1) cl.sync(); else __syncthreads();  // column k, p_k, 1 / pivot published
+    const T* pc = pubc + (k & 1) * m;
+    int pk;
+    T inv;
+    T c[RT];
+    if (cs > 1) {
+      const T* rc = cl.map_shared_rank(pc, ok);
+      pk = *cl.map_shared_rank(pubp + (k & 1), ok);
+      inv = *cl.map_shared_rank(pubinv + (k & 1), ok);
+#pragma unroll
+      for (int a = 0; a < RT; ++a) {
+        const int i = ty + 32 * a;
+        c[a] = i < m ? rc[i] : (T)0;
+      }
+    } else {
+      pk = pubp[k & 1];
+      inv = pubinv[k & 1];
+#pragma unroll
+      for (int a = 0; a < RT; ++a) {
+        const int i = ty + 32 * a;
+        c[a] = i < m ? pc[i] : (T)0;
+      }
+    }
+    const int ap = pk >> 5, lp = pk & 31;
+    // row p_k of this warp's columns, from the lane that holds it
+    T rs[CT];
+    dispatch_index<RT>(ap, [&](auto ac) {
+      constexpr int AP = decltype(ac)::value;
+#pragma unroll
+      for (int b = 0; b < CT; ++b) rs[b] = __shfl_sync(0xffffffffu, A[AP][b], lp) * inv;
+    });
+    if (ty == lp) used |= 1u << ap;
+    if (tid == 0) pivrow[k] = pk;
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < CT; ++b) A[a][b] = fma(-c[a], rs[b], A[a][b]);
+    if (ty == lp)
+      dispatch_index<RT>(ap, [&](auto ac) {
+        constexpr int AP = decltype(ac)::value;
+#pragma unroll
+        for (int b = 0; b < CT; ++b) A[AP][b] = rs[b];
+      });
+    if (rank == ok && tx == (jk & 31))
+      dispatch_index<CT>(jk >> 5, [&](auto bc) {
+        constexpr int BK = decltype(bc)::value;
+#pragma unroll
+        for (int a = 0; a < RT; ++a) A[a][BK] = (ty + 32 * a == pk) ? inv : -c[a] * inv;
+      });
+    // lookahead: the warp owning column k+1 searches its pivot now
+    const int k1 = k + 1;
+    if (k1 < m && rank == owner_of(k1) && tx == ((k1 - owner_of(k1) * w) & 31)) search(k1);
+  }
+  if (cs > 1) cl.sync(); else __syncthreads();  // every remote read of this CTA is done
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < CT; ++b) {
+      const int i = ty + 32 * a, jl = tx + 32 * b;
+      if (i < m && jl < wc) slab[i * lds + jl] = A[a][b];
+    }
+  __syncthreads();
+  // inv(D)[r][p_c] = W[p_r][c] for the columns c = c0 .. c0+wc-1 of W held here
+  for (int e = tid; e < m * wc; e += blockDim.x) {
+    const int r = e / wc, jl = e - r * wc;
+    g[(long long)r * m + pivrow[c0 + jl]] = slab[pivrow[r] * lds + jl];
   }
   if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
 }
@@ -1240,20 +1670,21 @@ int inv_cluster_size(int max_m) {
   return cs;
 }
 
-// Whether a cluster of cs CTAs with `bytes` of shared memory each can run.
-template <typename T>
-bool inv_cluster_ok(int cs, size_t bytes) {
+// Whether a cluster of cs CTAs of `kernel` with `bytes` of shared memory each
+// can run (cached per kernel, size and bytes).
+template <typename K>
+bool cluster_ok(K kernel, int cs, size_t bytes, int threads = 256) {
   static std::mutex mu;
-  static std::unordered_map<long long, bool> known;
-  const long long key = (long long)cs * (1ll << 32) + (long long)bytes;
+  static std::map<std::tuple<const void*, int, size_t>, bool> known;
+  const auto key = std::make_tuple(reinterpret_cast<const void*>(kernel), cs, bytes);
   std::lock_guard<std::mutex> lk(mu);
   auto it = known.find(key);
   if (it != known.end()) return it->second;
-  if (cs > 8) cudaFuncSetAttribute(k_inv_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  allow_smem(k_inv_cluster<T>, bytes);
+  if (cs > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  allow_smem(kernel, bytes);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = bytes;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1263,10 +1694,92 @@ bool inv_cluster_ok(int cs, size_t bytes) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_inv_cluster<T>, &cfg) == cudaSuccess && nclusters > 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) == cudaSuccess && nclusters > 0;
   cudaGetLastError();
   known[key] = ok;
   return ok;
+}
+
+template <typename K, typename... Args>
+void launch_cluster(K kernel, int nclusters, int cs, int threads, size_t bytes, cudaStream_t st, Args... args) {
+  allow_smem(kernel, bytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * cs);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// DM_INV_KERNEL=column / reg / panel forces one float32 inverse (for
+// comparisons; reg falls back to column above m = 128).  0 = column,
+// 1 = automatic, 2 = panel, 3 = reg.
+int inv_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("DM_INV_KERNEL");
+    if (!e) return 1;
+    const std::string s(e);
+    return s == "column" ? 0 : s == "panel" ? 2 : s == "reg" ? 3 : 1;
+  }();
+  return v;
+}
+
+int device_sms() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> known;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find(dev);
+  if (it != known.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  known[dev] = sms;
+  return sms;
+}
+
+// Thread tile (RT rows x CT columns per thread, 16 x 16 threads per CTA) and
+// cluster size of the register-resident inverse for blocks up to max_m:
+// float64 about 32 columns per CTA (the FP64 work of a block spread over
+// several SMs), float32 up to 128 columns per CTA; at most 64 elements per
+// thread.
+template <typename T>
+void inv_reg_shape(int max_m, int* rt, int* ct, int* cs) {
+  auto p2 = [](int v) { int q = 1; while (q < v) q *= 2; return q; };
+  const int r = p2((max_m + 31) / 32);
+  const int per = sizeof(T) == 8 ? 32 : (max_m <= 128 ? 128 : 64);
+  int c = 1;
+  while (c * per < max_m) c *= 2;
+  int w = (max_m + c - 1) / c;
+  int cc = p2((w + 31) / 32);
+  while (r * cc > 16 && c < 16) {
+    c *= 2;
+    w = (max_m + c - 1) / c;
+    cc = p2((w + 31) / 32);
+  }
+  if (r > 16 || r * cc > 16) { *rt = *ct = *cs = 0; return; }
+  *rt = r;
+  *ct = cc;
+  *cs = c;
+}
+
+template <typename T, typename F>
+void inv_reg_dispatch(int rt, int ct, F&& f) {
+#define DM_INV_REG_CASE(R, C) \
+  if (rt == R && ct == C) return f(k_inv_reg<T, R, C>);
+  DM_INV_REG_CASE(1, 1) DM_INV_REG_CASE(2, 1) DM_INV_REG_CASE(2, 2) DM_INV_REG_CASE(4, 1) DM_INV_REG_CASE(4, 2)
+  DM_INV_REG_CASE(4, 4) DM_INV_REG_CASE(8, 1) DM_INV_REG_CASE(8, 2) DM_INV_REG_CASE(16, 1)
+#undef DM_INV_REG_CASE
 }
 
 template <typename T>
@@ -1274,22 +1787,40 @@ void launch_inv(const PartDesc* parts, int nparts, int t, const double* B, T* G,
                 int max_m, cudaStream_t st) {
   if (nparts <= 0) return;
   const int cs = inv_cluster_size<T>(max_m);
+  // float32: the register-resident inverse while the blocks of a launch
+  // leave SMs idle (latency-bound, up to m = 128), the panel-blocked inverse
+  // when there are enough blocks to fill the GPU several times over
+  // (throughput-bound); float64: column by column, whose per-pivot update
+  // spreads the FP64 work over every warp of the cluster.
+  if (sizeof(T) == 4 && inv_variant() != 0) {
+    const bool many = inv_variant() == 3 ? false : nparts >= 2 * device_sms();
+    if (!many && max_m <= 128 && inv_variant() != 2) {
+      int rc = 0, cc = 0, ics = 0;
+      inv_reg_shape<T>(max_m, &rc, &cc, &ics);
+      const size_t bytes = inv_reg_smem<T>(max_m, (max_m + ics - 1) / ics);
+      if (ics > 0 && bytes <= 227 * 1024) {
+        bool launched = false;
+        inv_reg_dispatch<T>(rc, cc, [&](auto kern) {
+          if (ics <= 8 || cluster_ok(kern, ics, bytes, kInvRegThreads)) {
+            launch_cluster(kern, nparts, ics, kInvRegThreads, bytes, st, parts, t, B, G, status, ics);
+            launched = true;
+          }
+        });
+        if (launched) return;
+      }
+    }
+    if (cs <= 16 && (many || inv_variant() == 2)) {
+      constexpr int NB = 8;
+      const size_t bytes = inv_blocked_layout<T, NB>(max_m, (max_m + cs - 1) / cs, nullptr, nullptr, nullptr);
+      if (bytes <= 227 * 1024 && (cs <= 8 || cluster_ok(k_inv_blocked<T, NB>, cs, bytes))) {
+        launch_cluster(k_inv_blocked<T, NB>, nparts, cs, 256, bytes, st, parts, t, B, G, status, cs);
+        return;
+      }
+    }
+  }
   const size_t bytes = inv_cluster_smem<T>(max_m, cs);
-  if (cs <= 16 && bytes <= 227 * 1024 && (cs <= 8 || inv_cluster_ok<T>(cs, bytes))) {
-    allow_smem(k_inv_cluster<T>, bytes);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nparts * cs);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = bytes;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_inv_cluster<T>, parts, t, B, G, status, cs);
+  if (cs <= 16 && bytes <= 227 * 1024 && (cs <= 8 || cluster_ok(k_inv_cluster<T>, cs, bytes))) {
+    launch_cluster(k_inv_cluster<T>, nparts, cs, 256, bytes, st, parts, t, B, G, status, cs);
     return;
   }
   // no cluster fits: one CTA per block, working matrix in global memory
