@@ -58,6 +58,11 @@ extern "C" {
 #define DM_TF32 2    /* tcgen05 kind::tf32 block products, float32 accumulate + refinement */
 #define DM_BF16X3 3  /* tcgen05 kind::f16 split-bf16 (hi*hi + hi*lo + lo*hi) + refinement */
 
+/* How the residual r = b - T x is computed (dm_set_residual). */
+#define DM_RESIDUAL_FP64 0   /* float64 fused multiply-adds on the CUDA cores */
+#define DM_RESIDUAL_SLICED 1 /* exact bf16 slice products on the tensor cores, float64-accurate */
+#define DM_RESIDUAL_AUTO 2   /* SLICED for the systems where it is faster (m^2 nrhs >= 2^17), else FP64 */
+
 typedef struct dm_plan_s* dm_plan_t;
 
 /* Facts about a plan, filled by dm_plan_query. */
@@ -75,6 +80,8 @@ typedef struct dm_plan_info {
   double last_correction;/* last refinement step ||dx||_2 / ||x||_2 (0 for DM_FP64) */
   double factor_flops;   /* algorithmic flops of one dm_factor (2 per multiply-add) */
   double solve_flops;    /* algorithmic flops of one solve sweep (without refinement) */
+  int residual_mode;     /* DM_RESIDUAL_FP64 or DM_RESIDUAL_SLICED */
+  int residual_tc_systems; /* systems whose residual runs on the tensor cores */
 } dm_plan_info;
 
 /* Plan the solution of one system of N block rows, blocks m x m, nrhs
@@ -250,6 +257,29 @@ int dm_set_side_stream(dm_plan_t plan, int enable);
 /* Optional settings and queries. */
 int dm_set_stream(dm_plan_t plan, void* cuda_stream);            /* cudaStream_t for the plan's launches */
 int dm_set_refinement(dm_plan_t plan, double tol, int max_iters); /* default 1e-12, 30 */
+
+/* Residual method (the paper has none: it stops at the direct solve; the
+ * refinement of the mixed precisions needs r = b - T x in float64 accuracy).
+ * DM_RESIDUAL_SLICED cuts every float64 entry of a block row [A_i B_i C_i]
+ * and of [x_{i-1}; x_i; x_{i+1}] into nine 6-bit digits scaled by the row's
+ * (column's) largest power of two, multiplies digit matrices exactly on the
+ * bf16 tensor cores (integer partial sums below 2^24 in float32), and sums
+ * the digit products in float64: error per entry below
+ * 3m 2^-50 max|row of [A B C]| max|column of x|, the float64 dot product's own
+ * bound.  It serves systems with m <= 128 and nrhs <= 16; the others of the
+ * plan use DM_RESIDUAL_FP64.  DM_RESIDUAL_AUTO picks SLICED per system where
+ * it measured faster on GB300 (m^2 nrhs >= 2^17: m = 128 with nrhs >= 8,
+ * m = 96 with nrhs >= 15): the float64 kernel's cost grows with nrhs, the
+ * sliced kernel's mostly with m^2.  Default: AUTO for DM_FP32 / DM_TF32 /
+ * DM_BF16X3 plans, FP64 for DM_FP64 plans.  DM_EINVAL for other modes. */
+int dm_set_residual(dm_plan_t plan, int mode);
+
+/* r = b - T x with the plan's blocks (after dm_factor) in the plan's residual
+ * mode; x, b, r are [N][m][nrhs] float64 (host or device; r may alias b),
+ * relres_out (may be NULL) receives max over columns of ||r|| / ||b||.  For
+ * checking a solution computed elsewhere, or a residual method against
+ * another.  DM_ESTATE before dm_factor. */
+int dm_residual(dm_plan_t plan, const double* x, const double* b, double* r, double* relres_out);
 int dm_plan_query(dm_plan_t plan, dm_plan_info* info);
 void dm_destroy(dm_plan_t plan);
 const char* dm_last_error(void);

@@ -97,6 +97,7 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
   }
   // subsystem and separator tables
   nrows = 0;
+  long long eoff = 0;
   parts.clear();
   seps.clear();
   sysd.clear();
@@ -108,6 +109,9 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     sd.N = sp.N;
     sd.m = sp.m;
     sd.r = sp.r;
+    sd.sliced = 0;
+    sd.eoff = (int)eoff;
+    eoff += (long long)sp.N * sp.m;
     sd.row0 = nrows;
     nrows += sp.N;
     sysd.push_back(sd);
@@ -693,8 +697,24 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   if ((rc = alloc((void**)&R, top.nvec * sizeof(double)))) return rc;
   if ((rc = alloc((void**)&Dx, top.nvec * sizeof(double)))) return rc;
   if ((rc = alloc((void**)&nrm, (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double)))) return rc;
+  {
+    long long rows = 0;
+    for (const SysDesc& d : top.sysd) rows += (long long)d.N * d.m;
+    if ((rc = alloc((void**)&rowhi, (size_t)std::max(1ll, rows) * sizeof(unsigned)))) return rc;
+    if ((rc = alloc((void**)&colhi, (size_t)std::max(1, top.nrows) * 16 * sizeof(unsigned)))) return rc;
+  }
   h_nrm.assign((size_t)std::max(1, top.nsys) * 4 * kMaxR, 0.0);
   relres.assign(std::max(1, top.nsys), 0.0);
+  {
+    // mixed precision refines with many residuals: tensor cores by default;
+    // DM_RESIDUAL=fp64 / sliced overrides (for comparisons)
+    int mode = prec == DM_FP64 ? DM_RESIDUAL_FP64 : DM_RESIDUAL_AUTO;
+    const char* e = std::getenv("DM_RESIDUAL");
+    if (e && std::string(e) == "fp64") mode = DM_RESIDUAL_FP64;
+    if (e && std::string(e) == "sliced") mode = DM_RESIDUAL_SLICED;
+    if (e && std::string(e) == "auto") mode = DM_RESIDUAL_AUTO;
+    if ((rc = set_residual_mode(mode))) return rc;
+  }
   level_flops(top, &factor_flops, &solve_flops);
   device_bytes = top.bytes_needed() - 3 * top.nblk * sizeof(double) + 2 * top.nvec * sizeof(double);
   return DM_OK;
@@ -704,6 +724,8 @@ Plan::~Plan() {
   if (R) cudaFree(R);
   if (Dx) cudaFree(Dx);
   if (nrm) cudaFree(nrm);
+  if (rowhi) cudaFree(rowhi);
+  if (colhi) cudaFree(colhi);
   reset_graphs();
   if (own_stream) cudaStreamDestroy(own_stream);
   if (aux.st) cudaStreamDestroy(aux.st);
@@ -737,7 +759,10 @@ int Plan::factor(const double* A, const double* B, const double* C) {
     if ((rc = copy_in(top.B, B, top.nblk * sizeof(double), st))) return rc;
     if ((rc = copy_in(top.C, C, top.nblk * sizeof(double), st))) return rc;
   }
-  rc = run(g_factor, [&] { factor_level(top, stream, prof, overlap ? &aux : nullptr); });
+  rc = run(g_factor, [&] {
+    factor_level(top, stream, prof, overlap ? &aux : nullptr);
+    row_scales();
+  });
   if (rc) return rc;
   rc = check_status(top, st, 0);
   factored = (rc == DM_OK);
@@ -756,6 +781,68 @@ static double col_ratio(const std::vector<double>& h, int s, int r, int num, int
   return worst;
 }
 
+// Residual mode: the tensor-core residual for every system it fits (m <= 128,
+// nrhs <= 16; SLICED) or for those where it is faster (AUTO), float64 CUDA
+// cores for the others (or for all in FP64 mode).
+int Plan::set_residual_mode(int mode) {
+  if (mode != DM_RESIDUAL_FP64 && mode != DM_RESIDUAL_SLICED && mode != DM_RESIDUAL_AUTO)
+    return set_error(DM_EINVAL, "unknown residual mode %d", mode);
+  resid_mode = mode;
+  top.nres_tc = 0;
+  top.c_resid_tc = Cost();
+  for (SysDesc& d : top.sysd) {
+    const bool fits = residual_sliced_fits(d.m, d.r);
+    const bool faster = (long long)d.m * d.m * d.r >= (1ll << 17);
+    d.sliced = (fits && (mode == DM_RESIDUAL_SLICED || (mode == DM_RESIDUAL_AUTO && faster))) ? 1 : 0;
+    if (d.sliced) {
+      const double m2 = (double)d.m * d.m, mr = (double)d.m * d.r;
+      ++top.nres_tc;
+      top.c_resid_tc.flops += d.N * 6.0 * m2 * d.r;
+      top.c_resid_tc.bytes += d.N * (24.0 * m2 + 24.0 * mr);
+    }
+  }
+  if (top.d_sys && !top.sysd.empty())
+    DM_CUDA(cudaMemcpy(top.d_sys, top.sysd.data(), top.sysd.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+  reset_graphs();
+  if (factored) {
+    row_scales();
+    DM_CUDA(cudaStreamSynchronize(stream));
+  }
+  return DM_OK;
+}
+
+void Plan::residual(const double* x_dev, const double* b_dev, double* r_dev) {
+  Cost c64 = top.c_resid;
+  c64.flops -= top.c_resid_tc.flops;
+  c64.bytes -= top.c_resid_tc.bytes;
+  DM_LAUNCH(prof, stream, K_RESIDUAL, c64, top.nsys - top.nres_tc,
+            launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                            b_dev, r_dev, nrm, stream));
+  if (top.nres_tc > 0) {
+    DM_LAUNCH(prof, stream, K_RESIDUAL, Cost(), top.nres_tc,
+              launch_col_scales(top.d_sys, top.nsys, top.nrows, x_dev, colhi, stream));
+    DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid_tc, top.nres_tc,
+              launch_residual_sliced(top.d_sys, top.nsys, top.nrows, top.A, top.B, top.C, x_dev, b_dev, r_dev, nrm,
+                                     rowhi, colhi, top.d_err, stream));
+  }
+}
+
+void Plan::row_scales() {
+  if (top.nres_tc > 0)
+    DM_LAUNCH(prof, stream, K_RESIDUAL, Cost(), top.nres_tc,
+              launch_row_scales(top.d_sys, top.nsys, top.nrows, top.A, top.B, top.C, rowhi, stream));
+}
+
+// after a synchronisation: a tensor-core residual whose bounded wait expired
+int Plan::check_residual_error() {
+  if (top.nres_tc == 0) return DM_OK;
+  int herr = 0;
+  DM_CUDA(cudaMemcpyAsync(&herr, top.d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  DM_CUDA(cudaStreamSynchronize(stream));
+  if (herr) return set_error(DM_ETIMEOUT, "a tensor-core residual wait expired");
+  return DM_OK;
+}
+
 int Plan::solve_device(const double* b_dev, double* x_dev) {
   cudaStream_t st = stream;
   const size_t nb = (size_t)std::max(1, top.nsys) * 4 * kMaxR * sizeof(double);
@@ -763,15 +850,14 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
     auto body = [&] {
       solve_level(top, b_dev, x_dev, stream, prof);
       cudaMemsetAsync(nrm, 0, nb, stream);
-      DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
-                launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                                b_dev, R, nrm, stream));
+      residual(x_dev, b_dev, R);
     };
     int rc0 = (b_dev == top.F && x_dev == top.X) ? run(g_solve, body) : (body(), DM_OK);
     if (rc0) return rc0;
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));
+    if ((rc0 = check_residual_error())) return rc0;
     last_iters = 1;
     last_corr = 0.0;
     for (int s = 0; s < top.nsys; ++s) relres[s] = col_ratio(h_nrm, s, top.spec[s].r, 0, 1);
@@ -790,15 +876,14 @@ int Plan::solve_device(const double* b_dev, double* x_dev) {
       cudaMemsetAsync(nrm, 0, nb, stream);
       DM_LAUNCH(prof, stream, K_AXPY, top.c_axpy, top.nsys,
                 launch_axpy_norms(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, Dx, x_dev, nrm, stream));
-      DM_LAUNCH(prof, stream, K_RESIDUAL, top.c_resid, top.nsys,
-                launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                                b_dev, R, nrm, stream));
+      residual(x_dev, b_dev, R);
     };
     int rc0 = (b_dev == top.F && x_dev == top.X) ? run(it == 1 ? g_iter_first : g_iter_next, body) : (body(), DM_OK);
     if (rc0) return rc0;
     DM_CUDA(cudaGetLastError());
     DM_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, nb, cudaMemcpyDeviceToHost, st));
     DM_CUDA(cudaStreamSynchronize(st));
+    if ((rc0 = check_residual_error())) return rc0;
     rhs = R;
     corr = 0.0;
     bool bad = false;
@@ -1114,6 +1199,38 @@ int dm_plan_query(dm_plan_t plan, dm_plan_info* info) {
   info->last_correction = p.last_corr;
   info->factor_flops = p.factor_flops;
   info->solve_flops = p.solve_flops;
+  info->residual_mode = p.resid_mode;
+  info->residual_tc_systems = p.top.nres_tc;
+  return DM_OK;
+}
+
+int dm_set_residual(dm_plan_t plan, int mode) {
+  if (!plan) return set_error(DM_EINVAL, "NULL plan");
+  serve_drain(plan);
+  return plan->plan.set_residual_mode(mode);
+}
+
+int dm_residual(dm_plan_t plan, const double* x, const double* b, double* r, double* relres_out) {
+  if (!plan || !x || !b || !r) return set_error(DM_EINVAL, "NULL argument to dm_residual");
+  Plan& p = plan->plan;
+  if (!p.factored) return set_error(DM_ESTATE, "dm_residual before a successful dm_factor");
+  const size_t vb = p.top.nvec * sizeof(double);
+  const size_t nb = (size_t)std::max(1, p.top.nsys) * 4 * kMaxR * sizeof(double);
+  int rc;
+  if ((rc = copy_in(p.Dx, x, vb, p.stream))) return rc;
+  if ((rc = copy_in(p.top.F, b, vb, p.stream))) return rc;
+  DM_CUDA(cudaMemsetAsync(p.nrm, 0, nb, p.stream));
+  p.residual(p.Dx, p.top.F, p.R);
+  DM_CUDA(cudaGetLastError());
+  if ((rc = copy_out(r, p.R, vb, p.stream))) return rc;
+  DM_CUDA(cudaMemcpyAsync(p.h_nrm.data(), p.nrm, nb, cudaMemcpyDeviceToHost, p.stream));
+  DM_CUDA(cudaStreamSynchronize(p.stream));
+  if ((rc = p.check_residual_error())) return rc;
+  if (relres_out) {
+    double worst = 0.0;
+    for (int s = 0; s < p.top.nsys; ++s) worst = std::max(worst, col_ratio(p.h_nrm, s, p.top.spec[s].r, 0, 1));
+    *relres_out = worst;
+  }
   return DM_OK;
 }
 

@@ -41,6 +41,8 @@ struct SysDesc {
   long long blk, vec;  // offsets of row 0
   int N, m, r;
   int row0;            // first row of the system when the rows of all systems are numbered consecutively
+  int sliced;          // residual on the tensor cores (k_residual_sliced) instead of float64 CUDA cores
+  int eoff;            // offset of the system's rows in the per-row scale arrays (sum of N m before it)
 };
 
 // ---- launchers (dm_kernels.cu); T = double or float (factor storage type)
@@ -89,6 +91,19 @@ void launch_residual(const SysDesc* sys, int nsys, int nrows, int max_m, int max
                      const double* B, const double* C, const double* x, const double* b, double* r,
                      double* nrm, cudaStream_t st);
 // x += d, nrm[2] += ||d_c||^2, nrm[3] += ||x_c||^2 (after the update)
+// Residual b - T x of the systems with SysDesc::sliced set, float64-accurate
+// from exact bf16 slice products on the tensor cores (m <= 128, r <= 16).
+bool residual_sliced_fits(int m, int r);
+// Per point row of the sliced systems: the largest high word (sign cleared)
+// of the row of [A_i B_i C_i] -- computed once per factorisation.
+void launch_row_scales(const SysDesc* sys, int nsys, int nrows, const double* A, const double* B,
+                       const double* C, unsigned* rowhi, cudaStream_t st);
+// Per block row of the sliced systems: the largest high word of each column
+// of x_i ([global block row][16]), before each sliced residual.
+void launch_col_scales(const SysDesc* sys, int nsys, int nrows, const double* x, unsigned* colhi, cudaStream_t st);
+void launch_residual_sliced(const SysDesc* sys, int nsys, int nrows, const double* A, const double* B,
+                            const double* C, const double* x, const double* b, double* r, double* nrm,
+                            const unsigned* rowhi, const unsigned* colhi, int* errflag, cudaStream_t st);
 void launch_axpy_norms(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* d,
                        double* x, double* nrm, cudaStream_t st);
 

@@ -1522,6 +1522,7 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
   __shared__ double red[2 * kMaxR];
   const int si = find_sys(sys, nsys, blockIdx.x);
   const SysDesc sd = sys[si];
+  if (sd.sliced) return;  // residual on the tensor cores (k_residual_sliced)
   const int i = blockIdx.x - sd.row0;
   const int m = sd.m, r = sd.r;
   const long long mm = (long long)m * m, mr = (long long)m * r;

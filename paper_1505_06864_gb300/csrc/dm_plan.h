@@ -90,6 +90,8 @@ struct Level {
   std::vector<double> fwd_chain_frac;  // share of c_fwd[t] in the type-0 (chain) tiles
   std::vector<int> last_part;           // per system: index in parts of its last subsystem
   Cost c_asm_h, c_asm_f, c_backsub, c_resid, c_axpy, c_sepcopy;
+  Cost c_resid_tc;     // the part of c_resid computed by the tensor-core residual
+  int nres_tc = 0;     // systems whose residual runs on the tensor cores
   PartDesc* d_parts = nullptr;
   SepDesc* d_seps = nullptr;
   SysDesc* d_sys = nullptr;
@@ -144,7 +146,15 @@ struct Plan {
   bool borrow = false;  // use the caller's device A, B, C in place (no copy)
   bool overlap = false;  // left-spike tiles on the side stream
   const double *bA = nullptr, *bB = nullptr, *bC = nullptr;
+  int resid_mode = 0;  // DM_RESIDUAL_FP64 or DM_RESIDUAL_SLICED
+  unsigned* rowhi = nullptr;  // per point row of the top level: largest high word of [A_i B_i C_i]'s row
+  unsigned* colhi = nullptr;  // per block row x 16: largest high word of each column of x_i
+  void row_scales();          // rowhi from the resident blocks (after each factorisation)
   void reset_graphs();
+  int set_residual_mode(int mode);
+  // r = b - T x (float64-accurate) with the column norms into nrm; all device pointers
+  void residual(const double* x_dev, const double* b_dev, double* r_dev);
+  int check_residual_error();
   template <typename F>
   int run(GraphCache& g, F&& body);
 

@@ -667,6 +667,351 @@ __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __r
   tc_teardown(&st, ncols, errflag);
 }
 
+// ---------------------------------------------------------------- sliced residual
+// r = b - T x with float64 accuracy on the bf16 tensor cores (an exact
+// splitting in the manner of Ozaki's error-free matrix products).  Block
+// row i of a system is L = [A_i B_i C_i] (m x 3m) times X = [x_{i-1}; x_i;
+// x_{i+1}] (3m x r).  Every row of L is scaled by 2^-e (e: the exponent of
+// the row's largest magnitude) and every column of X by 2^-f, and each
+// scaled value y in (-1, 1) is cut into nine base-64 digits read straight
+// from its float64 bits: y = sign * sum_s d_s 2^(-6s) + (truncation below
+// 2^-54), d_s in [0, 63] -- integers, exact in bf16.  Then
+//   L X = 2^(e+f) sum_d 2^(-6d) acc_d,   acc_d = sum_{s+t=d} Lslice_s Xslice_t,
+// keeping the pairs with s + t <= 11.  Each acc_d sums at most 9 slice
+// products over K <= 384 terms of magnitude <= 63^2, so every partial sum is
+// an integer below 2^24 and the float32 accumulation in tensor memory is
+// exact; the ten acc_d are combined in float64.  The error per entry is
+// below K * 2^-50 * max|L_row| * max|X_col| (digit truncation and the
+// dropped pairs), within the float64 dot product's own bound.
+//
+// One CTA per block row (m <= 128, r <= 16), 256 threads.  K runs in chunks
+// of 64: the CTA slices the chunk of L (128 x 64, nine slices, K-major
+// 128-byte-swizzled bf16) and of X (16 x 64, nine slices + one zero slice,
+// stored consecutively so that slices t = 1..T form one N = 16 T operand),
+// then one thread issues per 16-wide K step nine MMAs: L slice s against X
+// slices 1..T_s (T_1 = 10 with the zero slice, which initialises all ten
+// accumulators; T_s = min(9, 11 - s) after), into the accumulators
+// d = s+1 .. s+T_s (TMEM columns (d - 2) * 16).
+constexpr int kRsThreads = 256;
+constexpr int kRsSlices = 9;
+constexpr int kRsNB = 16;                    // right-hand-side columns per tile
+constexpr int kRsAcc = 10;                   // accumulators d = 2 .. 11
+constexpr int kRsMaxM = 128;
+struct RsSmem {
+  static constexpr int a_slice = MT * 128;              // 128 rows x 64 bf16
+  static constexpr int b_slice = kRsNB * 128;           // 16 columns x 64 bf16
+  static constexpr int a_bytes = kRsSlices * a_slice;
+  static constexpr int b_bytes = (kRsSlices + 1) * b_slice;
+  static constexpr int total = 1024 + a_bytes + b_bytes;
+};
+
+__device__ __forceinline__ int rs_find_sys(const SysDesc* __restrict__ sys, int nsys, int row) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sys[mid].row0 <= row) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Nine signed base-64 digits of |v| * 2^(54 - e) (truncated), |v| < 2^e, from
+// the float64 bits of v (integer operations only: GB300's float64 pipe is
+// narrow); NaN digits for NaN or infinity.
+__device__ __forceinline__ void digits9(unsigned long long bits, int e, float (&q)[kRsSlices]) {
+  const bool neg = (bits >> 63) != 0;
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long mant = (bits & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+  const int sh = (ex ? ex : 1) - 1075 + 54 - e;  // <= 1 for |v| < 2^e
+  if (ex == 0x7ff || sh > 1) {
+#pragma unroll
+    for (int k = 0; k < kRsSlices; ++k) q[k] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const unsigned long long Y = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
+  const uint32_t hi = (uint32_t)(Y >> 32), lo = (uint32_t)Y;
+  // digit s occupies bits [48 - 6s, 54 - 6s) of Y
+  uint32_t d[kRsSlices];
+  d[0] = (hi >> 16) & 63;
+  d[1] = (hi >> 10) & 63;
+  d[2] = (hi >> 4) & 63;
+  d[3] = ((hi & 15) << 2) | (lo >> 30);
+  d[4] = (lo >> 24) & 63;
+  d[5] = (lo >> 18) & 63;
+  d[6] = (lo >> 12) & 63;
+  d[7] = (lo >> 6) & 63;
+  d[8] = lo & 63;
+#pragma unroll
+  for (int k = 0; k < kRsSlices; ++k) q[k] = neg ? -(float)d[k] : (float)d[k];
+}
+
+// Exponent e with |v| < 2^e for every v whose high word (sign cleared) is at
+// most hmax; subnormal or zero maxima share e = -1021.
+__device__ __forceinline__ int scale_exponent(uint32_t hmax) {
+  const int E = (int)(hmax >> 20);
+  return E == 0 ? -1021 : E - 1022;
+}
+
+__device__ __forceinline__ uint32_t abs_hi(unsigned long long bits) { return (uint32_t)(bits >> 32) & 0x7fffffffu; }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Largest high word (sign cleared) of every point row of [A_i B_i C_i] of the
+// sliced systems: a warp per point row, one CTA per block row.
+__global__ void __launch_bounds__(kRsThreads) k_row_scales(const SysDesc* __restrict__ sys, int nsys,
+                                                           const double* __restrict__ A,
+                                                           const double* __restrict__ B,
+                                                           const double* __restrict__ C, unsigned* __restrict__ rowhi) {
+  const int si = rs_find_sys(sys, nsys, blockIdx.x);
+  const SysDesc sd = sys[si];
+  if (!sd.sliced) return;
+  const int i = blockIdx.x - sd.row0, m = sd.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long o = sd.blk + (long long)i * m * m;
+  const bool hasA = i > 0, hasC = i < sd.N - 1;
+  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(A + o);
+  const unsigned long long* bb = reinterpret_cast<const unsigned long long*>(B + o);
+  const unsigned long long* c = reinterpret_cast<const unsigned long long*>(C + o);
+  for (int rr = warp; rr < m; rr += kRsThreads / 32) {
+    uint32_t mx = 0;
+    for (int k = lane; k < m; k += 32) {
+      const long long e = (long long)rr * m + k;
+      mx = max(mx, abs_hi(__ldg(bb + e)));
+      if (hasA) mx = max(mx, abs_hi(__ldg(a + e)));
+      if (hasC) mx = max(mx, abs_hi(__ldg(c + e)));
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) rowhi[sd.eoff + (long long)i * m + rr] = mx;
+  }
+}
+
+// Largest high word of every column of every block x_i of the sliced systems
+// ([global block row][16]): a warp per block row, lane = column + 16 * parity
+// of the point row.
+__global__ void __launch_bounds__(kRsThreads) k_col_scales(const SysDesc* __restrict__ sys, int nsys, int nrows,
+                                                           const double* __restrict__ x, unsigned* __restrict__ colhi) {
+  const int row = blockIdx.x * (kRsThreads / 32) + (threadIdx.x >> 5);
+  if (row >= nrows) return;
+  const int lane = threadIdx.x & 31;
+  const SysDesc sd = sys[rs_find_sys(sys, nsys, row)];
+  if (!sd.sliced) return;
+  const int i = row - sd.row0, m = sd.m, r = sd.r;
+  const int c = lane & 15, par = lane >> 4;
+  const unsigned long long* xi = reinterpret_cast<const unsigned long long*>(x + sd.vec + (long long)i * m * r);
+  uint32_t mx = 0;
+  if (c < r)
+    for (int k = par; k < m; k += 2) mx = max(mx, abs_hi(__ldg(xi + (long long)k * r + c)));
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+  if (lane < 16) colhi[(long long)row * kRsNB + c] = mx;
+}
+
+__global__ void __launch_bounds__(kRsThreads, 1) k_residual_sliced(const SysDesc* __restrict__ sys, int nsys,
+                                                                   const double* __restrict__ A,
+                                                                   const double* __restrict__ B,
+                                                                   const double* __restrict__ C,
+                                                                   const double* __restrict__ x,
+                                                                   const double* __restrict__ b,
+                                                                   double* __restrict__ rout,
+                                                                   double* __restrict__ nrm,
+                                                                   const unsigned* __restrict__ rowhi,
+                                                                   const unsigned* __restrict__ colhi,
+                                                                   int* __restrict__ errflag) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ TcState st;
+  __shared__ int s_erow[kRsMaxM];
+  __shared__ int s_fcol[kRsNB];
+  __shared__ double red[2 * kRsNB];
+  const int si = rs_find_sys(sys, nsys, blockIdx.x);
+  const SysDesc sd = sys[si];
+  if (!sd.sliced) return;  // the float64 kernel handles this system
+  const int i = blockIdx.x - sd.row0, m = sd.m, r = sd.r;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* As = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Bs = As + RsSmem::a_bytes;
+  const long long mm = (long long)m * m, mr = (long long)m * r;
+  const bool hasA = i > 0, hasC = i < sd.N - 1;
+  const unsigned long long* xbits = reinterpret_cast<const unsigned long long*>(x);
+  // the K chunks: (block j, first column k0) over the blocks present
+  const int nck = (m + 63) / 64;
+  const int j0 = hasA ? 0 : 1, j1 = hasC ? 3 : 2;
+  const int nchunks = (j1 - j0) * nck;
+  auto chunk_src = [&](int q, int* j, int* k0) {
+    *j = j0 + q / nck;
+    *k0 = (q % nck) * 64;
+  };
+  auto lrow = [&](int j) {
+    const double* base = j == 0 ? A : (j == 1 ? B : C);
+    return reinterpret_cast<const unsigned long long*>(base + sd.blk + i * mm);
+  };
+  constexpr int IT = MT * 8 / kRsThreads;  // 8-wide groups of L per thread per chunk
+  unsigned long long raw[IT][8];
+  auto load_chunk = [&](int q) {
+    int j, k0;
+    chunk_src(q, &j, &k0);
+    const unsigned long long* L = lrow(j);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int e = tid + it * kRsThreads;
+      const int rr = e >> 3, k = k0 + 8 * (e & 7);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) raw[it][u] = (rr < m && k + u < m) ? __ldg(L + (long long)rr * m + k + u) : 0ull;
+    }
+  };
+  load_chunk(0);  // in flight during the set-up below
+  tc_setup(&st, 256);
+  for (int rr = tid; rr < m; rr += kRsThreads) s_erow[rr] = scale_exponent(rowhi[sd.eoff + (long long)i * m + rr]);
+  if (tid < kRsNB) {
+    const long long g = (long long)blockIdx.x * kRsNB + tid;
+    uint32_t h = colhi[g];
+    if (hasA) h = max(h, colhi[g - kRsNB]);
+    if (hasC) h = max(h, colhi[g + kRsNB]);
+    s_fcol[tid] = scale_exponent(h);
+  }
+  if (tid < 2 * kRsNB) red[tid] = 0.0;
+  for (int e = tid; e < RsSmem::b_slice / 16; e += kRsThreads)  // the zero slice after the nine X slices
+    *reinterpret_cast<uint4*>(Bs + kRsSlices * RsSmem::b_slice + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
+  // rows m .. 127 of the L slices: zero for every chunk
+  for (int e = tid; e < (MT - m) * 8 * kRsSlices; e += kRsThreads) {
+    const int sl = e / ((MT - m) * 8), rem = e - sl * (MT - m) * 8;
+    *reinterpret_cast<uint4*>(As + sl * RsSmem::a_slice + sw128_off(m + (rem >> 3), 16 * (rem & 7))) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncthreads();
+
+  uint32_t ph = 0;
+  bool ok = true;
+  for (int q = 0; q < nchunks; ++q) {
+    int j, k0;
+    chunk_src(q, &j, &k0);
+    if (q > 0) {  // the previous chunk's MMAs have read shared memory
+      if (!mbar_wait(&st.bars[0], ph)) ok = false;
+      ph ^= 1u;
+    }
+    // L chunk (already in registers): nine digit slices; rows past m stay
+    // as zeroed on entry, groups wholly past m are stored as zeros
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int e = tid + it * kRsThreads;
+      const int rr = e >> 3, g8 = e & 7;
+      if (rr >= m) continue;
+      if (k0 + 8 * g8 >= m) {
+#pragma unroll
+        for (int sl = 0; sl < kRsSlices; ++sl)
+          *reinterpret_cast<uint4*>(As + sl * RsSmem::a_slice + sw128_off(rr, 16 * g8)) = make_uint4(0u, 0u, 0u, 0u);
+        continue;
+      }
+      const int er = s_erow[rr];
+      float qv[8][kRsSlices];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) digits9(raw[it][u], er, qv[u]);
+#pragma unroll
+      for (int sl = 0; sl < kRsSlices; ++sl)
+        *reinterpret_cast<uint4*>(As + sl * RsSmem::a_slice + sw128_off(rr, 16 * g8)) =
+            make_uint4(pack_bf16x2(qv[0][sl], qv[1][sl]), pack_bf16x2(qv[2][sl], qv[3][sl]),
+                       pack_bf16x2(qv[4][sl], qv[5][sl]), pack_bf16x2(qv[6][sl], qv[7][sl]));
+    }
+    // X chunk: 16 columns x 8 groups of 8 consecutive K
+    if (tid < kRsNB * 8) {
+      const int c = tid >> 3, g8 = tid & 7, k = k0 + 8 * g8;
+      const int fc = s_fcol[c];
+      const long long xo = sd.vec + (long long)(i - 1 + j) * mr;
+      float qv[8][kRsSlices];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        digits9((c < r && k + u < m) ? __ldg(xbits + xo + (long long)(k + u) * r + c) : 0ull, fc, qv[u]);
+#pragma unroll
+      for (int sl = 0; sl < kRsSlices; ++sl)
+        *reinterpret_cast<uint4*>(Bs + sl * RsSmem::b_slice + sw128_off(c, 16 * g8)) =
+            make_uint4(pack_bf16x2(qv[0][sl], qv[1][sl]), pack_bf16x2(qv[2][sl], qv[3][sl]),
+                       pack_bf16x2(qv[4][sl], qv[5][sl]), pack_bf16x2(qv[6][sl], qv[7][sl]));
+    }
+    fence_async_shared();
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t kb = (uint32_t)(ks * 32);
+        const uint64_t bd = sw128_desc(smem_u32(Bs) + kb);
+#pragma unroll
+        for (int sl = 0; sl < kRsSlices; ++sl) {
+          const int T = sl == 0 ? kRsSlices + 1 : min(kRsSlices, 10 - sl);
+          const uint64_t ad = sw128_desc(smem_u32(As + sl * RsSmem::a_slice) + kb);
+          const uint32_t acc = (q == 0 && ks == 0 && sl == 0) ? 0u : 1u;
+          const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((16 * T) >> 3) << 17) |
+                                 ((uint32_t)(MT >> 4) << 24);
+          mma<1>(st.tmem + (uint32_t)(sl * kRsNB), ad, bd, idesc, acc);
+        }
+      }
+      mma_commit(&st.bars[0]);
+    }
+    if (q + 1 < nchunks) load_chunk(q + 1);  // next chunk's loads overlap these MMAs
+  }
+  if (nchunks > 0 && ok) {
+    if (!mbar_wait(&st.bars[0], ph)) ok = false;
+    ph ^= 1u;
+  }
+  tc_fence_after();
+  ok = __syncthreads_and(ok);
+  // epilogue: warps 0-3 own TMEM lanes 0-127 = rows
+  const double* bi = b + sd.vec + i * mr;
+  double* ri = rout + sd.vec + i * mr;
+  if (warp < 4 && ok) {
+    const int row = warp * 32 + lane;
+    // sum_d acc_d 2^(-6d) from the exact integer accumulators: d = 2..6 and
+    // d = 7..11 combined in two 64-bit integers (each below 2^49), then one
+    // float64 fused multiply-add
+    long long ih[kRsNB], il[kRsNB];
+    uint32_t nan_cols = 0;  // a NaN digit (NaN or infinite input) reached the column
+#pragma unroll
+    for (int c = 0; c < kRsNB; ++c) ih[c] = il[c] = 0;
+#pragma unroll
+    for (int dd = 0; dd < kRsAcc; ++dd) {
+      float v[16];
+      tmem_ld16(st.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dd * kRsNB), v);
+#pragma unroll
+      for (int c = 0; c < kRsNB; ++c) {
+        if (v[c] != v[c]) nan_cols |= 1u << c;
+        const long long a = (long long)__float2int_rn(v[c]);
+        if (dd < 5)
+          ih[c] += a * (1ll << (6 * (4 - dd)));
+        else
+          il[c] += a * (1ll << (6 * (9 - dd)));
+      }
+    }
+    double sum[kRsNB];
+#pragma unroll
+    for (int c = 0; c < kRsNB; ++c)
+      sum[c] = ((nan_cols >> c) & 1u) ? __longlong_as_double(0x7ff8000000000000ll)
+                                      : fma((double)il[c], 0x1p-66, (double)ih[c] * 0x1p-36);
+    if (row < m) {
+      const int er = s_erow[row];
+#pragma unroll
+      for (int c = 0; c < kRsNB; ++c)
+        if (c < r) {
+          const long long e = (long long)row * r + c;
+          const double bb = bi[e];
+          const double rv = bb - ldexp(sum[c], er + s_fcol[c]);
+          ri[e] = rv;
+          atomicAdd(&red[c], rv * rv);
+          atomicAdd(&red[kRsNB + c], bb * bb);
+        }
+    }
+  }
+  __syncthreads();
+  if (tid < r && ok) {
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + tid], red[tid]);
+    atomicAdd(&nrm[(long long)si * 4 * kMaxR + kMaxR + tid], red[kRsNB + tid]);
+  }
+  if (!ok && tid == 0) st.err = 1;
+  tc_teardown(&st, 256, errflag);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- launchers
@@ -780,6 +1125,30 @@ bool make_tma_maps(const float* G, const float* A32, const float* Acal, long lon
 }
 
 int tma_maps_bytes() { return (int)sizeof(tc::TmaMaps); }
+
+bool residual_sliced_fits(int m, int r) { return m >= 1 && m <= tc::kRsMaxM && r >= 1 && r <= tc::kRsNB; }
+
+void launch_row_scales(const SysDesc* sys, int nsys, int nrows, const double* A, const double* B,
+                       const double* C, unsigned* rowhi, cudaStream_t st) {
+  if (nsys <= 0 || nrows <= 0) return;
+  tc::k_row_scales<<<nrows, tc::kRsThreads, 0, st>>>(sys, nsys, A, B, C, rowhi);
+}
+
+void launch_col_scales(const SysDesc* sys, int nsys, int nrows, const double* x, unsigned* colhi, cudaStream_t st) {
+  if (nsys <= 0 || nrows <= 0) return;
+  const int per = tc::kRsThreads / 32;
+  tc::k_col_scales<<<(nrows + per - 1) / per, tc::kRsThreads, 0, st>>>(sys, nsys, nrows, x, colhi);
+}
+
+void launch_residual_sliced(const SysDesc* sys, int nsys, int nrows, const double* A, const double* B,
+                            const double* C, const double* x, const double* b, double* r, double* nrm,
+                            const unsigned* rowhi, const unsigned* colhi, int* errflag, cudaStream_t st) {
+  if (nsys <= 0 || nrows <= 0) return;
+  static bool set = false;
+  raise_smem_once(tc::k_residual_sliced, tc::RsSmem::total, &set);
+  tc::k_residual_sliced<<<nrows, tc::kRsThreads, tc::RsSmem::total, st>>>(sys, nsys, A, B, C, x, b, r, nrm, rowhi,
+                                                                          colhi, errflag);
+}
 
 int tc_smem_bytes(int mode) { return mode == 0 ? tc::Smem<0>::total : tc::Smem<1>::total; }
 

@@ -40,7 +40,8 @@ class dm_plan_info(ctypes.Structure):
                 ("count", ctypes.c_int), ("last_iters", ctypes.c_int), ("max_rows", ctypes.c_int),
                 ("device_bytes", ctypes.c_size_t), ("last_relres", ctypes.c_double),
                 ("last_correction", ctypes.c_double), ("factor_flops", ctypes.c_double),
-                ("solve_flops", ctypes.c_double)]
+                ("solve_flops", ctypes.c_double), ("residual_mode", ctypes.c_int),
+                ("residual_tc_systems", ctypes.c_int)]
 
 
 class dm_profile_entry(ctypes.Structure):
@@ -72,6 +73,8 @@ def lib():
             "dm_solve_last": (I, [P, P, P]),
             "dm_set_stream": (I, [P, P]),
             "dm_set_refinement": (I, [P, D, I]),
+            "dm_set_residual": (I, [P, I]),
+            "dm_residual": (I, [P, P, P, P, ctypes.POINTER(D)]),
             "dm_set_borrow_inputs": (I, [P, I]),
             "dm_set_side_stream": (I, [P, I]),
             "dm_plan_query": (I, [P, ctypes.POINTER(dm_plan_info)]),
@@ -187,6 +190,29 @@ def dm_solve(plan, b, x, count=1, allow_notconv=False):
     rc = lib().dm_solve(plan, _ptr(b), _ptr(x, True), rel)
     _check(rc, (DM_OK, DM_ENOTCONV) if allow_notconv else (DM_OK,))
     return rel[0] if count == 1 else list(rel)
+
+
+DM_RESIDUAL_FP64 = 0
+DM_RESIDUAL_SLICED = 1
+DM_RESIDUAL_AUTO = 2
+RESIDUAL_MODES = {"fp64": DM_RESIDUAL_FP64, "sliced": DM_RESIDUAL_SLICED, "auto": DM_RESIDUAL_AUTO}
+
+
+def dm_set_residual(plan, mode):
+    """Residual method: "fp64" (CUDA-core float64), "sliced" (exact digit
+    products on the tensor cores, float64-accurate) or "auto" (sliced where
+    faster)."""
+    if isinstance(mode, str):
+        mode = RESIDUAL_MODES[mode]
+    return _check(lib().dm_set_residual(plan, int(mode)))
+
+
+def dm_residual(plan, x, b, r):
+    """r = b - T x with the plan's blocks (after dm_factor); returns max over
+    columns of ||r|| / ||b||."""
+    rel = ctypes.c_double(0.0)
+    _check(lib().dm_residual(plan, _ptr(x), _ptr(b), _ptr(r, True), ctypes.byref(rel)))
+    return rel.value
 
 
 def dm_solve_last(plan, b_last, x_last):
