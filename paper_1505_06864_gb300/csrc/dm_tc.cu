@@ -715,16 +715,20 @@ __device__ __forceinline__ int rs_find_sys(const SysDesc* __restrict__ sys, int 
 }
 
 // Nine signed base-64 digits of |v| * 2^(54 - e) (truncated), |v| < 2^e, from
-// the float64 bits of v (integer operations only: GB300's float64 pipe is
-// narrow); NaN digits for NaN or infinity.
-__device__ __forceinline__ void digits9(unsigned long long bits, int e, float (&q)[kRsSlices]) {
-  const bool neg = (bits >> 63) != 0;
+// the float64 bits of v, as bf16 bit patterns (the high half of each word;
+// the low half is ignored).  Integer and float32 operations only: GB300's
+// float64 pipe, which also carries the integer-float conversions, is narrow.
+// A digit d < 2^23 becomes the float d exactly as (2^23 + d) - 2^23, and a
+// float with at most 8 significant bits is its own bf16 truncation.  NaN
+// digits for NaN or infinity.
+__device__ __forceinline__ void digits9(unsigned long long bits, int e, uint32_t (&q)[kRsSlices]) {
+  const uint32_t sign = (uint32_t)(bits >> 63) << 31;
   const int ex = (int)((bits >> 52) & 0x7ff);
   const unsigned long long mant = (bits & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
   const int sh = (ex ? ex : 1) - 1075 + 54 - e;  // <= 1 for |v| < 2^e
   if (ex == 0x7ff || sh > 1) {
 #pragma unroll
-    for (int k = 0; k < kRsSlices; ++k) q[k] = __int_as_float(0x7fc00000);
+    for (int k = 0; k < kRsSlices; ++k) q[k] = 0x7fc00000u;
     return;
   }
   const unsigned long long Y = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
@@ -741,7 +745,8 @@ __device__ __forceinline__ void digits9(unsigned long long bits, int e, float (&
   d[7] = (lo >> 6) & 63;
   d[8] = lo & 63;
 #pragma unroll
-  for (int k = 0; k < kRsSlices; ++k) q[k] = neg ? -(float)d[k] : (float)d[k];
+  for (int k = 0; k < kRsSlices; ++k)
+    q[k] = __float_as_uint(__uint_as_float(0x4b000000u | d[k]) - 8388608.0f) | sign;
 }
 
 // Exponent e with |v| < 2^e for every v whose high word (sign cleared) is at
@@ -753,10 +758,8 @@ __device__ __forceinline__ int scale_exponent(uint32_t hmax) {
 
 __device__ __forceinline__ uint32_t abs_hi(unsigned long long bits) { return (uint32_t)(bits >> 32) & 0x7fffffffu; }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
+// two bf16 patterns (high halves of a, b) in one word: a low, b high
+__device__ __forceinline__ uint32_t pack_bf16x2(uint32_t a, uint32_t b) { return (a >> 16) | (b & 0xffff0000u); }
 
 // Largest high word (sign cleared) of every point row of [A_i B_i C_i] of the
 // sliced systems: a warp per point row, one CTA per block row.
@@ -903,7 +906,7 @@ __global__ void __launch_bounds__(kRsThreads, 1) k_residual_sliced(const SysDesc
         continue;
       }
       const int er = s_erow[rr];
-      float qv[8][kRsSlices];
+      uint32_t qv[8][kRsSlices];
 #pragma unroll
       for (int u = 0; u < 8; ++u) digits9(raw[it][u], er, qv[u]);
 #pragma unroll
@@ -917,7 +920,7 @@ __global__ void __launch_bounds__(kRsThreads, 1) k_residual_sliced(const SysDesc
       const int c = tid >> 3, g8 = tid & 7, k = k0 + 8 * g8;
       const int fc = s_fcol[c];
       const long long xo = sd.vec + (long long)(i - 1 + j) * mr;
-      float qv[8][kRsSlices];
+      uint32_t qv[8][kRsSlices];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         digits9((c < r && k + u < m) ? __ldg(xbits + xo + (long long)(k + u) * r + c) : 0ull, fc, qv[u]);
