@@ -4,8 +4,9 @@
 Workload (default): the PDE-shaped block-tridiagonal system -- second-order
 finite differences over N = 2048 grid points times cubic-spline collocation
 with m = 256 (banded blocks, half-bandwidth 3, stored dense), one right-hand
-side, float64 DM with P = 64 subsystems and DM on the supplementary system
-(levels = 2).  A step is one factor + solve of the whole system (every stage
+side, float64 DM with P = 64 subsystems, DM on the supplementary system and
+on its supplementary system (levels = 3: the fastest of P in {4, 16, 64} x
+levels {1, 2, 3} on GB300).  A step is one factor + solve of the whole system (every stage
 of the method: subsystem sweeps, supplementary assembly and solve,
 back-substitution, float64 residual), inputs resident in device memory.
 
@@ -36,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-N_, M_, R_, P_, LEV_ = 2048, 256, 1, 64, 2
+N_, M_, R_, P_, LEV_ = 2048, 256, 1, 64, 3
 SEED = 2
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal float64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
 
@@ -264,7 +265,7 @@ def main():
             t, xo = cpu_oracle_solve(s)
             line["cpu_baseline"] = {"value": 1.0 / t, "unit": "systems/s", "cores": blas_threads(),
                                     "kind": "oracle",
-                                    "sample": "the full workload: one numpy float64 DM solve (P=64, levels=2)"}
+                                    "sample": f"the full workload: one numpy float64 DM solve (P={P_}, levels={LEV_})"}
             line["rel_err_vs_oracle"] = rel_err(xh, xo)
     elif rank == 0:
         line["e2e"] = None
@@ -350,12 +351,12 @@ def timed(fn, reps=1):
 
 
 def sweep_leg(dm, A, B, C, b, stream):
-    """P in {4, 16, 64} x recursion depth {1, 2}: one warm-up and one timed step each."""
+    """P in {4, 16, 64} x recursion depth {1, 2, 3}: one warm-up and one timed step each."""
     import torch
     out = []
     x = torch.empty_like(b)
     for P in (4, 16, 64):
-        for lv in (1, 2):
+        for lv in (1, 2, 3):
             plan = dm.dm_plan(N_, M_, R_, P, lv, dm.DM_FP64)
             dm.dm_set_stream(plan, stream)
             q = dm.dm_plan_query(plan)

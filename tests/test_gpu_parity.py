@@ -161,7 +161,7 @@ def test_solve_before_factor(dm):
         dm.dm_destroy(plan)
 
 
-@pytest.mark.parametrize("P,levels", [(64, 1), (64, 2), (16, 2), (4, 1)])
+@pytest.mark.parametrize("P,levels", [(64, 1), (64, 2), (64, 3), (16, 2), (4, 1)])
 def test_config2_full_size(dm, P, levels):
     """N=2048 grid points x m=256 spline block, banded blocks, 1 right-hand side,
     float64 (the benchmarked workload), compared in full with the oracle."""
