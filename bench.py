@@ -406,11 +406,13 @@ def _timed_steps(dm, plan, A, B, C, b, x, steps, warmup, stream, mixed):
 
 
 def _profile_pass(dm, plan, A, B, C, b, x, mixed):
-    """One extra factor + solve with per-launch CUDA events (not timed above)."""
+    """One extra factor + solve with per-launch CUDA events (not timed above):
+    per kernel class, summed ms and algorithmic TFLOP/s."""
     dm.dm_profile(plan, True)
     dm.dm_factor(plan, A, B, C)
     dm.dm_solve(plan, b, x, allow_notconv=mixed, count=dm.dm_plan_query(plan)["count"])
-    return {k: round(v["ms"], 2) for k, v in dm.dm_profile(plan, False).items()}
+    return {k: {"ms": round(v["ms"], 2), "tflops": round(v["flops"] / (v["ms"] * 1e9), 3) if v["ms"] > 0 else 0.0}
+            for k, v in dm.dm_profile(plan, False).items()}
 
 
 def run_precision(args):

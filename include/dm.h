@@ -92,7 +92,9 @@ typedef struct dm_plan_info {
  * Section 4.2.1, its subsystem count from Eq. (SuppMatrM)).  P = 0 and
  * levels = 0 take the measured choice of dm_autotune for this shape and
  * precision if there is one, else (and for P = 0 or levels = 0 alone) the
- * paper's optimum: Eq. (MAXSpeedP) for P, depth 2 when P >= 21.  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
+ * paper's optimum: Eq. (MAXSpeedP) for P, depth 2 when P >= 21 (depth 3 when
+ * the supplementary system then has >= 8 subsystems: on the GPU each level's
+ * last block Thomas chain is latency-bound).  Limits: 1 <= m <= 512, 1 <= nrhs <= 64.  Allocates the
  * device workspace (factors, sweep vectors, supplementary systems) after an
  * admission check against the free device memory; returns DM_EINVAL or
  * DM_ENOMEM on failure.  The plan's copy of A, B, C (3 N m^2 doubles) is
@@ -191,7 +193,7 @@ int dm_solve_last(dm_plan_t plan, const double* b_last, double* x_last);
 
 /* The decomposition dm_plan would choose for P = 0 / levels = 0 (the tuner's
  * seed: P from Eq. (MAXSpeedP), recursion from the P >= 21 condition after
- * Eq. (SuppMatrM), P2 from Eq. (SuppMatrM)).  Host only: allocates nothing and
+ * Eq. (SuppMatrM) -- one level more when P2 >= 8 --, P2 from Eq. (SuppMatrM)).  Host only: allocates nothing and
  * needs no GPU.  Inputs P, levels as for dm_plan (0 = choose); outputs the
  * effective P, levels and P2.  DM_EINVAL for invalid sizes. */
 int dm_plan_tune(int N, int m, int nrhs, int* P, int* levels, int* P2);

@@ -1039,7 +1039,14 @@ int make_spec(int N, int m, int r, int P, int levels, SysSpec* out) {
   if (P == 0) P = tuner_seed_p(N, m, r);
   if (P > 1 && 2 * P - 1 > N)
     return set_error(DM_EINVAL, "P = %d too large for N = %d: every subsystem needs >= 1 row (P <= (N+1)/2)", P, N);
-  if (levels == 0) levels = (P >= 21) ? 2 : 1;   // Section 5.2.1: DM on the supplementary system pays from P >= 21
+  if (levels == 0) {
+    // Section 5.2.1: DM on the supplementary system pays from P >= 21.  On the
+    // GPU a level's block Thomas chain is latency-bound (one block at a time),
+    // so a third level pays as soon as the second has P2 >= 8 subsystems
+    // (measured: 2-10 % per step on the PDE-shaped and conditioned workloads).
+    levels = (P >= 21) ? 2 : 1;
+    if (levels == 2 && supp_partitions(P - 1, P, r, m) >= 8) levels = 3;
+  }
   SysSpec s;
   s.N = N;
   s.m = m;

@@ -57,9 +57,11 @@ def test_tuner_seed_is_paper_optimum(dm):
         P, levels, P2 = dm.dm_plan_tune(N, m, r)
         ref = min(max(1, round(o.p_opt_mp(N, m, r))), (N + 1) // 2)
         assert P == ref
-        assert levels == (2 if P >= 21 else 1)
-        if levels == 2:
+        if P >= 21:
             assert P2 == o.supp_partitions(P - 1, P, r, m)
+            assert levels == (3 if P2 >= 8 else 2)
+        else:
+            assert levels == 1
     # explicit choices pass through; P2 follows Eq. (SuppMatrM) or its boundary P/3
     assert dm.dm_plan_tune(2048, 256, 1, P=64, levels=2) == (64, 2, o_supp(64, 1, 256))
     assert dm.dm_plan_tune(2048, 256, 1, P=16, levels=2)[2] == round(16 / 3)
