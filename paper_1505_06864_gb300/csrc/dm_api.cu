@@ -815,9 +815,10 @@ void Plan::residual(const double* x_dev, const double* b_dev, double* r_dev) {
   Cost c64 = top.c_resid;
   c64.flops -= top.c_resid_tc.flops;
   c64.bytes -= top.c_resid_tc.bytes;
-  DM_LAUNCH(prof, stream, K_RESIDUAL, c64, top.nsys - top.nres_tc,
-            launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                            b_dev, r_dev, nrm, stream));
+  if (top.nsys > top.nres_tc)
+    DM_LAUNCH(prof, stream, K_RESIDUAL, c64, top.nsys - top.nres_tc,
+              launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
+                              b_dev, r_dev, nrm, stream));
   if (top.nres_tc > 0) {
     DM_LAUNCH(prof, stream, K_RESIDUAL, Cost(), top.nres_tc,
               launch_col_scales(top.d_sys, top.nsys, top.nrows, x_dev, colhi, stream));
