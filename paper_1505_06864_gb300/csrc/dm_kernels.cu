@@ -1026,33 +1026,35 @@ __global__ void __launch_bounds__(kThreads) k_assemble_h(const SepDesc* __restri
   if (c0 >= m) return;
   if (type == 1 && !(sp.flags & HAS_HA)) return;
   if (type == 2 && !(sp.flags & HAS_HC)) return;
-  double* R1 = reinterpret_cast<double*>(smem_raw);
-  double* R2 = R1 + m * W;
-  double* Lc = R2 + m * W;
+  // the level's arithmetic: float32 products (and sums) on float32 levels,
+  // whose spikes carry float32 accuracy anyway; H itself is float64
+  T* R1 = reinterpret_cast<T*>(smem_raw);
+  T* R2 = R1 + m * W;
+  T* Lc = R2 + m * W;
   const double* Aq = A + sp.blk_q;
   const double* Cq = C + sp.blk_q;
   if (type == 0) {
-    load_panel<double, T, W>(R1, ZR + sp.blk_prev, m, m, c0, m, 1.0);
-    load_panel<double, T, W>(R2, ZL + sp.blk_next, m, m, c0, m, 1.0);
+    load_panel<T, T, W>(R1, ZR + sp.blk_prev, m, m, c0, m, (T)1);
+    load_panel<T, T, W>(R2, ZL + sp.blk_next, m, m, c0, m, (T)1);
     __syncthreads();
     const double* Bq = B + sp.blk_q;
     double* dst = HB + sp.hblk;
-    panel_mm<double, double, double, W>(m, Aq, R1, Cq, R2, Lc, [&](int row, int col, double v) {
+    panel_mm<T, double, double, W>(m, Aq, R1, Cq, R2, Lc, [&](int row, int col, T v) {
       if (c0 + col < m) {
         const long long e = (long long)row * m + c0 + col;
-        dst[e] = Bq[e] - v;
+        dst[e] = Bq[e] - (double)v;
       }
     });
   } else {
     const T* Z = (type == 1) ? ZL + sp.blk_prev : ZR + sp.blk_next;
     const double* Lop = (type == 1) ? Aq : Cq;
     double* dst = ((type == 1) ? HA : HC) + sp.hblk;
-    load_panel<double, T, W>(R1, Z, m, m, c0, m, 1.0);
+    load_panel<T, T, W>(R1, Z, m, m, c0, m, (T)1);
     __syncthreads();
-    panel_mm<double, double, double, W>(m, Lop, R1, (const double*)nullptr, (const double*)nullptr, Lc,
-                                        [&](int row, int col, double v) {
-                                          if (c0 + col < m) dst[(long long)row * m + c0 + col] = -v;
-                                        });
+    panel_mm<T, double, double, W>(m, Lop, R1, (const double*)nullptr, (const T*)nullptr, Lc,
+                                   [&](int row, int col, T v) {
+                                     if (c0 + col < m) dst[(long long)row * m + c0 + col] = -(double)v;
+                                   });
   }
 }
 
@@ -1992,13 +1994,13 @@ void launch_assemble_h(const SepDesc* seps, int nseps, int max_m, const double* 
   if (max_m <= 256) {
     constexpr int W = 32;
     const int tiles = ntiles<W>(max_m);
-    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
     allow_smem(k_assemble_h<T, W>, bytes);
     k_assemble_h<T, W><<<dim3(3 * tiles, nseps), kThreads, bytes, st>>>(seps, tiles, A, B, C, ZL, ZR, HA, HB, HC);
   } else {
     constexpr int W = 16;
     const int tiles = ntiles<W>(max_m);
-    const size_t bytes = panel_smem<double>(max_m, W, 2);
+    const size_t bytes = panel_smem<T>(max_m, W, 2);
     allow_smem(k_assemble_h<T, W>, bytes);
     k_assemble_h<T, W><<<dim3(3 * tiles, nseps), kThreads, bytes, st>>>(seps, tiles, A, B, C, ZL, ZR, HA, HB, HC);
   }
