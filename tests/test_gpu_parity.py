@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances (spec targets): plain float64 GPU DM within 1e-12 relative
+Tolerances (the accuracy targets of this solver): plain float64 GPU DM within 1e-12 relative
 of the float64 oracle; mixed precision with float64 iterative refinement
 within 1e-10.  Every comparison is element by element (|x - x_ref| <= tol *
 max|x_ref| per right-hand-side column) and normwise (max over columns of
