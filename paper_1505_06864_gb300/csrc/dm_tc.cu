@@ -376,7 +376,7 @@ struct Smem {
 template <int MODE>
 __device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* lbuf0, uint8_t* right,
                         uint64_t* bars, uint32_t (&ph)[2], uint32_t tmem, bool elect, const CUtensorMap* tm,
-                        long long row0, uint64_t* lbars, uint32_t (&lph)[2]) {
+                        long long row0, uint64_t* lbars, uint32_t (&lph)[2], int lbuf_bytes) {
   using S = Smem<MODE>;
   constexpr int KA = Fmt<MODE>::katom;
   constexpr int KS = Fmt<MODE>::kstep;
@@ -388,7 +388,7 @@ __device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* 
   // next block row past m only feed output rows that are never stored;
   // columns past m are zero-filled) or cp.async / register copies
   auto stage = [&](int slab, int buf) {
-    uint8_t* dstb = lbuf0 + buf * S::lbuf_bytes;
+    uint8_t* dstb = lbuf0 + buf * lbuf_bytes;
     if (tma) {
       if (elect) {
         mbar_expect_tx(&lbars[buf], (uint32_t)(tiles * MT * 128));
@@ -402,7 +402,7 @@ __device__ bool product(const float* __restrict__ L, int m, int tiles, uint8_t* 
   stage(0, 0);
   for (int s = 0; s < nslab; ++s) {
     const int b = s & 1;
-    uint8_t* lb = lbuf0 + b * S::lbuf_bytes;
+    uint8_t* lb = lbuf0 + b * lbuf_bytes;
     if (tma) {
       if (!mbar_wait(&lbars[b], lph[b])) ok = false;
       lph[b] ^= 1u;
@@ -481,12 +481,11 @@ struct __align__(64) TmaMaps {
   CUtensorMap G, A, Acal;
 };
 
-template <int MODE>
-__device__ __forceinline__ uint8_t* carve(uint8_t* raw, uint8_t** lbuf, uint8_t** right) {
-  using S = Smem<MODE>;
+// Two left buffers of `lbuf_bytes` (the launch's M-tiles), then the right panel.
+__device__ __forceinline__ uint8_t* carve(uint8_t* raw, uint8_t** lbuf, uint8_t** right, int lbuf_bytes) {
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   *lbuf = base;
-  *right = base + 2 * S::lbuf_bytes;
+  *right = base + 2 * lbuf_bytes;
   return base;
 }
 
@@ -530,7 +529,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
                                                             const float* __restrict__ C, float* __restrict__ G,
                                                             float* __restrict__ Acal, float* __restrict__ ZL,
                                                             float* __restrict__ ZR, int* __restrict__ errflag,
-                                                            const __grid_constant__ TmaMaps tmaps, int use_tma) {
+                                                            const __grid_constant__ TmaMaps tmaps, int use_tma,
+                                                            int cap_tiles) {
   using S = Smem<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ TcState st;
@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
   if (type == 0 && last && !(p.flags & HAS_RIGHT)) return;
   if (type == 1 && !(p.flags & HAS_LEFT)) return;
   uint8_t *lbuf, *right;
-  carve<MODE>(smem_raw, &lbuf, &right);
+  const int lbuf_bytes = cap_tiles * S::tile_bytes;
+  carve(smem_raw, &lbuf, &right, lbuf_bytes);
   const int tiles = (m + MT - 1) / MT;
   const int ncols = tmem_cols(tiles);
   tc_setup(&st, ncols);
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
     stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, C + o, m, m, c0, m, 1.f);
     fence_async_shared();
     __syncthreads();
-    ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph);
+    ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph, lbuf_bytes);
     if (ok) {
       float* dst = last ? ZR + o : Acal + o;
       // result to global, and (not last) transposed into `right` for the next product
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
         __syncthreads();
         tc_fence_after();
         ok = product<MODE>(A + o + mm, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tA, (o + mm) / m,
-                           st.lbars, lph);
+                           st.lbars, lph, lbuf_bytes);
         if (ok) {
           const float* Bn = B + o + mm;
           float* Dn = G + o + mm;
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
       stage_right<MODE, float>(right, S::rslab_bytes, S::right_lo, ZL + o - mm, m, m, c0, m, 1.f);
       fence_async_shared();
       __syncthreads();
-      ok = product<MODE>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tA, o / m, st.lbars, lph);
+      ok = product<MODE>(A + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tA, o / m, st.lbars, lph, lbuf_bytes);
       if (ok) {
         tc_fence_before();
         __syncthreads();
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_factor_tc(const PartDesc* __re
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (ok) ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph);
+    if (ok) ok = product<MODE>(G + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, elect, tG, o / m, st.lbars, lph, lbuf_bytes);
     if (ok) {
       float* dst = ZL + o;
       drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -628,7 +629,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __restrict__ parts, int s, int tiles_n,
                                                              const float* __restrict__ Acal, float* __restrict__ ZL,
                                                              float* __restrict__ ZR, int* __restrict__ errflag,
-                                                             const __grid_constant__ TmaMaps tmaps, int use_tma) {
+                                                             const __grid_constant__ TmaMaps tmaps, int use_tma,
+                                                             int cap_tiles) {
   using S = Smem<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ TcState st;
@@ -641,7 +643,8 @@ __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __r
   if (type == 0 && !(p.flags & HAS_LEFT)) return;
   if (type == 1 && !(p.flags & HAS_RIGHT)) return;
   uint8_t *lbuf, *right;
-  carve<MODE>(smem_raw, &lbuf, &right);
+  const int lbuf_bytes = cap_tiles * S::tile_bytes;
+  carve(smem_raw, &lbuf, &right, lbuf_bytes);
   const int tiles = (m + MT - 1) / MT;
   const int ncols = tmem_cols(tiles);
   tc_setup(&st, ncols);
@@ -653,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_back_factor_tc(const PartDesc* __r
   fence_async_shared();
   __syncthreads();
   bool ok = product<MODE>(Acal + o, m, tiles, lbuf, right, st.bars, ph, st.tmem, threadIdx.x == 0,
-                         use_tma ? &tmaps.Acal : nullptr, o / m, st.lbars, lph);
+                         use_tma ? &tmaps.Acal : nullptr, o / m, st.lbars, lph, lbuf_bytes);
   if (ok) {
     const bool keep = (type == 0);
     drain_acc(st.tmem, tiles, m, [&](int row, int col, float v) {
@@ -1023,10 +1026,24 @@ template <typename K>
 void raise_smem_once(K kernel, int bytes, bool* done) {
   if (!*done) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // the largest shared-memory carve-out, so that launches sized below the
+    // maximum fit several CTAs per SM
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     *done = true;
   }
 }
 bool g_set_fwd[2], g_set_back[2];
+
+// Shared memory of one launch: the left buffers for its M-tiles and the right
+// panel for its K-slabs (blocks up to max_m), so that blocks of m <= 128 fit
+// two CTAs per SM.
+template <int MODE>
+int tc_launch_smem(int max_m, int* cap_tiles) {
+  using S = tc::Smem<MODE>;
+  *cap_tiles = (max_m + tc::MT - 1) / tc::MT;
+  const int nsl = (max_m + S::KA - 1) / S::KA;
+  return 1024 + 2 * *cap_tiles * S::tile_bytes + nsl * S::rslab_bytes + 64;
+}
 }  // namespace
 
 void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, int max_m, const float* A,
@@ -1039,16 +1056,17 @@ void launch_fwd_factor_tc(int mode, const PartDesc* parts, int nparts, int t, in
   const int use_tma = (tmaps != nullptr && mode == 0) ? 1 : 0;
   const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
   const dim3 grid((type_hi - type_lo) * tiles_n, nparts);
+  int cap = 0;
   if (mode == 0) {
-    const int bytes = tc::Smem<0>::total;
-    raise_smem_once(tc::k_fwd_factor_tc<0>, bytes, &g_set_fwd[0]);
+    const int bytes = tc_launch_smem<0>(max_m, &cap);
+    raise_smem_once(tc::k_fwd_factor_tc<0>, tc::Smem<0>::total, &g_set_fwd[0]);
     tc::k_fwd_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
-                                                              errflag, tm, use_tma);
+                                                              errflag, tm, use_tma, cap);
   } else {
-    const int bytes = tc::Smem<1>::total;
-    raise_smem_once(tc::k_fwd_factor_tc<1>, bytes, &g_set_fwd[1]);
+    const int bytes = tc_launch_smem<1>(max_m, &cap);
+    raise_smem_once(tc::k_fwd_factor_tc<1>, tc::Smem<1>::total, &g_set_fwd[1]);
     tc::k_fwd_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, t, tiles_n, type_lo, A, B, C, G, Acal, ZL, ZR,
-                                                              errflag, tm, 0);
+                                                              errflag, tm, 0, cap);
   }
 }
 
@@ -1061,14 +1079,16 @@ void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, i
   const int use_tma = (tmaps != nullptr && mode == 0) ? 1 : 0;
   const int tiles_n = (max_m + tc::NP - 1) / tc::NP;
   const dim3 grid(2 * tiles_n, nparts);
+  int cap = 0;
   if (mode == 0) {
-    const int bytes = tc::Smem<0>::total;
-    raise_smem_once(tc::k_back_factor_tc<0>, bytes, &g_set_back[0]);
-    tc::k_back_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, use_tma);
+    const int bytes = tc_launch_smem<0>(max_m, &cap);
+    raise_smem_once(tc::k_back_factor_tc<0>, tc::Smem<0>::total, &g_set_back[0]);
+    tc::k_back_factor_tc<0><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, use_tma,
+                                                               cap);
   } else {
-    const int bytes = tc::Smem<1>::total;
-    raise_smem_once(tc::k_back_factor_tc<1>, bytes, &g_set_back[1]);
-    tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, 0);
+    const int bytes = tc_launch_smem<1>(max_m, &cap);
+    raise_smem_once(tc::k_back_factor_tc<1>, tc::Smem<1>::total, &g_set_back[1]);
+    tc::k_back_factor_tc<1><<<grid, tc::kThreads, bytes, st>>>(parts, s, tiles_n, Acal, ZL, ZR, errflag, tm, 0, cap);
   }
 }
 
