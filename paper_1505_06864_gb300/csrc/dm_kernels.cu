@@ -297,8 +297,7 @@ __global__ void __launch_bounds__(256) k_inv_cluster(const PartDesc* __restrict_
   int* idx = perm + kMaxM;                                  // [kMaxM]
   int* inv_idx = idx + kMaxM;                               // [kMaxM]
   __shared__ int pubp[2];
-  __shared__ int s_p, s_bad;
-  __shared__ T s_akk, s_apk;
+  __shared__ int s_bad;
   const long long o = p.blk + (long long)t * m * m;
   T* g = G + o;
   if (tid == 0) s_bad = 0;

@@ -113,10 +113,8 @@ class Server {
   }
 
   void worker() {
-    int dev = 0;
     cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    (void)dev;
     for (;;) {
       Request r;
       {

@@ -477,7 +477,7 @@ struct TcState {
 };
 
 // Tensor maps of a level's float32 arrays (one 2-D view [rows][m] each).
-struct __align__(64) TmaMaps {
+struct TmaMaps {
   CUtensorMap G, A, Acal;
 };
 
