@@ -27,7 +27,9 @@ Functions and the passages they follow:
     partition_lengths_equal_time   Section 5.1 (equal execution time, Table 2)
     ta_factor/ta_solve/thomas   Section 3 (Thomas algorithm, forward and backward sweeps)
     dm               Section 2, Eqs. (e220)-(endSolution); recursion on the
-                     supplementary system as in Section 4.2.1
+                     supplementary system as in Section 4.2.1; with J >= 2 every
+                     subsystem solved by DM with J sub-subsystems (Section
+                     4.2.2, ``_dm_groups``)
     dense_ge         textbook Gaussian elimination with partial pivoting on the
                      assembled dense matrix (independent check, tiny systems)
     residual, refine_truth   r = b - T x in float64 / extended precision
@@ -35,9 +37,12 @@ Functions and the passages they follow:
                      Eq. DMrec1, Eqs. DMrec121/DMrec1212/DMrec122) and
                      Section 5 (Eqs. SpeedupMP, MAXSpeedP, SpeedupMPNk,
                      SuppMatrM, SuppMatrPM, DMrec2-P3DMrec4)
-Parity pins: every function above is pinned in tests/test_oracle_*.py by
-dense Gaussian elimination, manufactured solutions, exact operation counts and
-the paper's printed optimum values.  No function here is "parity unpinned".
+Parity pins: every function above is pinned in tests/test_oracle_pins.py by
+dense Gaussian elimination, manufactured solutions, an exactly known solution
+(``refine_truth``), exact operation counts of instrumented runs (Table 1,
+Table 2, Eqs. DMtotal, DMrec1, DMrec121/DMrec1212/DMrec122, DMrec3, DMrec4,
+SpeedupMPNk, SpeedupMiPNk) and the paper's printed optimum values.  No
+function here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -272,13 +277,102 @@ def supp_partitions(Ms: int, P: int, l: int, m: int):
     return max(p2, 1)
 
 
-def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=None):
+def _dm_groups(Ak, Bk, Ck, groups, J, ctr):
+    """DM applied to one subsystem of Eq. (e231) (Section 4.2.2): the
+    subsystem's block-tridiagonal matrix (Ak[0] and Ck[-1] unused) is split
+    into J sub-subsystems by J-1 inner separator rows (placement as in
+    partition_plan), each sub-subsystem is solved by the Thomas algorithm for
+    every right-hand-side group and for its own two spikes, the inner
+    supplementary system (J-1 blocks, Eq. e2311) is assembled and solved by
+    the Thomas algorithm, and Eq. (endSolution) gives every group's solution.
+
+    ``groups`` is a list of right-hand-side groups, each a list of one block
+    per row (None = structurally zero block) or None for an absent group;
+    the result has the same structure.  Operation counts go to the stages
+    "sub/<i>" (sub-subsystem i: its Thomas solves, its products with the
+    inner separators' blocks, its rows of Eq. endSolution) and "supp" (the
+    inner supplementary system), the split the paper's Eqs. (DMrec121),
+    (DMrec1212), (DMrec122) use."""
+    L = len(Bk)
+    starts, lens, seps = partition_plan(L, J)
+    ng = len(groups)
+    Y = [[None] * J for _ in range(ng)]       # Y[g][i]: group g on sub-subsystem i
+    SL, SR = [None] * J, [None] * J            # inner spikes of sub-subsystem i
+    for i in range(J):
+        s, Li = starts[i], lens[i]
+        Ai = [None] + [Ak[s + t] for t in range(1, Li)]
+        Bi = [Bk[s + t] for t in range(Li)]
+        Ci = [Ck[s + t] for t in range(Li - 1)] + [None]
+        with ctr.stage(f"sub/{i}"):
+            G, Acal = ta_factor(Ai, Bi, Ci, ctr)
+            for g, grp in enumerate(groups):
+                if grp is not None:
+                    Y[g][i] = ta_solve(G, Acal, Ai, [grp[s + t] for t in range(Li)], ctr)
+            if i > 0:
+                SL[i] = ta_solve(G, Acal, Ai, [Ak[s]] + [None] * (Li - 1), ctr)
+            if i < J - 1:
+                SR[i] = ta_solve(G, Acal, Ai, [None] * (Li - 1) + [Ck[s + Li - 1]], ctr)
+    # inner supplementary system on the separators q_0..q_{J-2}
+    Ms = J - 1
+    HA, HB, HC = [None] * Ms, [Bk[q] for q in seps], [None] * Ms
+    fh = [None if grp is None else [grp[q] for q in seps] for grp in groups]
+    for i in range(J):
+        with ctr.stage(f"sub/{i}"):
+            if i > 0:            # separator i-1 above: its C meets row 0 of sub-subsystem i
+                j = i - 1
+                Cq = Ck[seps[j]]
+                HB[j] = _sub(HB[j], _mul(Cq, SL[i][0], ctr))
+                if i < J - 1:
+                    HC[j] = _sub(None, _mul(Cq, SR[i][0], ctr))
+                for g in range(ng):
+                    if fh[g] is not None:
+                        fh[g][j] = _sub(fh[g][j], _mul(Cq, Y[g][i][0], ctr))
+            if i < J - 1:        # separator i below: its A meets the last row of sub-subsystem i
+                j = i
+                Aq = Ak[seps[j]]
+                if i > 0:
+                    HA[j] = _sub(None, _mul(Aq, SL[i][-1], ctr))
+                HB[j] = _sub(HB[j], _mul(Aq, SR[i][-1], ctr))
+                for g in range(ng):
+                    if fh[g] is not None:
+                        fh[g][j] = _sub(fh[g][j], _mul(Aq, Y[g][i][-1], ctr))
+    with ctr.stage("supp"):
+        G, Acal = ta_factor(HA, HB, HC, ctr)
+        h = [None if f is None else ta_solve(G, Acal, HA, f, ctr) for f in fh]
+    # Eq. (endSolution) inside the subsystem, for every group
+    out = []
+    for g in range(ng):
+        if groups[g] is None:
+            out.append(None)
+            continue
+        x = [None] * L
+        for i in range(J):
+            s, Li = starts[i], lens[i]
+            with ctr.stage(f"sub/{i}"):
+                for t in range(Li):
+                    v = Y[g][i][t]
+                    if i > 0:
+                        v = _sub(v, _mul(SL[i][t], h[g][i - 1], ctr))
+                    if i < J - 1:
+                        v = _sub(v, _mul(SR[i][t], h[g][i], ctr))
+                    x[s + t] = v
+        for j, q in enumerate(seps):
+            x[q] = h[g][j]
+        out.append(x)
+    return out
+
+
+def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=None, J=None):
     """Solve A_i X_{i-1} + B_i X_i + C_i X_{i+1} = F_i by the decomposition
     method with P subsystems (Section 2).
 
     levels = 1 solves the supplementary system (Eq. e232) by the Thomas
     algorithm; levels = L > 1 solves it by DM with P2 subsystems and
     levels = L - 1 (Section 4.2.1).  P = 1 is the Thomas algorithm itself.
+    J >= 2 solves every subsystem's Eq. (e231) by DM with J sub-subsystems
+    (Section 4.2.2): the right-hand sides F^k and the two columns of W_R^k
+    are carried as separate groups, so the structurally zero blocks of W_R^k
+    cost nothing.
     """
     ctr = ctr or _NoCount()
     A, B, C, F = np.asarray(A), np.asarray(B), np.asarray(C), np.asarray(F)
@@ -304,6 +398,15 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
         Bk = [B[s + t] for t in range(L)]
         Ck = [C[s + t] for t in range(L - 1)] + [None]
         with ctr.stage(f"solve/{k}"):
+            if J is not None and J >= 2:
+                grp = [[F[s + t] for t in range(L)],
+                       [A[s]] + [None] * (L - 1) if k > 0 else None,
+                       [None] * (L - 1) + [C[s + L - 1]] if k < P - 1 else None]
+                zk, zl, zr = _dm_groups(Ak, Bk, Ck, grp, J, ctr)
+                z.append(zk)
+                ZL.append(zl)
+                ZR.append(zr)
+                continue
             G, Acal = ta_factor(Ak, Bk, Ck, ctr)
             z.append(ta_solve(G, Acal, Ak, [F[s + t] for t in range(L)], ctr))
             ZL.append(ta_solve(G, Acal, Ak, [A[s]] + [None] * (L - 1), ctr) if k > 0 else None)

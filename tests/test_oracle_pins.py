@@ -104,6 +104,60 @@ def test_manufactured_solution_and_residual():
             assert np.linalg.norm(r) / np.linalg.norm(s.b) < 1e-15
 
 
+def _dyadic_ill_conditioned(N=4, eps_pow=22, seed=3):
+    """A block-tridiagonal system (m = 3, two right-hand sides) whose entries
+    are dyadic rationals with few bits, an integer solution x and b = T x
+    formed exactly (checked with Fractions), so x is known without rounding.
+    Every B_i has rows [1, 1, 0], [1, 1 + 2^-eps_pow, 0] and every A_i, C_i has
+    equal columns 0 and 1, so (1, -1, 0) placed in any block row is nearly a
+    null vector of T: cond(T) ~ 2^eps_pow."""
+    from fractions import Fraction as Fr
+    m = 3
+    rng = np.random.default_rng(seed)
+    A, B, C = (np.zeros((N, m, m)) for _ in range(3))
+    for i in range(N):
+        a = rng.integers(-4, 5) / 8.0
+        B[i] = [[1, 1, 0], [1, 1 + 2.0 ** -eps_pow, 0], [a, a, 2]]
+        for M_, on in ((A, i > 0), (C, i < N - 1)):
+            if on:
+                Mi = rng.integers(-2, 3, (m, m)) / 16.0
+                Mi[:, 1] = Mi[:, 0]
+                M_[i] = Mi
+    x = rng.integers(-8, 9, (N, m, 2)).astype(np.float64)
+    b = np.zeros((N, m, 2))
+    for i in range(N):
+        for r in range(m):
+            for c in range(2):
+                acc = Fr(0)
+                for k in range(m):
+                    acc += Fr(B[i, r, k]) * Fr(x[i, k, c])
+                    if i > 0:
+                        acc += Fr(A[i, r, k]) * Fr(x[i - 1, k, c])
+                    if i < N - 1:
+                        acc += Fr(C[i, r, k]) * Fr(x[i + 1, k, c])
+                b[i, r, c] = float(acc)
+                assert Fr(b[i, r, c]) == acc          # b is exact in float64
+    return A, B, C, x, b
+
+
+def test_refine_truth_reaches_exact_solution():
+    """refine_truth against an exactly known x on a system with cond(T) ~ 2e7:
+    the plain float64 solve is off by ~1e-5 and refinement with float64
+    residuals stalls near cond * 2^-53 (here 2.5e-10); refine_truth's
+    extended-precision residuals must get within 1e-12 (on x86 long double,
+    u = 2^-64; binary128 elsewhere)."""
+    A, B, C, x, b = _dyadic_ill_conditioned()
+    assert np.linalg.cond(o.dense_from_blocks(A, B, C)) > 1e7
+    assert o.rel_err(o.thomas(A, B, C, b), x) > 1e-7
+    xt = o.refine_truth(A, B, C, b)
+    assert o.rel_err(xt, x) < 1e-12
+    # the same loop with float64 residuals cannot pass this pin
+    xf = o.thomas(A, B, C, b)
+    for _ in range(6):
+        xf = xf + o.thomas(A, B, C, o.residual(A, B, C, xf, b))
+    assert o.rel_err(xf, x) > 1e-11
+
+
 def test_refine_truth_reduces_extended_residual():
     s = w.conditioned_system(10, 8, 1, 5, cond=1e4)
     x0 = o.thomas(s.A, s.B, s.C, s.b)
@@ -182,14 +236,124 @@ def test_table2_totals_are_sums_of_rows():
         assert rows + o.mo_dm_supp(M, n, l) == o.mo_dm_total(Ns, n, l)
 
 
-def test_dm_sub_counts_reduce_consistently():
-    # Eqs. (DMrec121)/(DMrec122): equal sub-subsystems give the L_i(9n^3+5n^2 l)
-    # and L_i(11n^3+5n^2 l) middle terms of Eq. (DMrec3).
-    n, l = 10, 1
-    L = [4, 4, 4, 4]
-    mid = o.mo_dm_sub_mid(L, n, l)
-    assert mid == ((9 * 4 - 2) * 2 + 11 * 4 * 2 + 7 * 4 - 11) * n ** 3 + ((4 * 4 - 1) * 2 + 5 * 8 + 3 * 4 - 5) * n ** 2 * l
-    assert o.mo_dm_sub_first([4, 4], n, l) > 0 and o.mo_dm_sub_last([4, 4], n, l) > 0
+# ---------------------------------------------------------------- DM inside subsystems (Section 4.2.2)
+@pytest.mark.parametrize("N,m,l,P,J,seed", [(40, 3, 2, 2, 2, 5), (40, 3, 2, 3, 3, 6), (31, 2, 1, 3, 2, 7),
+                                            (57, 4, 3, 4, 3, 8), (25, 2, 2, 2, 5, 9)])
+def test_dm_inside_matches_dense_ge(N, m, l, P, J, seed):
+    s = w.dominant_system(N, m, l, seed)
+    xd = o.dense_ge(o.dense_from_blocks(s.A, s.B, s.C), s.b.reshape(-1, l)).reshape(N, m, l)
+    for levels in (1, 2):
+        assert o.rel_err(o.dm(s.A, s.B, s.C, s.b, P, levels=levels, J=J), xd) < 1e-13
+
+
+def test_dm_inside_conditioned_blocks_matches_dense_ge():
+    s = w.conditioned_system(23, 4, 2, 12, cond=1e3)
+    xd = o.dense_ge(o.dense_from_blocks(s.A, s.B, s.C), s.b.reshape(-1, 2)).reshape(23, 4, 2)
+    assert o.rel_err(o.dm(s.A, s.B, s.C, s.b, 3, J=3), xd) < 1e-11
+
+
+@pytest.mark.parametrize("N,P,J,n,l", [(40, 2, 2, 3, 2), (40, 3, 3, 3, 2), (61, 4, 3, 2, 5), (52, 3, 4, 4, 1),
+                                       (33, 5, 2, 3, 3)])
+def test_dm_inside_counts_dmrec121_1212_122(N, P, J, n, l):
+    """The instrumented count of each subsystem's Eq. (e231) solved by DM with
+    J sub-subsystems equals Eq. (DMrec121) for k = 1, Eq. (DMrec1212) for
+    k = M and Eq. (DMrec122) in between, exactly, for the sub-subsystem sizes
+    the partition produces (unequal ones included)."""
+    s = w.dominant_system(N, n, l, 13)
+    ctr = o.OpCounter()
+    o.dm(s.A, s.B, s.C, s.b, P, J=J, ctr=ctr)
+    _, Ls, _ = o.partition_plan(N, P)
+    for k in range(P):
+        _, Lk, _ = o.partition_plan(Ls[k], J)
+        f = o.mo_dm_sub_first if k == 0 else (o.mo_dm_sub_last if k == P - 1 else o.mo_dm_sub_mid)
+        assert ctr.total(f"solve/{k}") == f(Lk, n, l), k
+        # the inner supplementary system's share is the formulas' last term
+        inner = {0: (4 * J - 6), P - 1: (6 * J - 10)}.get(k, 7 * J - 11)
+        assert ctr.total(f"solve/{k}/supp") == inner * n ** 3 + (3 * J - 5) * n ** 2 * l
+        # the rest of Eq. (DMtotal) is unchanged (Table 2 wings, Eq. endSolution)
+        assert ctr.total(f"wing/{k}") == o.mo_dm_wing(k + 1, P, n, l)
+        assert ctr.total(f"back/{k}") == o.mo_dm_back(k + 1, P, Ls[k], n, l)
+    assert ctr.total("supp") == o.mo_dm_supp(P, n, l)
+
+
+def test_dm_inside_serial_count_dmrec3():
+    """Eq. (DMrec3) is the serial count with P = M J processors: one middle
+    sub-subsystem of a middle subsystem (N_2 rows), that subsystem's inner
+    supplementary system, its wing products, the supplementary system of
+    Eq. (e232) and its rows of Eq. (endSolution) -- read off the counter."""
+    n, l, M, J, N2 = 3, 2, 3, 3, 2
+    N1 = J * N2 + J - 1
+    N = M * N1 + M - 1
+    s = w.dominant_system(N, n, l, 14)
+    ctr = o.OpCounter()
+    o.dm(s.A, s.B, s.C, s.b, M, J=J, ctr=ctr)
+    k, i = 1, 1
+    serial = (ctr.total(f"solve/{k}/sub/{i}") + ctr.total(f"solve/{k}/supp") + ctr.total(f"wing/{k}")
+              + ctr.total("supp") + ctr.total(f"back/{k}"))
+    assert ctr.total(f"solve/{k}/sub/{i}") == N2 * (11 * n ** 3 + 5 * n ** 2 * l)
+    assert serial == o.mo_dm_rec3(N, M, J, n, l)
+
+
+def test_dm_both_levels_serial_count_dmrec4():
+    """Eq. (DMrec4): Eq. (DMrec3) with the supplementary system solved by DM
+    with m subsystems of M_j = (M - m)/m rows: its serial part is one middle
+    subsystem of that DM plus its own supplementary system."""
+    n, l, msub, Mj, J, N2 = 3, 2, 3, 1, 3, 1
+    M = msub * (Mj + 1)
+    N1 = J * N2 + J - 1
+    N = M * N1 + M - 1
+    s = w.dominant_system(N, n, l, 15)
+    ctr = o.OpCounter()
+    o.dm(s.A, s.B, s.C, s.b, M, levels=2, P2=msub, J=J, ctr=ctr)
+    k, i, j = 1, 1, 1
+    supp_serial = (ctr.total(f"supp/solve/{j}") + ctr.total(f"supp/wing/{j}") + ctr.total(f"supp/back/{j}")
+                   + ctr.total("supp/supp"))
+    serial = (ctr.total(f"solve/{k}/sub/{i}") + ctr.total(f"solve/{k}/supp") + ctr.total(f"wing/{k}")
+              + supp_serial + ctr.total(f"back/{k}"))
+    assert serial == o.mo_dm_rec4(N, M, J, msub, n, l)
+
+
+# ---------------------------------------------------------------- Section 5.1 speedups from counted runs
+def _serial_count(ctr, ks):
+    return sum(ctr.total(f"{st}/{k}") for k in ks for st in ("solve", "wing", "back")) + ctr.total("supp")
+
+
+def test_speedup_unequal_from_counted_run():
+    """Eq. (SpeedupMPNk) is Mo_TA over the serial count of a run whose first
+    and last subsystems are alpha and beta times a middle one (the middle
+    subsystems take the longest): both counts come from the instrumented
+    solvers, not from the formulas."""
+    n, l = 4, 2
+    Nk, a, b, P = 4, 6, 5, 5
+    lengths = [a] + [Nk] * (P - 2) + [b]
+    N = sum(lengths) + P - 1
+    s = w.dominant_system(N, n, l, 16)
+    cta, ctr = o.OpCounter(), o.OpCounter()
+    o.thomas(s.A, s.B, s.C, s.b, cta)
+    o.dm(s.A, s.B, s.C, s.b, P, lengths=lengths, ctr=ctr)
+    per = [_serial_count(ctr, [k]) - ctr.total("supp") for k in range(P)]
+    assert max(per) == per[1]                       # a middle subsystem sets the time
+    S = cta.total() / _serial_count(ctr, [1])
+    assert o.speedup_mp_unequal(N, P, n, l, a / Nk, b / Nk) == pytest.approx(S, rel=1e-13)
+    # alpha = beta = 1 is Eq. (SpeedupMP)
+    assert o.speedup_mp_unequal(61, 6, n, l, 1.0, 1.0) == pytest.approx(o.speedup_mp(61, 6, n, l), rel=1e-15)
+
+
+@pytest.mark.parametrize("i", [1, 2, 3])
+def test_speedup_queue_from_counted_run(i):
+    """Eq. (SpeedupMiPNk): M = iP subsystems, a processor runs i middle
+    subsystems one after another, then the supplementary system."""
+    n, l, P = 3, 1, 3
+    Nk, a, b = 4, 7, 5
+    M = i * P
+    lengths = [a] + [Nk] * (M - 2) + [b]
+    N = sum(lengths) + M - 1
+    s = w.dominant_system(N, n, l, 17)
+    cta, ctr = o.OpCounter(), o.OpCounter()
+    o.thomas(s.A, s.B, s.C, s.b, cta)
+    o.dm(s.A, s.B, s.C, s.b, M, lengths=lengths, ctr=ctr)
+    S = cta.total() / _serial_count(ctr, list(range(1, i + 1)))
+    assert o.speedup_queue(N, P, i, n, l, a / Nk, b / Nk) == pytest.approx(S, rel=1e-13)
 
 
 # ---------------------------------------------------------------- Section 5 formulas
