@@ -39,7 +39,31 @@ import numpy as np  # noqa: E402
 
 N_, M_, R_, P_, LEV_ = 2048, 256, 1, 64, 3
 SEED = 2
-FP64_PEAK_TFLOPS = 1.25     # GB300 nominal float64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal float64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+BF16_FALLBACK_TFLOPS = 1900.0  # recipe fallback when the measured-peaks file is absent
+
+
+def measured_peaks():
+    """The measured peaks (HBM copy GB/s, cuBLAS bf16 TFLOP/s) if present."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def probe_peaks(dm):
+    """This library's own probes (dm_peak_probe): float64 and float32 FMA
+    loops, tcgen05 TF32 and bf16 MMA loops; best of 3 timed launches each."""
+    out = {}
+    for name, kind in (("fp64", dm.DM_PROBE_FP64), ("fp32", dm.DM_PROBE_FP32), ("tf32", dm.DM_PROBE_TF32),
+                       ("bf16", dm.DM_PROBE_BF16)):
+        try:
+            tf, ms = dm.dm_peak_probe(kind, 3)
+            out[name] = {"tflops": tf, "ms": ms}
+        except dm.DMError as e:
+            out[name] = {"error": str(e)}
+    return out
 
 
 def parse():
@@ -197,6 +221,8 @@ def main():
         dm.dm_factor(plan, A, B, C)
         return dm.dm_solve(plan, b, x, allow_notconv=mixed)
 
+    # measured arithmetic peaks (before any timing; ~2 s)
+    peaks = probe_peaks(dm) if rank == 0 or ws == 1 else {}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -206,9 +232,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
+    # timed region: the product's path (launch sequences replayed from CUDA
+    # graphs, no per-launch instrumentation)
     clocks = Clocks(local)
     clocks.start()
-    dm.dm_profile(plan, True)
     launches0 = dm.dm_launch_count(plan)
     barrier()
     torch.cuda.synchronize()
@@ -220,7 +247,6 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    prof = dm.dm_profile(plan, False)
     launches = dm.dm_launch_count(plan) - launches0
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
@@ -230,15 +256,34 @@ def main():
     flops_step = info["factor_flops"] + info["solve_flops"]
     value = job_value(args.steps, ws, total_ms)
 
+    # per-kernel durations: the same steps again, eagerly, with CUDA events
+    # around every launch on the plan's stream (a second timed region)
+    dm.dm_profile(plan, True)
+    ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev2[0].record(stream)
+    for k in range(args.steps):
+        step()
+    ev2[1].record(stream)
+    torch.cuda.synchronize()
+    prof = dm.dm_profile(plan, False)
+    prof_ms_step = ev2[0].elapsed_time(ev2[1]) / args.steps
+
     # roofline of the dominant kernel class (largest summed event time)
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     kname, kd = top
     achieved = kd["flops"] / (kd["ms"] / 1e3) / 1e12
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": read_traffic(kname) if not mixed else None,
-            "peak_source": "GB300 nominal float64 rate (152 SMs x 2.07 GHz x 4 flop/clk/SM)",
+    fp64_peak = peaks.get("fp64", {}).get("tflops")
+    if fp64_peak:
+        peak, src = fp64_peak, "measured: dm_peak_probe float64 FMA loop on this GPU (best of 3 launches)"
+    else:
+        peak, src = FP64_NOMINAL_TFLOPS, "GB300 nominal float64 rate (probe unavailable)"
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": read_traffic(kname) if not mixed else None,
+            "peak_source": src, "nominal_peak": FP64_NOMINAL_TFLOPS,
             "launches": kd["launches"], "avg_launch_ms": kd["ms"] / kd["launches"],
-            "share_of_step": kd["ms"] / sum(v["ms"] for v in prof.values())}
+            "share_of_step": kd["ms"] / sum(v["ms"] for v in prof.values()),
+            "timing": "CUDA events around each launch in a second run of the same steps "
+                      f"({prof_ms_step:.1f} ms/step instrumented vs {total_ms / args.steps:.1f} graph-replayed)"}
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                    "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
                for k, v in prof.items()}
@@ -256,11 +301,13 @@ def main():
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "relres": relres, "rel_err_vs_xtrue": rel_true,
         "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
+        "peaks": {"probes": peaks, "measured_file": {k: measured_peaks().get(k) for k in
+                                                      ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")}},
     }
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(dm, s, stream, ws)
         line["sweep"] = sweep_leg(dm, A, B, C, b, stream)
-        line["mixed"] = mixed_leg(dm, A, B, C, b, stream, xh)
+        line["mixed"] = mixed_leg(dm, A, B, C, b, stream, xh, peaks)
         if ws == 1:
             t, xo = cpu_oracle_solve(s)
             line["cpu_baseline"] = {"value": 1.0 / t, "unit": "systems/s", "cores": blas_threads(),
@@ -317,15 +364,18 @@ def read_traffic(kernel):
 
 
 def e2e_leg(dm, s, stream, ws, steps=3):
-    """Same metric through the C ABI with pinned host buffers (copies timed)."""
+    """Same metric through the C ABI with pinned host buffers (copies timed),
+    after three warm-up steps (the first replay captures the CUDA graphs);
+    beside it the pinned host-to-device bandwidth of one 1 GiB copy."""
     import torch
     pin = lambda a: torch.from_numpy(a).pin_memory()
     A, B, C, b = pin(s.A), pin(s.B), pin(s.C), pin(s.b)
     x = torch.empty_like(b).pin_memory()
     plan = dm.dm_plan(N_, M_, R_, P_, LEV_, dm.DM_FP64)
     dm.dm_set_stream(plan, stream)
-    dm.dm_factor(plan, A, B, C)
-    dm.dm_solve(plan, b, x)
+    for _ in range(3):
+        dm.dm_factor(plan, A, B, C)
+        dm.dm_solve(plan, b, x)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -333,10 +383,45 @@ def e2e_leg(dm, s, stream, ws, steps=3):
         dm.dm_solve(plan, b, x)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
+    # the same plan with device-resident inputs, and the factor / solve calls
+    # of the host-input step timed apart (host clock around synchronised calls)
+    dev = [t.to("cuda") for t in (A, B, C, b)]
+    xd = torch.empty_like(dev[3])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dm.dm_factor(plan, *dev[:3])
+        dm.dm_solve(plan, dev[3], xd)
+    torch.cuda.synchronize()
+    dt_dev = (time.perf_counter() - t0) / steps
+    tf = ts = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        dm.dm_factor(plan, A, B, C)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dm.dm_solve(plan, b, x)
+        torch.cuda.synchronize()
+        tf += t1 - t0
+        ts += time.perf_counter() - t1
+    del dev, xd
     dm.dm_destroy(plan)
+    dA = torch.empty(A.shape, dtype=A.dtype, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dA.copy_(A, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record()
+    dA.copy_(A, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    h2d_gbs = A.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del dA
     h2d = 8 * (3 * N_ * M_ * M_ + N_ * M_ * R_)
     return {"value": ws / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * N_ * M_ * R_,
-            "ms_per_step": 1e3 * dt}
+            "ms_per_step": 1e3 * dt, "pinned_h2d_gbs": h2d_gbs,
+            "h2d_ms_at_that_rate": h2d / (h2d_gbs * 1e9) * 1e3,
+            "same_plan_device_inputs_ms": 1e3 * dt_dev,
+            "host_inputs_factor_ms": 1e3 * tf / steps, "host_inputs_solve_ms": 1e3 * ts / steps}
 
 
 def timed(fn, reps=1):
@@ -367,23 +452,45 @@ def sweep_leg(dm, A, B, C, b, stream):
     return out
 
 
-def mixed_leg(dm, A, B, C, b, stream, x64):
-    """float32 factors + float64 refinement on the same workload."""
+def mixed_leg(dm, A, B, C, b, stream, x64, peaks, steps=5):
+    """float32 factors + float64 refinement on the same workload: systems/s
+    from CUDA events over `steps` graph-replayed steps after 3 warm-ups; then
+    one instrumented step for the per-kernel times and the roofline of the
+    factor products (fwd_factor: tcgen05 for tf32 / bf16x3, whose MMA flops
+    are 1x / 3x the algorithmic ones)."""
     import torch
     out = {}
     x = torch.empty_like(b)
+    mp = measured_peaks()
+    bf16_peak = mp.get("bf16_tflops") or BF16_FALLBACK_TFLOPS
     for name in ("fp32", "tf32", "bf16x3"):
         plan = dm.dm_plan(N_, M_, R_, P_, LEV_, name)
         dm.dm_set_stream(plan, stream)
-        dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x, allow_notconv=True))[1], reps=3)
+        ms, rel = _timed_steps(dm, plan, A, B, C, b, x, steps, 3, stream, True)
         q = dm.dm_plan_query(plan)
-        dm.dm_profile(plan, True)
+        prof = dm.dm_profile(plan, True)
         dm.dm_factor(plan, A, B, C)
         dm.dm_solve(plan, b, x, allow_notconv=True)
         prof = dm.dm_profile(plan, False)
-        out[name] = {"systems_per_s": 1.0 / dt, "ms": 1e3 * dt, "iters": q["last_iters"], "relres": rel,
-                     "rel_err_vs_fp64_dm": rel_err(x.cpu().numpy(), x64),
-                     "kernels_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+        rec = {"systems_per_s": 1e3 / ms, "ms": ms, "iters": q["last_iters"], "relres": rel,
+               "rel_err_vs_fp64_dm": rel_err(x.cpu().numpy(), x64),
+               "kernels_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+        ff = prof.get("fwd_factor")
+        if ff and ff["ms"] > 0 and name != "fp32":
+            alg = ff["flops"] / (ff["ms"] / 1e3) / 1e12
+            mult = 3.0 if name == "bf16x3" else 1.0
+            if name == "bf16x3":
+                pk, src = bf16_peak, "bf16 dense, measured cuBLAS burst (MEASURED_PEAKS.json)" if mp.get(
+                    "bf16_tflops") else "bf16 dense, recipe fallback"
+            else:
+                pk = peaks.get("tf32", {}).get("tflops") or bf16_peak / 2
+                src = "tf32 dense, measured dm_peak_probe tcgen05 kind::tf32 loop"
+            rec["roofline"] = {"kernel": "fwd_factor (k_fwd_factor_tc)", "bound": "tensor",
+                               "achieved_algorithmic": alg, "mma_flops_per_algorithmic": mult,
+                               "achieved": alg * mult, "peak": pk, "unit": "TFLOP/s", "frac": alg * mult / pk,
+                               "peak_source": src, "launches": ff["launches"],
+                               "avg_launch_ms": ff["ms"] / ff["launches"]}
+        out[name] = rec
         dm.dm_destroy(plan)
     return out
 

@@ -82,6 +82,7 @@ typedef struct dm_plan_info {
   double solve_flops;    /* algorithmic flops of one solve sweep (without refinement) */
   int residual_mode;     /* DM_RESIDUAL_FP64 or DM_RESIDUAL_SLICED */
   int residual_tc_systems; /* systems whose residual runs on the tensor cores */
+  int J;                 /* sub-subsystems per subsystem (dm_plan_inside), else 1 */
 } dm_plan_info;
 
 /* Plan the solution of one system of N block rows, blocks m x m, nrhs
@@ -110,6 +111,27 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
  * normally faster there. */
 #define DM_PLAN_EQUAL_TIME 1
 int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags);
+
+/* DM inside the subsystems (Section 4.2.2; counts Eqs. DMrec121, DMrec1212,
+ * DMrec122; serial counts Eq. DMrec3 and, with outer_levels = 2, Eq. DMrec4).
+ * The system is split into M subsystems (equal sizes as in dm_plan), and the
+ * subsystem equations of Eq. (e231) are themselves solved by DM: every
+ * subsystem is split into J sub-subsystems (the same rule; each needs >= 1
+ * row, i.e. every subsystem >= 2J - 1 rows), their J - 1 inner separators
+ * form the subsystem's inner supplementary system, and the M - 1 outer
+ * separators the supplementary system of Eq. (e232), solved by block Thomas
+ * (outer_levels = 1) or by DM (outer_levels = 2, its subsystem count from
+ * Eq. SuppMatrM).  The sub-subsystems' sweeps (M J of them, each about
+ * (N - M + 1) / (M J) rows long) run in parallel, so the sequential chain is
+ * J times shorter than with M subsystems.  Executed as DM with the M J
+ * sub-subsystems whose supplementary system is split into M parts at the
+ * outer separators: each part is one subsystem's inner supplementary system,
+ * and the subsystem spikes Z^k of Eq. (e231) are applied in this factored
+ * form (sub-subsystem spikes, inner supplementary solution) rather than
+ * formed over all rows; x is the same.  Arguments and errors as for dm_plan;
+ * DM_EINVAL also for M < 1, J < 2, outer_levels not 1 or 2, or subsystems
+ * too short for J. */
+int dm_plan_inside(dm_plan_t* out, int N, int m, int nrhs, int M, int J, int outer_levels, int precision);
 
 /* Subsystem sizes (rows, in order) a plan with these arguments uses; host
  * only.  `lengths` receives P values (P = the effective P: 0 = the tuner's). */
@@ -283,6 +305,24 @@ int dm_set_residual(dm_plan_t plan, int mode);
  * another.  DM_ESTATE before dm_factor. */
 int dm_residual(dm_plan_t plan, const double* x, const double* b, double* r, double* relres_out);
 int dm_plan_query(dm_plan_t plan, dm_plan_info* info);
+
+/* Measured arithmetic peak of the current device, for roofline denominators
+ * (the paper has no counterpart).  kind: DM_PROBE_FP64 / DM_PROBE_FP32 -- the
+ * inner loop of a register-tiled matrix product (4 x 4 accumulators per
+ * thread, each fused multiply-add reading two shared operands) at full
+ * occupancy;
+ * DM_PROBE_TF32 / DM_PROBE_BF16 -- one CTA per SM issuing back-to-back
+ * tcgen05.mma (M = 128, N = 256, float32 accumulate) from shared memory.
+ * One warm-up launch, then `repeat` launches of about 0.1 s timed with CUDA
+ * events; *tflops_out receives the best (flops = 2 per multiply-add),
+ * *ms_out (may be NULL) that launch's time.  Allocates 64 bytes.  Changes no
+ * clock or power setting. */
+#define DM_PROBE_FP64 0
+#define DM_PROBE_FP32 1
+#define DM_PROBE_TF32 2
+#define DM_PROBE_BF16 3
+int dm_peak_probe(int kind, int repeat, double* tflops_out, double* ms_out);
+
 void dm_destroy(dm_plan_t plan);
 const char* dm_last_error(void);
 

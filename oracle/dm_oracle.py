@@ -377,6 +377,11 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
     ctr = ctr or _NoCount()
     A, B, C, F = np.asarray(A), np.asarray(B), np.asarray(C), np.asarray(F)
     N, m, l = B.shape[0], B.shape[1], F.shape[2]
+    if P == 1 and J is not None and J >= 2:
+        # the whole system is the one subsystem: Eq. (e231) without spikes, by DM
+        with ctr.stage("solve/0"):
+            x = _dm_groups([None] + list(A[1:]), list(B), list(C[:-1]) + [None], [list(F)], J, ctr)[0]
+        return np.stack(x)
     if P == 1:
         with ctr.stage("ta"):
             return thomas(A, B, C, F, ctr)

@@ -116,7 +116,10 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     nrows += sp.N;
     sysd.push_back(sd);
     std::vector<int> starts, lens, sepr;
-    partition_lengths(sp.N, sp.P, sp.m, sp.r, sp.flags, lens);
+    if (sp.J >= 2)
+      nested_lengths(sp.N, sp.P / sp.J, sp.J, lens);
+    else
+      partition_lengths(sp.N, sp.P, sp.m, sp.r, sp.flags, lens);
     {
       int r0 = 0;
       for (int k = 0; k < sp.P; ++k) {
@@ -205,6 +208,9 @@ void Level::compute_costs() {
   c_back.assign(std::max(Lmax, 1), Cost());
   c_fwds.assign(std::max(Lmax, 1), Cost());
   c_backs.assign(std::max(Lmax, 1), Cost());
+  c_fwdA.assign(std::max(Lmax, 1), Cost());
+  c_fwdB.assign(std::max(Lmax, 1), Cost());
+  c_cvt = Cost();
   c_asm_h = c_asm_f = c_backsub = c_resid = c_axpy = c_sepcopy = Cost();
   std::vector<double> chain(std::max(Lmax, 1), 0.0);
   for (const PartDesc& p : parts) {
@@ -220,6 +226,19 @@ void Level::compute_costs() {
       if (t < p.L - 1) { cf.flops += 2 * m3; cf.bytes += es * m2 * 3 + 24.0 * m2; }
       else if (hr) { cf.flops += m3; cf.bytes += es * m2 * 2 + 8.0 * m2; }
       if (hl) { cf.flops += (t == 0 ? m3 : 2 * m3); cf.bytes += 8.0 * m2 + es * m2 * (t == 0 ? 1 : 2) + (hl && t + 1 < p.L ? 0 : 0); }
+      {
+        // the same products split as the tensor-core step kernels launch them:
+        // A = G_t [C_t | Y_t], B = A_{t+1} [Acal_t | Bcal_t]
+        Cost& ca = c_fwdA[t];
+        if (t < p.L - 1 || hr) { ca.flops += m3; ca.bytes += es * m2 * 2 + 3 * es * m2; }
+        if (hl) { ca.flops += m3; ca.bytes += es * m2 * 2 + 2 * es * m2; }
+        if (t < p.L - 1) {
+          Cost& cb = c_fwdB[t];
+          cb.flops += m3;
+          cb.bytes += es * m2 * 2 + 2 * es * m2;
+          if (hl) { cb.flops += m3; cb.bytes += es * m2 + es * m2; }
+        }
+      }
       Cost& cs = c_fwds[t];
       cs.flops += (t == 0 ? m2r : 2 * m2r);
       cs.bytes += es * m2 + (t ? 8.0 * m2 + es * mr : 0) + 8.0 * mr + es * mr;
@@ -238,6 +257,7 @@ void Level::compute_costs() {
       c_backsub.bytes += ns * es * m2 + es * mr + 8.0 * mr;
     }
   }
+  c_cvt.bytes = (double)nblk * (3 * 8.0 + 3 * 4.0);  // A, B, C read as float64, their copies written
   fwd_chain_frac.assign(std::max(Lmax, 1), 1.0);
   for (int t = 0; t < Lmax; ++t) fwd_chain_frac[t] = c_fwd[t].flops > 0 ? chain[t] / c_fwd[t].flops : 1.0;
   for (const SepDesc& d : seps) {
@@ -258,10 +278,31 @@ void Level::compute_costs() {
   }
 }
 
+// Device bytes of the tensor-core step kernels' operand copies (4 bytes per
+// element in both modes: float32, or bf16 hi + lo): B32, A, C^T (+ Acal for
+// split bf16) over all blocks, and the rolling buffers (G for split bf16,
+// Acal^T, Y^T, two slots each of ZL^T, ZR^T) per subsystem.
+static size_t tc2_bytes(int mode, long long nblk, int nparts, int m) {
+  const size_t mm = (size_t)m * m;
+  return (size_t)nblk * 4 * (mode == 1 ? 4 : 3) + (size_t)nparts * mm * 4 * (mode == 1 ? 7 : 6);
+}
+
+static bool uniform_m(const std::vector<SysSpec>& spec, int m) {
+  for (const SysSpec& sp : spec)
+    if (sp.m != m) return false;
+  return true;
+}
+
+static bool tc2_wanted(const Level& L) {
+  const char* e = std::getenv("DM_TC_STEP");
+  return L.tc_mode >= 0 && !(e && e[0] == '0') && uniform_m(L.spec, L.max_m) && tc2_eligible(L.max_m);
+}
+
 size_t Level::bytes_needed() const {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   size_t b = 3 * nblk * sizeof(double);     // A, B, C
-  if (tc_mode >= 0) b += 3 * nblk * sizeof(float);
+  if (tc2_wanted(*this)) b += tc2_bytes(tc_mode, nblk, nparts, max_m);
+  else if (tc_mode >= 0) b += 3 * nblk * sizeof(float);
   b += 4 * nblk * es;                       // G, Acal, ZL, ZR
   b += nvec * es;                           // z
   b += 2 * nvec * sizeof(double);           // F, X
@@ -306,14 +347,47 @@ int Level::allocate() {
   DM_ALLOC(d_sys, std::max<size_t>(1, sysd.size()) * sizeof(SysDesc));
   DM_ALLOC(status, std::max(1, nsys) * sizeof(int));
   DM_ALLOC(d_err, sizeof(int));
-  if (tc_mode >= 0) {
+  if (tc_mode >= 0 && tc2_wanted(*this)) {
+    // operand copies and tensor maps of the tensor-core step kernels
+    Tc2Level& T = tc2;
+    const int m = max_m, mode = tc_mode, np = std::max(1, nparts), parts_ = mode == 1 ? 2 : 1;
+    const long long mm = (long long)m * m, nb = nblk / mm;
+    const size_t blk4 = (size_t)mm * 4;  // bytes of one block copy (both modes)
+    T.mode = mode;
+    DM_ALLOC(B32, nblk * sizeof(float));
+    if (mode == 0) {
+      DM_ALLOC(A32, nblk * sizeof(float));
+      T.A = A32;
+    } else {
+      DM_ALLOC(T.A, nb * blk4);
+      DM_ALLOC(T.Acal, nb * blk4);
+      DM_ALLOC(T.G, np * blk4);
+    }
+    DM_ALLOC(T.CT, nb * blk4);
+    DM_ALLOC(T.AcalT, np * blk4);
+    DM_ALLOC(T.YT, np * blk4);
+    DM_ALLOC(T.ZLT, 2 * np * blk4);
+    DM_ALLOC(T.ZRT, 2 * np * blk4);
+    T.capA = T.capCT = T.capAcal = nb;
+    T.capG = T.capAcalT = T.capYT = np;
+    T.capZLT = T.capZRT = 2 * np;
+    const int nt = tc2_ntile(m);
+    const void* lbase[3] = {mode == 0 ? G : T.G, T.A, mode == 0 ? Acal : T.Acal};
+    const long long lblk[3] = {mode == 0 ? nb : T.capG * parts_, T.capA * parts_, mode == 0 ? nb : T.capAcal * parts_};
+    const void* rbase[5] = {T.CT, T.YT, T.AcalT, T.ZLT, T.ZRT};
+    const long long rblk[5] = {T.capCT * parts_, T.capYT * parts_, T.capAcalT * parts_, T.capZLT * parts_,
+                               T.capZRT * parts_};
+    bool ok = tc2_map_bytes() == 128;
+    for (int i = 0; ok && i < 3; ++i) ok = tc2_make_map(mode, lbase[i], lblk[i], m, 128, T.maps[i]);
+    for (int i = 0; ok && i < 5; ++i) ok = tc2_make_map(mode, rbase[i], rblk[i], m, nt, T.maps[3 + i]);
+    if (!ok) return set_error(DM_ECUDA, "tensor map creation for the tensor-core step kernels failed (m = %d)", m);
+    T.on = true;
+  } else if (tc_mode >= 0) {
     DM_ALLOC(A32, nblk * sizeof(float));
     DM_ALLOC(B32, nblk * sizeof(float));
     DM_ALLOC(C32, nblk * sizeof(float));
     // TF32 sweeps stream G, A32, Acal by TMA when every system has the same m
-    bool uniform = true;
-    for (const SysSpec& sp : spec) uniform = uniform && sp.m == max_m;
-    if (tc_mode == 0 && uniform && tma_maps_bytes() <= (int)sizeof(tmaps))
+    if (tc_mode == 0 && uniform_m(spec, max_m) && tma_maps_bytes() <= (int)sizeof(tmaps))
       has_tma = make_tma_maps(static_cast<float*>(G), A32, static_cast<float*>(Acal), nblk / max_m, max_m, tmaps);
   }
 #undef DM_ALLOC
@@ -366,7 +440,7 @@ Level::~Level() {
 // Profiler
 const char* const kClassNames[K_NCLASS] = {
     "inv", "fwd_factor", "back_factor", "assemble_h", "fwd_solve", "back_solve", "assemble_f",
-    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve"};
+    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve", "tc_convert"};
 
 cudaEvent_t Prof::take() {
   if (!pool.empty()) {
@@ -434,6 +508,66 @@ Prof::~Prof() {
     (pf).end((st), e0_, (cls), (cost).flops, (cost).bytes, (active) > 0); \
   } while (0)
 
+// Forward and backward sweeps of a float32 level on the tensor-core step
+// kernels (dm_tc2.cu): operand copies of A, B, C^T and Y_0 = A_first^T, then
+// per step the inversion, (split bf16) the copy of G_t, launch A = G_t [C_t |
+// Y_t] and launch B = A_{t+1} [Acal_t | Bcal_t]; then the backward steps.
+static void factor_level_tc2(Level& L, cudaStream_t st, Prof& pf) {
+  Tc2Level& T = L.tc2;
+  const int m = L.max_m, mode = T.mode;
+  const long long nb = L.nblk / ((long long)m * m);
+  float* G = static_cast<float*>(L.G);
+  Tc2Out out;
+  out.B32 = L.B32;
+  out.G = G;
+  out.Acal = static_cast<float*>(L.Acal);
+  out.ZL = static_cast<float*>(L.ZL);
+  out.ZR = static_cast<float*>(L.ZR);
+  out.acal_l = T.Acal;
+  out.acalT = T.AcalT;
+  out.yT = T.YT;
+  out.zlT = T.ZLT;
+  out.zrT = T.ZRT;
+  out.cap_acal_l = T.capAcal;
+  out.cap_acalT = T.capAcalT;
+  out.cap_yT = T.capYT;
+  out.cap_zlT = T.capZLT;
+  out.cap_zrT = T.capZRT;
+  alignas(64) unsigned char maps[3][3][128];
+  const int sel[3][3] = {{0, 3, 4}, {1, 5, 6}, {2, 6, 7}};  // left, right 0, right 1 of kinds 0, 1, 2
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i) std::memcpy(maps[k][i], T.maps[sel[k][i]], 128);
+  const int lo[3][3] = {{(int)T.capG, (int)T.capCT, (int)T.capYT},
+                        {(int)T.capA, (int)T.capAcalT, (int)T.capZLT},
+                        {(int)T.capAcal, (int)T.capZLT, (int)T.capZRT}};
+  auto convert_inputs = [&] {
+    launch_to_f32(L.B, L.B32, L.nblk, st);
+    if (mode == 0) launch_to_f32(L.A, L.A32, L.nblk, st);
+    else launch_tc2_convert(1, L.A, nullptr, nullptr, (int)nb, 0, m, false, T.A, T.capA, st);
+    launch_tc2_convert(mode, L.C, nullptr, nullptr, (int)nb, 0, m, true, T.CT, T.capCT, st);
+    launch_tc2_convert(mode, L.A, nullptr, L.d_parts, L.nparts, 0, m, true, T.YT, T.capYT, st);
+  };
+  DM_LAUNCH(pf, st, K_TC_CONVERT, L.c_cvt, 1, convert_inputs());
+  for (int t = 0; t < L.Lmax; ++t) {
+    const int np = L.active_fwd[t];
+    DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<float>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
+    if (mode == 1) {
+      Cost c;
+      c.bytes = 8.0 * np * m * m;
+      DM_LAUNCH(pf, st, K_TC_CONVERT, c, np,
+                launch_tc2_convert(1, nullptr, G, L.d_parts, np, t, m, false, T.G, T.capG, st));
+    }
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdA[t], np,
+              launch_tc2_step(mode, 0, L.d_parts, np, t, m, lo[0], out, maps[0], L.d_err, st));
+    const int nbk = L.active_back[t];
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdB[t], nbk,
+              launch_tc2_step(mode, 1, L.d_parts, nbk, t, m, lo[1], out, maps[1], L.d_err, st));
+  }
+  for (int s = 0; s + 1 < L.Lmax; ++s)
+    DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], L.active_back[s],
+              launch_tc2_step(mode, 2, L.d_parts, L.active_back[s], s, m, lo[2], out, maps[2], L.d_err, st));
+}
+
 // Forward and backward spike sweeps, assembly, and the factorisation of the
 // supplementary level (recursively).  A, B, C must hold the level's blocks.
 template <typename T>
@@ -444,6 +578,16 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   T* ZR = static_cast<T*>(L.ZR);
   // With a side stream, the left-spike tiles of step t (type 1) run there,
   // overlapping the next inversion, which depends only on the type-0 tiles.
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.tc2.on) {
+      factor_level_tc2(L, st, pf);
+      if (L.supp)
+        DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
+                  launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
+                                       L.supp->C, st));
+      return;
+    }
+  }
   const bool split = aux && aux->st;
   cudaStream_t sb = split ? aux->st : st;
   if (L.tc_mode >= 0) {
@@ -665,6 +809,7 @@ int Plan::run(GraphCache& g, F&& body) {
 
 int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
+  DM_CUDA(cudaGetDevice(&device));
   top.lazy_inputs = true;
   int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
@@ -1013,6 +1158,20 @@ void partition_lengths(int N, int P, int m, int r, int flags, std::vector<int>& 
   }
 }
 
+// DM inside the subsystems (Section 4.2.2): M subsystems of the equal
+// partition, each split into J sub-subsystems by the same rule; the M J
+// sub-subsystem lengths in order (an inner separator between the
+// sub-subsystems of one subsystem, the outer separators between subsystems).
+void nested_lengths(int N, int M, int J, std::vector<int>& lens) {
+  std::vector<int> st, Lk, sp, st2, Li, sp2;
+  partition_plan(N, M, st, Lk, sp);
+  lens.clear();
+  for (int k = 0; k < M; ++k) {
+    partition_plan(Lk[k], J, st2, Li, sp2);
+    lens.insert(lens.end(), Li.begin(), Li.end());
+  }
+}
+
 // Eq. (MAXSpeedP): P* = sqrt((N+1)/3 (5 + 2/(1 + l/n))), clamped to 1..(N+1)/2.
 int tuner_seed_p(int N, int m, int r) {
   const double c = 5.0 + 2.0 / (1.0 + (double)r / m);
@@ -1102,6 +1261,39 @@ int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int pr
   s.flags = flags;
   std::unique_ptr<dm_plan_s> p(new dm_plan_s());
   rc = p->plan.init(std::vector<SysSpec>{s}, precision);
+  if (rc) return rc;
+  *out = p.release();
+  return DM_OK;
+}
+
+int dm_plan_inside(dm_plan_t* out, int N, int m, int nrhs, int M, int J, int outer_levels, int precision) {
+  if (!out) return set_error(DM_EINVAL, "out is NULL");
+  if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
+    return set_error(DM_EINVAL, "unknown precision %d", precision);
+  if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)
+    return set_error(DM_EINVAL, "tensor-core precisions support m <= %d", kMaxMTensor);
+  if (N < 1 || m < 1 || nrhs < 1 || m > kMaxM || nrhs > kMaxR)
+    return set_error(DM_EINVAL, "invalid sizes N = %d, m = %d, nrhs = %d", N, m, nrhs);
+  if (M < 1 || J < 2 || (outer_levels != 1 && outer_levels != 2))
+    return set_error(DM_EINVAL, "dm_plan_inside needs M >= 1, J >= 2, outer_levels 1 or 2");
+  if (M > 1 && 2 * M - 1 > N) return set_error(DM_EINVAL, "M = %d too large for N = %d", M, N);
+  {
+    std::vector<int> st, Lk, sp;
+    partition_plan(N, M, st, Lk, sp);
+    const int Lmin = *std::min_element(Lk.begin(), Lk.end());
+    if (2 * J - 1 > Lmin)
+      return set_error(DM_EINVAL, "J = %d too large: the shortest subsystem has %d rows (needs >= 2J - 1)", J, Lmin);
+  }
+  SysSpec s;
+  s.N = N;
+  s.m = m;
+  s.r = nrhs;
+  s.P = M * J;
+  s.J = J;
+  s.P2 = M;
+  s.levels = M > 1 ? 1 + outer_levels : 2;
+  std::unique_ptr<dm_plan_s> p(new dm_plan_s());
+  int rc = p->plan.init(std::vector<SysSpec>{s}, precision);
   if (rc) return rc;
   *out = p.release();
   return DM_OK;
@@ -1209,6 +1401,7 @@ int dm_plan_query(dm_plan_t plan, dm_plan_info* info) {
   info->solve_flops = p.solve_flops;
   info->residual_mode = p.resid_mode;
   info->residual_tc_systems = p.top.nres_tc;
+  info->J = s.J;
   return DM_OK;
 }
 

@@ -119,6 +119,30 @@ void launch_back_factor_tc(int mode, const PartDesc* parts, int nparts, int s, i
 bool make_tma_maps(const float* G, const float* A32, const float* Acal, long long rows, int m, void* out);
 int tma_maps_bytes();
 constexpr int kMaxMTensor = 256;
+// Peak probe: one CTA per SM issuing back-to-back tcgen05 MMAs (mode 0 TF32,
+// 1 bf16); returns the launch's flops.
+double launch_mma_probe(int mode, int iters, int* errflag, cudaStream_t st);
+
+// Tensor-core step kernels with TMA-fed operand copies (dm_tc2.cu); see
+// Tc2Level.  kind 0: G_t [C_t | Y_t]; 1: A_{t+1} [Acal_t | Bcal_t];
+// 2: Acal_t [ZL_{t+1} | ZR_{t+1}] (backward step).
+// Destinations of the step kernels' epilogues (element offsets of the operand
+// copies are block index x m^2; `cap_*` are the copies' block capacities,
+// i.e. where their lo parts start).
+struct Tc2Out {
+  const float* B32;
+  float *G, *Acal, *ZL, *ZR;
+  void *acal_l, *acalT, *yT, *zlT, *zrT;
+  long long cap_acal_l, cap_acalT, cap_yT, cap_zlT, cap_zrT;
+};
+bool tc2_eligible(int m);
+int tc2_ntile(int m);
+bool tc2_make_map(int mode, const void* base, long long blocks, int m, int box_rows, void* out);
+int tc2_map_bytes();
+void launch_tc2_convert(int mode, const double* src64, const float* src32, const PartDesc* parts, int nq, int t, int m,
+                        bool trans, void* dst, long long cap_blocks, cudaStream_t st);
+void launch_tc2_step(int mode, int kind, const PartDesc* parts, int nparts, int step, int m, const int lo[3],
+                     const Tc2Out& out, const void* maps3, int* errflag, cudaStream_t st);
 
 constexpr int kMaxM = 512;
 constexpr int kMaxR = 64;

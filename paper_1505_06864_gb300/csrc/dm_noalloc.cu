@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/dm.h"
@@ -77,15 +78,45 @@ extern "C" int dm_solve_noalloc(int N, int m, int nrhs, int P, const double* A, 
   if (m > kMaxM || nrhs > kMaxR) return set_error(DM_EINVAL, "m or nrhs above the library limits");
   if (P > kNoallocMaxP) return set_error(DM_EINVAL, "dm_solve_noalloc supports P <= %d", kNoallocMaxP);
   if (P > 1 && 2 * P - 1 > N) return set_error(DM_EINVAL, "P = %d too large for N = %d", P, N);
-  const long long mm = (long long)m * m, mr = (long long)m * nrhs, Ms = P - 1;
-  // bytes this call needs in the scratch array (same carving order as below)
-  const size_t need = 256 * 20 + sizeof(double) * (size_t)(4 * N * mm + N * mr + 5 * Ms * mm + 3 * Ms * mr) +
-                      sizeof(PartDesc) * (P + 1) + sizeof(SepDesc) * std::max(1, P - 1) + 2 * sizeof(int);
+  // every block row needs at least 4 doubles of workspace (G, Acal, ZL, ZR of
+  // a 1 x 1 block): reject N beyond that before any size arithmetic
+  if ((size_t)N > kScratchBytes / (4 * sizeof(double)))
+    return set_error(DM_EINVAL, "N = %d above dm_solve_noalloc's workspace limit", N);
+  const long long mm = (long long)m * m, mr = (long long)m * nrhs, Ms = P - 1, NN = N;
+  // bytes this call needs in the scratch array (same carving order as below);
+  // N <= 2^20 and m^2 <= 2^18 keep every term far inside 64 bits
+  const unsigned long long need =
+      256ull * 20 + sizeof(double) * (unsigned long long)(4 * NN * mm + NN * mr + 5 * Ms * mm + 3 * Ms * mr) +
+      sizeof(PartDesc) * (unsigned long long)(P + 1) + sizeof(SepDesc) * (unsigned long long)std::max(1, P - 1) +
+      2 * sizeof(int);
   if (need > kScratchBytes)
     return set_error(DM_EINVAL,
-                     "system needs %zu bytes of workspace, above dm_solve_noalloc's static %zu bytes "
+                     "system needs %llu bytes of workspace, above dm_solve_noalloc's static %zu bytes "
                      "(4 N m^2 + 5 (P-1) m^2 doubles must stay below about 4 Mi)",
                      need, (size_t)kScratchBytes);
+  // every array must be device (or managed) memory of the current device,
+  // and x must not overlap b: the kernels read b while they write x
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(DM_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+    const void* ptrs[5] = {A, B, C, b, x};
+    const char* names[5] = {"A", "B", "C", "b", "x"};
+    for (int i = 0; i < 5; ++i) {
+      cudaPointerAttributes at;
+      e = cudaPointerGetAttributes(&at, ptrs[i]);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DM_EINVAL, "dm_solve_noalloc: %s is not a CUDA pointer (%s)", names[i], cudaGetErrorString(e));
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+        return set_error(DM_EINVAL, "dm_solve_noalloc: %s must be device memory of the current device %d", names[i],
+                         dev);
+    }
+    const unsigned long long vb = (unsigned long long)(NN * mr) * sizeof(double);
+    const unsigned long long pb = (unsigned long long)(uintptr_t)b, px = (unsigned long long)(uintptr_t)x;
+    if (px < pb + vb && pb < px + vb) return set_error(DM_EINVAL, "dm_solve_noalloc: x must not overlap b");
+  }
   void* base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;

@@ -15,7 +15,7 @@ namespace dm {
 // Kernel classes of the profiler (one per launcher).
 enum KClass {
   K_INV, K_FWD_FACTOR, K_BACK_FACTOR, K_ASSEMBLE_H, K_FWD_SOLVE, K_BACK_SOLVE, K_ASSEMBLE_F,
-  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_NCLASS
+  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_TC_CONVERT, K_NCLASS
 };
 extern const char* const kClassNames[K_NCLASS];
 
@@ -64,6 +64,25 @@ struct SysSpec {
   int levels = 1;  // 1: supplementary system by block Thomas; L > 1: by DM, L-1 levels
   int P2 = 1;      // subsystems of the supplementary system when levels > 1
   int flags = 0;   // DM_PLAN_* (subsystem sizing)
+  int J = 1;       // >= 2: DM inside each of P / J subsystems (nested lengths, P2 = P / J)
+};
+
+// Operand copies of the tensor-core step kernels (dm_tc2.cu) for a float32
+// level with one block size m (m % 8 == 0, m <= 256): TF32 (mode 0, float32
+// values) or split bf16 (mode 1, hi blocks then lo blocks, `cap` blocks
+// apart).  Full copies hold every block of the level; rolling ones one block
+// per subsystem (two for the spikes of the backward sweep).
+struct Tc2Level {
+  bool on = false;
+  int mode = 0;
+  void* A = nullptr;     // A_i row-major (mode 0: the float32 copy A32)
+  void* CT = nullptr;    // C_i transposed
+  void* Acal = nullptr;  // Acal_t row-major (mode 1 only; mode 0 reads the float32 factor)
+  void* G = nullptr;     // G_t row-major, rolling (mode 1 only)
+  void *AcalT = nullptr, *YT = nullptr, *ZLT = nullptr, *ZRT = nullptr;  // transposed, rolling
+  long long capA = 0, capCT = 0, capAcal = 0, capG = 0, capAcalT = 0, capYT = 0, capZLT = 0, capZRT = 0;
+  // tensor maps: left G, A, Acal; right CT, YT, AcalT, ZLT, ZRT
+  alignas(64) unsigned char maps[8][128];
 };
 
 // One level of the recursion: a set of independent systems, each split into
@@ -75,6 +94,7 @@ struct Level {
   float *A32 = nullptr, *B32 = nullptr, *C32 = nullptr;  // float32 copies streamed by the tensor-core sweeps
   alignas(64) unsigned char tmaps[3 * 128];  // TMA tensor maps of G, A32, Acal (TF32 level, one block size)
   bool has_tma = false;
+  Tc2Level tc2;
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0
@@ -87,6 +107,8 @@ struct Level {
   std::vector<int> active_fwd, active_back;  // subsystems still active at each step (prefix counts)
   // per-step launch costs
   std::vector<Cost> c_inv, c_fwd, c_back, c_fwds, c_backs;
+  std::vector<Cost> c_fwdA, c_fwdB;  // the two launches of a forward step of the tensor-core step kernels
+  Cost c_cvt;                         // one operand conversion of the level's blocks
   std::vector<double> fwd_chain_frac;  // share of c_fwd[t] in the type-0 (chain) tiles
   std::vector<int> last_part;           // per system: index in parts of its last subsystem
   Cost c_asm_h, c_asm_f, c_backsub, c_resid, c_axpy, c_sepcopy;
@@ -126,6 +148,7 @@ struct GraphCache {
 
 struct Plan {
   int precision = 0;
+  int device = 0;  // the CUDA device current at dm_plan: every launch of the plan goes there
   Level top;
   cudaStream_t stream = nullptr, own_stream = nullptr;
   double* R = nullptr;    // float64 residual
@@ -167,8 +190,10 @@ struct Plan {
 };
 
 int set_error(int code, const char* fmt, ...);
+extern thread_local std::string g_last_error;  // text of the calling thread's last failure
 void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps);
 void partition_lengths(int N, int P, int m, int r, int flags, std::vector<int>& lens);
+void nested_lengths(int N, int M, int J, std::vector<int>& lens);
 int tuner_seed_p(int N, int m, int r);
 int supp_partitions(int Ms, int P, int r, int m);
 int make_spec(int N, int m, int r, int P, int levels, SysSpec* out);

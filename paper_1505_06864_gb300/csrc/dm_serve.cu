@@ -16,6 +16,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -39,6 +40,7 @@ struct Outcome {
   int status = DM_PENDING;
   double relres = 0.0;
   double t_submit = 0, t_start = 0, t_done = 0;  // steady clock, seconds
+  std::string msg;  // the worker's error text for a failed request
 };
 
 double now_s() {
@@ -76,6 +78,8 @@ class Server {
       return DM_OK;
     }
     *status = it->second.status;
+    // hand the worker's error text to the polling thread's dm_last_error
+    if (it->second.status != DM_OK && !it->second.msg.empty()) set_error(it->second.status, "%s", it->second.msg.c_str());
     if (relres) *relres = it->second.relres;
     if (times) {
       times[0] = it->second.t_submit;
@@ -113,8 +117,9 @@ class Server {
   }
 
   void worker() {
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // one stream per device this worker has served; the plan's device is
+    // made current before any of its work (plans may live on any device)
+    std::unordered_map<int, cudaStream_t> streams;
     for (;;) {
       Request r;
       {
@@ -123,10 +128,25 @@ class Server {
         outcomes_[r.ticket].t_start = now_s();
       }
       Plan& p = r.plan->plan;
-      cudaStream_t keep = p.stream;
-      p.stream = st;
       int rc = DM_OK;
-      if (r.factor) rc = p.factor(r.A, r.B, r.C);
+      cudaStream_t st = nullptr;
+      cudaError_t e = cudaSetDevice(p.device);
+      if (e == cudaSuccess) {
+        auto it = streams.find(p.device);
+        if (it == streams.end()) {
+          e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+          if (e == cudaSuccess) streams[p.device] = st;
+        } else {
+          st = it->second;
+        }
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(DM_ECUDA, "serving worker: device %d: %s", p.device, cudaGetErrorString(e));
+      }
+      cudaStream_t keep = p.stream;
+      if (rc == DM_OK) p.stream = st;
+      if (rc == DM_OK && r.factor) rc = p.factor(r.A, r.B, r.C);
       double rel = 0.0;
       if (rc == DM_OK) {
         std::vector<double> rr(std::max(1, p.top.nsys));
@@ -140,6 +160,7 @@ class Server {
         Outcome& o = outcomes_[r.ticket];
         o.done = true;
         o.status = rc;
+        if (rc != DM_OK) o.msg = g_last_error;
         o.relres = rel;
         o.t_done = now_s();
         busy_.erase(r.plan);

@@ -1018,6 +1018,36 @@ __global__ void __launch_bounds__(kRsThreads, 1) k_residual_sliced(const SysDesc
   tc_teardown(&st, 256, errflag);
 }
 
+// ---------------------------------------------------------------- throughput probe
+// Peak tcgen05 throughput of one SM: one thread issues `iters` x 4
+// back-to-back MMAs (M = 128, N = 256, one 128-byte K atom each: K = 32
+// TF32 / 64 bf16 per 4 instructions) from zeroed shared-memory operands into
+// one float32 accumulator, then commits and waits (bounded).  Launched with
+// one CTA per SM; flops = 2 * 128 * 256 * K per instruction.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_mma_probe(int iters, int* __restrict__ errflag) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ TcState st;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int a_bytes = MT * 128, b_bytes = 256 * 128;
+  for (int i = threadIdx.x; i < (a_bytes + b_bytes) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+  fence_async_shared();
+  tc_setup(&st, 256);
+  if (threadIdx.x == 0) {
+    constexpr uint32_t idesc = make_idesc(MODE == 0 ? 2u : 1u, MT, 256);
+    const uint32_t a = smem_u32(base), b = a + a_bytes;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        mma<MODE>(st.tmem, sw128_desc(a + 32 * j), sw128_desc(b + 32 * j), idesc, (i | j) ? 1u : 0u);
+    }
+    mma_commit(&st.bars[0]);
+    if (!mbar_wait(&st.bars[0], 0)) st.err = 1;
+  }
+  tc_teardown(&st, 256, errflag);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- launchers
@@ -1171,6 +1201,24 @@ void launch_residual_sliced(const SysDesc* sys, int nsys, int nrows, const doubl
   raise_smem_once(tc::k_residual_sliced, tc::RsSmem::total, &set);
   tc::k_residual_sliced<<<nrows, tc::kRsThreads, tc::RsSmem::total, st>>>(sys, nsys, A, B, C, x, b, r, nrm, rowhi,
                                                                           colhi, errflag);
+}
+
+// One CTA per SM (the dynamic shared memory keeps a second one out), `iters`
+// x 4 MMAs each; returns the flops of the launch.
+double launch_mma_probe(int mode, int iters, int* errflag, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int smem = 116 * 1024;
+  if (mode == 0) {
+    cudaFuncSetAttribute(tc::k_mma_probe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    tc::k_mma_probe<0><<<sms, tc::kThreads, smem, st>>>(iters, errflag);
+  } else {
+    cudaFuncSetAttribute(tc::k_mma_probe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    tc::k_mma_probe<1><<<sms, tc::kThreads, smem, st>>>(iters, errflag);
+  }
+  const double k_per_instr = mode == 0 ? 8.0 : 16.0;
+  return 2.0 * tc::MT * 256.0 * k_per_instr * 4.0 * iters * sms;
 }
 
 int tc_smem_bytes(int mode) { return mode == 0 ? tc::Smem<0>::total : tc::Smem<1>::total; }

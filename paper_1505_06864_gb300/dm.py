@@ -41,7 +41,7 @@ class dm_plan_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("last_relres", ctypes.c_double),
                 ("last_correction", ctypes.c_double), ("factor_flops", ctypes.c_double),
                 ("solve_flops", ctypes.c_double), ("residual_mode", ctypes.c_int),
-                ("residual_tc_systems", ctypes.c_int)]
+                ("residual_tc_systems", ctypes.c_int), ("J", ctypes.c_int)]
 
 
 class dm_profile_entry(ctypes.Structure):
@@ -66,6 +66,7 @@ def lib():
                                   ctypes.POINTER(I), I]),
             "dm_plan_tune": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "dm_plan_ex": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I]),
+            "dm_plan_inside": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I]),
             "dm_partition_sizes": (I, [I, I, I, I, I, ctypes.POINTER(I)]),
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
@@ -86,6 +87,7 @@ def lib():
             "dm_poll": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_poll_times": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
             "dm_serve_slots": (I, [I]),
+            "dm_peak_probe": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "dm_destroy": (V, [P]),
             "dm_last_error": (ctypes.c_char_p, []),
         }
@@ -141,6 +143,16 @@ def dm_plan_ex(N, m, nrhs, P=0, levels=0, precision=DM_FP64, flags=0):
     h = ctypes.c_void_p()
     _check(lib().dm_plan_ex(ctypes.byref(h), int(N), int(m), int(nrhs), int(P), int(levels), int(precision),
                             int(flags)))
+    return h
+
+
+def dm_plan_inside(N, m, nrhs, M, J, outer_levels=1, precision=DM_FP64):
+    """DM with M subsystems, each solved by DM with J sub-subsystems (Section 4.2.2)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = ctypes.c_void_p()
+    _check(lib().dm_plan_inside(ctypes.byref(h), int(N), int(m), int(nrhs), int(M), int(J), int(outer_levels),
+                                int(precision)))
     return h
 
 
@@ -262,7 +274,11 @@ def dm_launch_count(plan) -> int:
 
 def dm_solve_noalloc(N, m, nrhs, P, A, B, C, b, x, stream=None):
     """Factor + solve one system in the library's static device workspace
-    (no allocation).  All arrays must be CUDA tensors; x must not alias b."""
+    (no allocation).  All arrays must be CUDA tensors of the current device;
+    x must not overlap b.  Host arrays are refused here, before the call."""
+    for name, a in (("A", A), ("B", B), ("C", C), ("b", b), ("x", x)):
+        if not (hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)):
+            raise DMError(DM_EINVAL, f"dm_solve_noalloc: {name} must be a CUDA tensor, not {type(a).__name__}")
     h = getattr(stream, "cuda_stream", stream)
     return _check(lib().dm_solve_noalloc(int(N), int(m), int(nrhs), int(P), _ptr(A), _ptr(B), _ptr(C),
                                          _ptr(b), _ptr(x, True), ctypes.c_void_p(h) if h else None))
@@ -300,6 +316,16 @@ def dm_poll_times(ticket):
 
 def dm_serve_slots(slots):
     return _check(lib().dm_serve_slots(int(slots)))
+
+
+DM_PROBE_FP64, DM_PROBE_FP32, DM_PROBE_TF32, DM_PROBE_BF16 = 0, 1, 2, 3
+
+
+def dm_peak_probe(kind, repeat=3):
+    """(TFLOP/s, ms) of the best of `repeat` timed launches of the probe kernel."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().dm_peak_probe(int(kind), int(repeat), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def dm_destroy(plan):

@@ -81,3 +81,24 @@ def test_partition_sizes_match_oracle(dm):
         assert dm.dm_partition_sizes(N, m, r, P) == o.partition_plan(N, P)[1]
         assert dm.dm_partition_sizes(N, m, r, P, dm.DM_PLAN_EQUAL_TIME) == \
             o.partition_lengths_equal_time(N, P, m, r)
+
+
+def test_noalloc_refuses_host_arrays_before_the_call(dm):
+    """dm_solve_noalloc takes device memory only: numpy arrays are refused by
+    the binding with DM_EINVAL and nothing reaches the library."""
+    import numpy as np
+    A = np.zeros((4, 2, 2))
+    v = np.zeros((4, 2, 1))
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_solve_noalloc(4, 2, 1, 1, A, A, A, v, v.copy())
+    assert e.value.code == dm.DM_EINVAL and "CUDA tensor" in str(e.value)
+
+
+def test_dm_inside_arguments_rejected_without_gpu(dm):
+    """dm_plan_inside validates M, J and the subsystem lengths before it
+    touches the device."""
+    for args in [(20, 4, 1, 4, 5, 1), (20, 4, 1, 2, 1, 1), (20, 4, 1, 0, 2, 1), (20, 4, 1, 2, 2, 3),
+                 (5, 4, 1, 4, 2, 1)]:
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_plan_inside(*args)
+        assert e.value.code == dm.DM_EINVAL, args

@@ -221,6 +221,65 @@ def test_batch_uneven_systems(dm, prec, tol):
     assert max(rel) < 1e-13
 
 
+_B4 = {}
+
+
+def _config4_batch():
+    """Uneven systems drawn like the batching workload (N ~ U{32..2048},
+    m in {32, 64, 96, 128}, nrhs ~ U{1..16}), the four corners of that
+    distribution forced in, the total kept small enough for the oracle."""
+    if "b" not in _B4:
+        shapes = [(2048, 128, 3), (1400, 96, 16), (700, 64, 1), (1200, 32, 8), (33, 128, 2), (32, 32, 16)]
+        shapes += w.batch_shapes(8, 44, n_hi=600)
+        systems, A, B, C, b = _batch(shapes, 80)
+        ref = []
+        for s, (N, m, r) in zip(systems, shapes):
+            P, lv, P2 = dm_tune_host(N, m, r)
+            ref.append(o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=P2 if P2 > 1 else None))
+        _B4["b"] = (shapes, systems, A, B, C, b, ref)
+    return _B4["b"]
+
+
+def dm_tune_host(N, m, r):
+    from paper_1505_06864_gb300 import dm as D
+    return D.dm_plan_tune(N, m, r)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_batch_mixed_precision_config4_shapes(dm, prec):
+    """The batching workload's launch shape on the tensor cores: m in
+    {32, 64, 96, 128} mixed in one grid (shared memory sized per launch), N up
+    to 2048, 1..16 right-hand sides -- refined x against the oracle per system,
+    and the first pass (no refinement) within its product-error bound."""
+    shapes, systems, A, B, C, b, ref = _config4_batch()
+    Ns, ms, rs = zip(*shapes)
+    out = {}
+    for iters in (30, 1):
+        plan = dm.dm_plan_batch(Ns, ms, rs, prec)
+        try:
+            dm.dm_set_refinement(plan, 1e-12, iters)
+            dm.dm_factor(plan, A, B, C)
+            x = np.zeros_like(b)
+            rel = dm.dm_solve(plan, b, x, count=len(shapes), allow_notconv=(iters == 1))
+            info = dm.dm_plan_query(plan)
+        finally:
+            dm.dm_destroy(plan)
+        out[iters] = (x, rel, info)
+    x, rel, info = out[30]
+    assert max(rel) < 1e-13 and info["last_iters"] <= {"tf32": 6, "bf16x3": 4}[prec]
+    x1 = out[1][0]
+    u = {"tf32": 2.0 ** -10, "bf16x3": 2.0 ** -16}[prec]
+    off = 0
+    for s, (N, m, r), xo in zip(systems, shapes, ref):
+        n = N * m * r
+        check(x[off:off + n].reshape(N, m, r), xo, TOLMIX)
+        d = np.abs(s.B.diagonal(axis1=1, axis2=2))
+        rs_ = np.abs(s.A).sum(2) + np.abs(s.B).sum(2) + np.abs(s.C).sum(2)
+        kappa = float(rs_.max() / (2 * d - rs_).min())
+        check(x1[off:off + n].reshape(N, m, r), xo, 16.0 * kappa * u)
+        off += n
+
+
 def test_batch_same_as_alone(dm):
     """A system's x from a batch equals (within tolerance) its x solved alone."""
     shapes = [(120, 16, 2), (37, 24, 1), (200, 8, 3)]
@@ -384,3 +443,29 @@ def test_solve_sweep_and_per_step_kernels(dm, monkeypatch, N, m, r, P, levels, p
         out[flag] = x
     monkeypatch.delenv("DM_SOLVE_SWEEP")
     check(out["1"], out["0"], tol)
+
+
+@pytest.mark.parametrize("N,m,r,M,J,outer,prec", [(200, 8, 2, 4, 3, 1, "fp64"), (130, 24, 1, 3, 4, 1, "fp64"),
+                                                  (301, 16, 3, 9, 3, 2, "fp64"), (512, 128, 1, 8, 4, 1, "fp64"),
+                                                  (41, 6, 1, 1, 4, 1, "fp64"), (150, 32, 2, 3, 3, 1, "bf16x3"),
+                                                  (150, 32, 2, 3, 3, 1, "tf32"), (97, 40, 2, 4, 2, 1, "fp32")])
+def test_dm_inside_subsystems(dm, N, m, r, M, J, outer, prec):
+    """DM inside the subsystems (Section 4.2.2): M subsystems, each split into
+    J sub-subsystems, the outer supplementary system by block Thomas or by DM
+    (outer = 2, both levels recursive) -- against the oracle's construction in
+    the paper's order (every subsystem's Eq. e231 solved by DM)."""
+    s = w.dominant_system(N, m, r, 1000 + N + m)
+    plan = dm.dm_plan_inside(N, m, r, M, J, outer, prec)
+    try:
+        q = dm.dm_plan_query(plan)
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        x = np.zeros_like(s.b)
+        rel = dm.dm_solve(plan, s.b, x)
+    finally:
+        dm.dm_destroy(plan)
+    assert q["J"] == J and q["P"] == M * J and (q["P2"] == M or M == 1)
+    _, Lk, _ = o.partition_plan(N, M)
+    assert q["max_rows"] == max(Li for L in Lk for Li in o.partition_plan(L, J)[1])
+    xo = o.dm(s.A, s.B, s.C, s.b, M, levels=outer, J=J)
+    check(x, xo, TOL64 if prec == "fp64" else TOLMIX)
+    assert rel < 1e-13

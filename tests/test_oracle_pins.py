@@ -313,6 +313,28 @@ def test_dm_both_levels_serial_count_dmrec4():
     assert serial == o.mo_dm_rec4(N, M, J, msub, n, l)
 
 
+@pytest.mark.parametrize("N,m,l,M,J,outer,seed", [(60, 3, 2, 3, 3, 1, 18), (101, 2, 1, 4, 4, 1, 19),
+                                                  (130, 3, 2, 7, 3, 2, 20), (41, 2, 3, 1, 4, 1, 21)])
+def test_dm_inside_equals_aligned_form(N, m, l, M, J, outer, seed):
+    """DM inside the subsystems (the paper's construction, Section 4.2.2) and
+    the form the library executes -- DM with the M J sub-subsystems whose
+    supplementary system is split into M parts at the outer separators, so
+    that part k is subsystem k's inner supplementary system -- give the same
+    x; the executed form never forms the subsystem spikes over all rows and
+    so counts fewer multiplicative operations."""
+    s = w.dominant_system(N, m, l, seed)
+    c1, c2 = o.OpCounter(), o.OpCounter()
+    x1 = o.dm(s.A, s.B, s.C, s.b, M, levels=outer, J=J, ctr=c1)
+    _, Lk, _ = o.partition_plan(N, M)
+    nested = [Li for L in Lk for Li in o.partition_plan(L, J)[1]]
+    x2 = o.dm(s.A, s.B, s.C, s.b, M * J, levels=outer + 1, P2=M, lengths=nested, ctr=c2)
+    assert o.rel_err(x1, x2) < 1e-13
+    # the supplementary partition of the executed form falls on the outer separators
+    assert o.partition_plan(M * J - 1, M)[1] == [J - 1] * M
+    # (with M = 1 there are no subsystem spikes and the two forms coincide)
+    assert c2.total() < c1.total() if M > 1 else c2.total() == c1.total()
+
+
 # ---------------------------------------------------------------- Section 5.1 speedups from counted runs
 def _serial_count(ctr, ks):
     return sum(ctr.total(f"{st}/{k}") for k in ks for st in ("solve", "wing", "back")) + ctr.total("supp")

@@ -75,3 +75,23 @@ def test_no_alloc_single_subsystem_and_limits(dm):
     with pytest.raises(dm.DMError) as e:
         dm.dm_solve_noalloc(70, 128, 1, 4, big, big, big, v, v.clone())
     assert e.value.code == dm.DM_EINVAL and "static" in str(e.value)
+
+
+def test_no_alloc_rejects_host_memory_and_overlap(dm):
+    """The library itself checks every pointer before it launches anything:
+    host memory (given through the raw C entry point, past the binding's own
+    check) and an x that overlaps b are DM_EINVAL."""
+    import ctypes
+    import torch
+    s = w.dominant_system(9, 8, 2, 3)
+    T = lambda a: torch.from_numpy(a).cuda()
+    A, B, C, b = T(s.A), T(s.B), T(s.C), T(s.b)
+    L = dm.lib()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    host = np.ascontiguousarray(s.b)
+    rc = L.dm_solve_noalloc(9, 8, 2, 1, P(A), P(B), P(C), ctypes.c_void_p(host.ctypes.data), P(b.clone()), None)
+    assert rc == dm.DM_EINVAL and "device memory" in dm.dm_last_error()
+    rc = L.dm_solve_noalloc(9, 8, 2, 1, P(A), P(B), P(C), P(b), P(b), None)
+    assert rc == dm.DM_EINVAL and "overlap" in dm.dm_last_error()
+    # the refused calls left nothing behind: the next call is still exact
+    close(no_alloc(dm, s, 1), allocating(dm, s, 1))
