@@ -52,17 +52,23 @@ def measured_peaks():
         return {}
 
 
-def probe_peaks(dm):
-    """This library's own probes (dm_peak_probe): float64 and float32 FMA
-    loops, tcgen05 TF32 and bf16 MMA loops; best of 3 timed launches each."""
+def probe_peaks(dm, dev=0):
+    """This library's own probes (dm_peak_probe): float64 and float32
+    register-tile FMA loops, tcgen05 TF32 and bf16 MMA loops; best of 5
+    timed launches each, with the SM clock sampled while each runs."""
     out = {}
     for name, kind in (("fp64", dm.DM_PROBE_FP64), ("fp32", dm.DM_PROBE_FP32), ("tf32", dm.DM_PROBE_TF32),
                        ("bf16", dm.DM_PROBE_BF16)):
+        clk = Clocks(dev)
+        clk.start()
         try:
-            tf, ms = dm.dm_peak_probe(kind, 3)
+            tf, ms = dm.dm_peak_probe(kind, 5)
             out[name] = {"tflops": tf, "ms": ms}
         except dm.DMError as e:
             out[name] = {"error": str(e)}
+        c = clk.stop()
+        out[name]["sm_mhz"] = c.get("sm_mhz")
+        out[name]["reasons"] = c.get("reasons")
     return out
 
 
@@ -222,7 +228,7 @@ def main():
         return dm.dm_solve(plan, b, x, allow_notconv=mixed)
 
     # measured arithmetic peaks (before any timing; ~2 s)
-    peaks = probe_peaks(dm) if rank == 0 or ws == 1 else {}
+    peaks = probe_peaks(dm, local)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -272,14 +278,19 @@ def main():
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     kname, kd = top
     achieved = kd["flops"] / (kd["ms"] / 1e3) / 1e12
-    fp64_peak = peaks.get("fp64", {}).get("tflops")
-    if fp64_peak:
-        peak, src = fp64_peak, "measured: dm_peak_probe float64 FMA loop on this GPU (best of 3 launches)"
-    else:
-        peak, src = FP64_NOMINAL_TFLOPS, "GB300 nominal float64 rate (probe unavailable)"
+    # float64 is bound by the FP64 pipe (plain ALU arithmetic): peak = SMs x 2
+    # DFMA/clk (4 flop/clk) x the SM clock sampled during the timed region
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = sms * 4.0 * mhz * 1e6 / 1e12
+    src = (f"derived: {sms} SMs x 4 float64 flop/clk x {mhz:.0f} MHz (median SM clock sampled in the timed "
+           f"region); the dm_peak_probe register-tile FMA loop reaches "
+           f"{peaks.get('fp64', {}).get('tflops', float('nan')):.3f} TFLOP/s at "
+           f"{peaks.get('fp64', {}).get('sm_mhz') or float('nan'):.0f} MHz")
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": read_traffic(kname) if not mixed else None,
             "peak_source": src, "nominal_peak": FP64_NOMINAL_TFLOPS,
+            "probe_peak": peaks.get("fp64", {}).get("tflops"),
             "launches": kd["launches"], "avg_launch_ms": kd["ms"] / kd["launches"],
             "share_of_step": kd["ms"] / sum(v["ms"] for v in prof.values()),
             "timing": "CUDA events around each launch in a second run of the same steps "

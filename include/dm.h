@@ -133,6 +133,24 @@ int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int pr
  * too short for J. */
 int dm_plan_inside(dm_plan_t* out, int N, int m, int nrhs, int M, int J, int outer_levels, int precision);
 
+/* Complex systems (the paper's application, Section 7, has complex
+ * boundary conditions).  Arrays are complex128 as interleaved (real,
+ * imaginary) double pairs with the real layouts: A, B, C [N][m][m], b, x
+ * [N][m][nrhs]; host or device pointers as for the real calls.  The plan
+ * solves the real embedding of the system: every complex block X + iY becomes
+ * the real 2m x 2m block [[X, -Y], [Y, X]] and every right-hand-side block
+ * u + iv the 2m x nrhs block [u; v], a real block-tridiagonal system with the
+ * same N, P and recursion, on which every precision and kernel of the real
+ * path runs unchanged (twice the multiply-adds of complex arithmetic).
+ * Limits: m <= 256 (m <= 128 for DM_TF32 / DM_BF16X3).  The plan holds the
+ * embedded blocks (3 N (2m)^2 doubles) and a staging buffer for host arrays.
+ * dm_solve_complex returns DM_ENOTCONV as dm_solve does; relres_out is the
+ * relative residual of the embedded system, equal to that of the complex one.
+ * dm_factor / dm_solve on such a plan take the embedded real arrays. */
+int dm_plan_complex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision);
+int dm_factor_complex(dm_plan_t plan, const double* A, const double* B, const double* C);
+int dm_solve_complex(dm_plan_t plan, const double* b, double* x, double* relres_out);
+
 /* Subsystem sizes (rows, in order) a plan with these arguments uses; host
  * only.  `lengths` receives P values (P = the effective P: 0 = the tuner's). */
 int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths);

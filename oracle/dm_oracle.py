@@ -377,6 +377,7 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
     ctr = ctr or _NoCount()
     A, B, C, F = np.asarray(A), np.asarray(B), np.asarray(C), np.asarray(F)
     N, m, l = B.shape[0], B.shape[1], F.shape[2]
+    dt = np.result_type(A, B, C, F, np.float64)   # float64, or complex128 for complex systems
     if P == 1 and J is not None and J >= 2:
         # the whole system is the one subsystem: Eq. (e231) without spikes, by DM
         with ctr.stage("solve/0"):
@@ -423,10 +424,10 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
     # and separator k's A (against its last row).  The result is the
     # block-tridiagonal supplementary system of Eq. (e232) on h_0..h_{P-2}.
     Ms = P - 1
-    HA = np.zeros((Ms, m, m))
-    HB = np.zeros((Ms, m, m))
-    HC = np.zeros((Ms, m, m))
-    fh = np.zeros((Ms, m, l))
+    HA = np.zeros((Ms, m, m), dtype=dt)
+    HB = np.zeros((Ms, m, m), dtype=dt)
+    HC = np.zeros((Ms, m, m), dtype=dt)
+    fh = np.zeros((Ms, m, l), dtype=dt)
     for j in range(Ms):
         q = seps[j]
         HB[j] = B[q]
@@ -458,7 +459,7 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
 
     # Eq. (endSolution): s^k = z^k - Z^k_(left) h^{k-1} - Z^k_(right) h^k,
     # with h^0 = h^M = 0 (here: no left term for k = 0, no right term for k = P-1).
-    X = np.zeros((N, m, l))
+    X = np.zeros((N, m, l), dtype=dt)
     for k in range(P):
         s, L = starts[k], lengths[k]
         with ctr.stage(f"back/{k}"):
@@ -483,7 +484,7 @@ def dm(A, B, C, F, P, levels=1, P2=None, ctr=None, return_parts=False, lengths=N
 def dense_from_blocks(A, B, C):
     """The (Nm) x (Nm) matrix T of Eq. (1)."""
     N, m = B.shape[0], B.shape[1]
-    T = np.zeros((N * m, N * m))
+    T = np.zeros((N * m, N * m), dtype=np.result_type(A, B, C, np.float64))
     for i in range(N):
         T[i * m:(i + 1) * m, i * m:(i + 1) * m] = B[i]
         if i > 0:
@@ -495,9 +496,11 @@ def dense_from_blocks(A, B, C):
 
 def dense_ge(T, b):
     """Textbook Gaussian elimination with partial pivoting and back
-    substitution on a dense n x n matrix (n small); b is n x l."""
-    T = np.array(T, dtype=np.float64)
-    b = np.array(b, dtype=np.float64)
+    substitution on a dense n x n matrix (n small); b is n x l.  Real or
+    complex (pivot by largest modulus)."""
+    dt = np.result_type(T, b, np.float64)
+    T = np.array(T, dtype=dt)
+    b = np.array(b, dtype=dt)
     n = T.shape[0]
     for k in range(n):
         p = k + int(np.argmax(np.abs(T[k:, k])))
@@ -517,7 +520,10 @@ def dense_ge(T, b):
 
 
 def residual(A, B, C, x, b, dtype=np.float64):
-    """r = b - T x evaluated in ``dtype`` (float64 or np.longdouble)."""
+    """r = b - T x evaluated in ``dtype`` (float64 or np.longdouble; for
+    complex systems the complex type of that precision)."""
+    if any(np.iscomplexobj(v) for v in (A, B, C, x, b)):
+        dtype = np.clongdouble if dtype == np.longdouble else np.complex128
     A, B, C, x, b = (np.asarray(v, dtype=dtype) for v in (A, B, C, x, b))
     r = b - np.matmul(B, x)
     r[1:] -= np.matmul(A[1:], x[:-1])
@@ -527,8 +533,9 @@ def residual(A, B, C, x, b, dtype=np.float64):
 
 def rel_err(x, xref):
     """max over right-hand-side columns of ||x - xref||_2 / ||xref||_2."""
-    x = np.asarray(x, dtype=np.float64).reshape(-1, x.shape[-1])
-    xref = np.asarray(xref, dtype=np.float64).reshape(-1, xref.shape[-1])
+    dt = np.result_type(x, xref, np.float64)
+    x = np.asarray(x, dtype=dt).reshape(-1, x.shape[-1])
+    xref = np.asarray(xref, dtype=dt).reshape(-1, xref.shape[-1])
     num = np.linalg.norm(x - xref, axis=0)
     den = np.linalg.norm(xref, axis=0)
     den[den == 0] = 1.0
@@ -538,15 +545,17 @@ def rel_err(x, xref):
 def refine_truth(A, B, C, b, x0=None, iters=6):
     """Near-exact solution of T x = b: float64 Thomas solves corrected with
     residuals evaluated in extended precision (np.longdouble)."""
-    x = thomas(A, B, C, b) if x0 is None else np.array(x0, dtype=np.float64)
-    xl = x.astype(np.longdouble)
+    cplx = any(np.iscomplexobj(v) for v in (A, B, C, b))
+    lo, hi = (np.complex128, np.clongdouble) if cplx else (np.float64, np.longdouble)
+    x = thomas(A, B, C, b) if x0 is None else np.array(x0, dtype=lo)
+    xl = x.astype(hi)
     for _ in range(iters):
         r = residual(A, B, C, xl, b, dtype=np.longdouble)
-        d = thomas(A, B, C, r.astype(np.float64))
-        xl = xl + d.astype(np.longdouble)
+        d = thomas(A, B, C, r.astype(lo))
+        xl = xl + d.astype(hi)
         if np.max(np.abs(d)) <= 1e-18 * max(1.0, float(np.max(np.abs(xl)))):
             break
-    return xl.astype(np.float64)
+    return xl.astype(lo)
 
 
 # --------------------------------------------------------------------------

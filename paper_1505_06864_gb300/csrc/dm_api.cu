@@ -749,7 +749,7 @@ void level_flops(const Level& L, double* ffac, double* fsol) {
 }
 
 // ---------------------------------------------------------------------------
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
@@ -866,6 +866,7 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
 }
 
 Plan::~Plan() {
+  for (void* p : cbuf) cudaFree(p);
   if (R) cudaFree(R);
   if (Dx) cudaFree(Dx);
   if (nrm) cudaFree(nrm);

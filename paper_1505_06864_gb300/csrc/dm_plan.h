@@ -170,6 +170,14 @@ struct Plan {
   bool overlap = false;  // left-spike tiles on the side stream
   const double *bA = nullptr, *bB = nullptr, *bC = nullptr;
   int resid_mode = 0;  // DM_RESIDUAL_FP64 or DM_RESIDUAL_SLICED
+  // complex systems (dm_plan_complex): the real embedding of block size 2m
+  bool cplx = false;
+  int cm = 0;                             // the complex block size m
+  double *embA = nullptr, *embB = nullptr, *embC = nullptr;  // [N][2m][2m] real blocks
+  double *cstage = nullptr;               // complex staging for host inputs / outputs
+  double *bR = nullptr, *xR = nullptr;    // [N][2m][nrhs] real right-hand side / solution
+  size_t cstage_bytes = 0;
+  std::vector<void*> cbuf;                // the buffers above (freed with the plan)
   unsigned* rowhi = nullptr;  // per point row of the top level: largest high word of [A_i B_i C_i]'s row
   unsigned* colhi = nullptr;  // per block row x 16: largest high word of each column of x_i
   void row_scales();          // rowhi from the resident blocks (after each factorisation)
@@ -202,6 +210,7 @@ void solve_level(Level& L, const double* F, double* X, cudaStream_t st, Prof& pf
 void level_flops(const Level& L, double* ffac, double* fsol);
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
+bool is_device_ptr(const void* p);
 
 void serve_drain(struct dm_plan_s* plan);
 bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels);

@@ -85,31 +85,47 @@ __device__ __forceinline__ void put(void* base, long long cap, long long e, floa
   }
 }
 
-// Sixteen consecutive values of one row into a row-major operand copy.
+// Four consecutive values of one row into a row-major operand copy (the
+// element offset is a multiple of 4).
 template <int MODE>
-__device__ __forceinline__ void put16(void* base, long long cap, long long e, const float (&v)[16]) {
+__device__ __forceinline__ void put4(void* base, long long cap, long long e, const float (&v)[4]) {
   if (MODE == 0) {
-    float4* d = reinterpret_cast<float4*>(static_cast<float*>(base) + e);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      d[q] = make_float4(round_tf32(v[4 * q]), round_tf32(v[4 * q + 1]), round_tf32(v[4 * q + 2]),
-                         round_tf32(v[4 * q + 3]));
+    *reinterpret_cast<float4*>(static_cast<float*>(base) + e) =
+        make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
   } else {
-    uint32_t hi[8], lo[8];
+    uint32_t hi[2], lo[2];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 2; ++q) {
       const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
       const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
       const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
       hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
       lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
     }
-    uint4* dh = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + e);
-    uint4* dl = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + e + cap);
-    dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-    dl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    dl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(base) + e) = make_uint2(hi[0], hi[1]);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(base) + e + cap) = make_uint2(lo[0], lo[1]);
+  }
+}
+
+// 16 bytes of consecutive elements (4 float32 or 8 bf16 hi + 8 bf16 lo) at
+// element offset e, a multiple of 4 (float32) or 8 (bf16).
+template <int MODE>
+__device__ __forceinline__ void putT(void* base, long long cap, long long e, const float (&v)[MODE == 0 ? 4 : 8]) {
+  if (MODE == 0) {
+    *reinterpret_cast<float4*>(static_cast<float*>(base) + e) =
+        make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
+  } else {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+      hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + e) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + e + cap) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -185,7 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_tc_step(const PartDesc* __restrict
   const int nslab = (m + KS - 1) / KS;
   const uint32_t tx = (uint32_t)(Cf::parts * (MT + ntile) * Cf::row);
 
-  if (threadIdx.x == 0) {
+  // Lane 0 of warp 0 produces, lane 0 of warp 1 issues the MMAs; the other
+  // lanes of those warps park at __syncwarp (no spinning beside them), warps
+  // 2 and 3 wait for the accumulator.
+  if (warp == 0 && lane == 0) {
     // producer: K slab s into stage s % 2 once the MMAs of slab s - 2 are done
     uint32_t ph[kStages] = {0u, 0u};
     int s = 0;
@@ -206,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_step(const PartDesc* __restrict
       if (MODE == 1) tma_load_3d(sb + Cf::parts * Cf::lpart + Cf::rpart, mr, s * KS, 0, zr + lo_r, &full[st]);
     }
     nissued = s;
-  } else if (threadIdx.x == 32) {
+  } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t idesc = make_idesc(Cf::fmt, MT, ntile);
     int s = 0;
@@ -235,77 +254,118 @@ __global__ void __launch_bounds__(kThreads) k_tc_step(const PartDesc* __restrict
     ncons = s;
     mma_commit(&accb);
   }
+  if (warp < 2) __syncwarp();
   bool ok = mbar_wait(&accb, 0u);
   tc_fence_after();
   ok = __syncthreads_and(ok) && !err;
 
   if (ok) {
-    const int row = tm * MT + warp * 32 + lane;
+    // Epilogue in chunks of 32 columns.  Each thread holds one row of the
+    // chunk (tensor-memory lane = row); transposed copies are written straight
+    // from there (consecutive lanes = consecutive addresses), row-major
+    // results go through a per-warp 32 x 33 tile in the (now idle) pipeline
+    // buffers so that a warp writes 128 contiguous bytes of one row at a time.
+    float* stg = reinterpret_cast<float*>(base) + warp * (32 * 33);
+    const int rbase = tm * MT + warp * 32, row = rbase + lane;
     const bool rok = row < m;
     const long long o = p.blk + (long long)t * mm;
-    const long long er = (long long)row * m;
-    for (int c0 = 0; c0 < ntile; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (!rok || c0 >= m) continue;
-      const int nc = min(16, m - c0);
-      if (KIND == 0 && j == 0 && t < p.L - 1) {
-        // Acal_t: float32 factor, row-major copy (left operand of the
-        // backward sweep), transposed copy (right operand of launch B)
-        float* d = out.Acal + o + er + c0;
-        if (nc == 16) {
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // which outputs this tile has
+    const bool acal = KIND == 0 && j == 0 && t < p.L - 1;          // Acal_t (+ row-major copy + transposed)
+    const bool spike0 = KIND == 0 && !acal;                        // ZR seed (j = 0) or Bcal_t (j = 1)
+    void* tr = nullptr;                                            // transposed copy
+    long long tcap = 0, tz = 0;
+    float sgn = 1.f;
+    if (acal) tr = out.acalT, tcap = out.cap_acalT, tz = pidx;
+    else if (spike0) tr = j == 0 ? out.zrT : out.zlT, tcap = j == 0 ? out.cap_zrT : out.cap_zlT, tz = 2 * pidx + (t & 1);
+    else if (KIND == 1 && j == 1) tr = out.yT, tcap = out.cap_yT, tz = pidx, sgn = -1.f;
+    else if (KIND == 2) tr = j == 0 ? out.zlT : out.zrT, tcap = j == 0 ? out.cap_zlT : out.cap_zrT,
+                        tz = 2 * pidx + (t & 1), sgn = -1.f;
+    float* rm = nullptr;  // row-major float32 result (KIND 1, j = 0 writes D_{t+1} into G instead)
+    if (acal) rm = out.Acal;
+    else if (spike0) rm = j == 0 ? out.ZR : out.ZL;
+    else if (KIND == 2) rm = j == 0 ? out.ZL : out.ZR;
+    const bool rmw = KIND == 2 && j == 0;  // ZL_t -= ...: the transposed copy needs the updated value
+    for (int c0 = 0; c0 < ntile; c0 += 32) {
+      {
+        float v[32];
+        float h[16];
+        tmem_ld16(tl + (uint32_t)c0, h);
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            reinterpret_cast<float4*>(d)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          if (MODE == 1) put16<MODE>(out.acal_l, out.cap_acal_l * mm, (b0 + t) * mm + er + c0, v);
+        for (int i = 0; i < 16; ++i) v[i] = h[i];
+        if (c0 + 16 < ntile) {
+          tmem_ld16(tl + (uint32_t)(c0 + 16), h);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[16 + i] = h[i];
         } else {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (i < nc) {
-              d[i] = v[i];
-              if (MODE == 1) put<MODE>(out.acal_l, out.cap_acal_l * mm, (b0 + t) * mm + er + c0 + i, v[i]);
-            }
+          for (int i = 0; i < 16; ++i) v[16 + i] = 0.f;
+        }
+        if (c0 >= m) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
+      }
+      __syncwarp();
+      // row-major results: lane = (row r0 + 4 i, columns cq .. cq + 3), float4
+      // accesses (m % 8 == 0: a group of four columns is all inside or all out)
+      const bool dnext = KIND == 1 && j == 0;  // D_{t+1} = B_{t+1} - A_{t+1} Acal_t into G
+      if (rm || dnext) {
+        const int r0 = lane >> 3, cq = (lane & 7) * 4, cc = c0 + cq;
+        float4 in[8];
+        if (dnext || rmw) {
+          const float* src = KIND == 1 ? out.B32 + mm : rm;  // B_{t+1} / the forward ZL_t
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int rr = rbase + r0 + 4 * i;
+            in[i] = (rr < m && cc < m) ? *reinterpret_cast<const float4*>(src + o + (long long)rr * m + cc)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nc) put<MODE>(out.acalT, out.cap_acalT * mm, pidx * mm + (long long)(c0 + i) * m + row, v[i]);
-      } else if (KIND == 0) {
-        // j == 0 at the last row: ZR = G C (right spike seed); j == 1: Bcal_t
-        float* f = (j == 0 ? out.ZR : out.ZL) + o + er + c0;
-        void* tr = j == 0 ? out.zrT : out.zlT;
-        const long long cap = (j == 0 ? out.cap_zrT : out.cap_zlT) * mm;
-        const long long zt = (long long)(2 * pidx + (t & 1)) * mm;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nc) {
-            f[i] = v[i];
-            put<MODE>(tr, cap, zt + (long long)(c0 + i) * m + row, v[i]);
+        for (int i = 0; i < 8; ++i) {
+          const int r = r0 + 4 * i, rr = rbase + r;
+          if (rr >= m || cc >= m) continue;
+          float* sp = stg + r * 33 + cq;
+          float4 a = make_float4(sp[0], sp[1], sp[2], sp[3]);
+          const long long e = (long long)rr * m + cc;
+          if (dnext) {
+            *reinterpret_cast<float4*>(out.G + o + mm + e) = make_float4(in[i].x - a.x, in[i].y - a.y, in[i].z - a.z,
+                                                                        in[i].w - a.w);
+          } else if (rmw) {
+            a = make_float4(in[i].x - a.x, in[i].y - a.y, in[i].z - a.z, in[i].w - a.w);
+            *reinterpret_cast<float4*>(rm + o + e) = a;
+            sp[0] = a.x, sp[1] = a.y, sp[2] = a.z, sp[3] = a.w;
+          } else {
+            if (KIND == 2) a = make_float4(-a.x, -a.y, -a.z, -a.w);
+            *reinterpret_cast<float4*>(rm + o + e) = a;
+            if (acal && MODE == 1) {
+              const float f4[4] = {a.x, a.y, a.z, a.w};
+              put4<MODE>(out.acal_l, out.cap_acal_l * mm, (long long)(b0 + t) * mm + e, f4);
+            }
           }
-      } else if (KIND == 1 && j == 0) {
-        // D_{t+1} = B_{t+1} - A_{t+1} Acal_t, inverted in place next step
-        const long long e = o + mm + er + c0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nc) out.G[e + i] = out.B32[e + i] - v[i];
-      } else if (KIND == 1) {
-        // Y_{t+1} = -A_{t+1} Bcal_t (transposed: right operand of launch A)
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nc) put<MODE>(out.yT, out.cap_yT * mm, pidx * mm + (long long)(c0 + i) * m + row, -v[i]);
-      } else {
-        // backward: ZL_t -= Acal_t ZL_{t+1}  /  ZR_t = -Acal_t ZR_{t+1}
-        float* f = (j == 0 ? out.ZL : out.ZR) + o + er + c0;
-        void* tr = j == 0 ? out.zlT : out.zrT;
-        const long long cap = (j == 0 ? out.cap_zlT : out.cap_zrT) * mm;
-        const long long zt = (long long)(2 * pidx + (t & 1)) * mm;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nc) {
-            const float nv = (j == 0 ? f[i] : 0.f) - v[i];
-            f[i] = nv;
-            put<MODE>(tr, cap, zt + (long long)(c0 + i) * m + row, nv);
-          }
+        }
+        __syncwarp();
       }
+      // transposed copies: lane = (column, a group of rows), 16-byte stores of
+      // consecutive rows of one column (8 bf16 / 4 float32)
+      if (tr) {
+        constexpr int RG = MODE == 0 ? 4 : 8;      // rows per lane
+        constexpr int LPC = 32 / RG;               // lanes per column
+        constexpr int CPI = 32 / LPC;              // columns per pass
+        const long long cap = tcap * mm, zb = tz * mm;
+        const int g = (lane % LPC) * RG, cl = lane / LPC;
+        const float sg = rmw ? 1.f : sgn;
+#pragma unroll
+        for (int q = 0; q < 32 / CPI; ++q) {
+          const int c = q * CPI + cl, rr = rbase + g;
+          if (c0 + c >= m || rr >= m) continue;
+          float f[RG];
+#pragma unroll
+          for (int k = 0; k < RG; ++k) f[k] = sg * stg[(g + k) * 33 + c];
+          putT<MODE>(tr, cap, zb + (long long)(c0 + c) * m + rr, f);
+        }
+      }
+      __syncwarp();  // the staging tile is free for the next chunk
     }
   }
   // copies still in flight after an expired wait land before the CTA leaves

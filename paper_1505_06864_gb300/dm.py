@@ -67,6 +67,9 @@ def lib():
             "dm_plan_tune": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "dm_plan_ex": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I]),
             "dm_plan_inside": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I]),
+            "dm_plan_complex": (I, [ctypes.POINTER(P), I, I, I, I, I, I]),
+            "dm_factor_complex": (I, [P, P, P, P]),
+            "dm_solve_complex": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_partition_sizes": (I, [I, I, I, I, I, ctypes.POINTER(I)]),
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
@@ -123,6 +126,42 @@ def _ptr(a, writable=False):
             raise ValueError("tensors must be float64 and contiguous")
         return ctypes.c_void_p(a.data_ptr())
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _ptrc(a, writable=False):
+    """Raw pointer of a complex128 C-contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.complex128 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("complex arrays must be complex128 and C-contiguous")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("output array is read-only")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise ValueError("complex tensors must be complex128 and contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def dm_plan_complex(N, m, nrhs, P=0, levels=0, precision=DM_FP64):
+    """Plan a complex system (solved through its real embedding of block size 2m)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = ctypes.c_void_p()
+    _check(lib().dm_plan_complex(ctypes.byref(h), int(N), int(m), int(nrhs), int(P), int(levels), int(precision)))
+    return h
+
+
+def dm_factor_complex(plan, A, B, C):
+    return _check(lib().dm_factor_complex(plan, _ptrc(A), _ptrc(B), _ptrc(C)))
+
+
+def dm_solve_complex(plan, b, x, allow_notconv=False):
+    rel = ctypes.c_double(0.0)
+    rc = lib().dm_solve_complex(plan, _ptrc(b), _ptrc(x, True), ctypes.byref(rel))
+    _check(rc, (DM_OK, DM_ENOTCONV) if allow_notconv else (DM_OK,))
+    return rel.value
 
 
 def dm_plan(N, m, nrhs, P=0, levels=0, precision=DM_FP64):

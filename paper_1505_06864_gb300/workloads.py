@@ -37,6 +37,15 @@ Workload recipes (one function each):
   values, the shape of the paper's validation matrices.
 * ``batch_shapes`` -- shapes of a batch of independent systems: N uniform in
   [n_lo, n_hi], m drawn from a set, nrhs uniform in [r_lo, r_hi].
+* ``dominant_system_complex`` -- the dominant recipe with complex entries:
+  real and imaginary parts uniform in [-1, 1] from separate streams, the
+  diagonal shift summing complex moduli; x_true with N(0, 1) real and
+  imaginary parts.
+* ``pde_banded_system_complex`` -- the PDE-shaped recipe whose last block row
+  (A_N, B_N) is complex, as where the paper's application imposes its
+  asymptotic boundary condition with complex (Hankel-function) coefficients
+  (Section 7): the band entries of that row get imaginary parts uniform in
+  [0.5, 2]; the dominance shift uses complex moduli.
 """
 from __future__ import annotations
 
@@ -45,6 +54,7 @@ import numpy as np
 __all__ = [
     "uniform", "normal", "dominant_system", "pde_banded_system",
     "conditioned_system", "batch_shapes", "manufacture_rhs", "System",
+    "dominant_system_complex", "pde_banded_system_complex",
 ]
 
 _G = np.uint64(0x9E3779B97F4A7C15)
@@ -55,6 +65,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 STREAM_A, STREAM_B, STREAM_C, STREAM_X = 1, 2, 3, 4
 STREAM_X2, STREAM_U, STREAM_V, STREAM_SHAPE = 5, 6, 7, 8
 STREAM_RHS, STREAM_RHS2 = 9, 10
+STREAM_IM = 100  # added to a quantity's stream for its imaginary part
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -146,6 +157,21 @@ def dominant_system(N: int, m: int, nrhs: int, seed: int) -> System:
                   f"dominant N={N} m={m} nrhs={nrhs} seed={seed}")
 
 
+def dominant_system_complex(N: int, m: int, nrhs: int, seed: int) -> System:
+    """Complex diagonally dominant system (real and imaginary parts uniform in
+    [-1, 1], per-row shift by the sum of complex moduli plus one); x_true with
+    N(0, 1) real and imaginary parts, b = T x_true (complex128 arrays)."""
+    draw = lambda st: (uniform(seed, st, N * m * m, -1.0, 1.0)
+                       + 1j * uniform(seed, st + STREAM_IM, N * m * m, -1.0, 1.0)).reshape(N, m, m)
+    A, B, C = draw(STREAM_A), draw(STREAM_B), draw(STREAM_C)
+    A[0] = 0.0
+    C[N - 1] = 0.0
+    _dominance_shift(A, B, C)
+    x = (normal(seed, STREAM_X, N * m * nrhs) + 1j * normal(seed, STREAM_X + STREAM_IM, N * m * nrhs)).reshape(N, m, nrhs)
+    return System(A, B, C, manufacture_rhs(A, B, C, x), x,
+                  f"dominant-complex N={N} m={m} nrhs={nrhs} seed={seed}")
+
+
 def _band(seed: int, stream: int, N: int, m: int, hb: int, lo: float, hi: float):
     """Dense [N, m, m] blocks whose entries with |r - c| <= hb are uniform in
     [lo, hi) (draw (i, r, d) fills column r + d - hb) and zero elsewhere."""
@@ -175,6 +201,25 @@ def pde_banded_system(N: int, m: int, nrhs: int, seed: int, hb: int = 3) -> Syst
     x = normal(seed, STREAM_X, N * m * nrhs).reshape(N, m, nrhs)
     return System(A, B, C, manufacture_rhs(A, B, C, x), x,
                   f"pde-banded N={N} m={m} nrhs={nrhs} hb={hb} seed={seed}")
+
+
+def pde_banded_system_complex(N: int, m: int, nrhs: int, seed: int, hb: int = 3) -> System:
+    """pde_banded_system with a complex last block row: the band entries of
+    A_N and B_N get imaginary parts uniform in [0.5, 2] (drawn from their own
+    streams), then the dominance shift with complex moduli; x_true with N(0, 1)
+    real and imaginary parts, b = T x_true (complex128 arrays)."""
+    A = -_band(seed, STREAM_A, N, m, hb, 0.5, 2.0).astype(np.complex128)
+    B = _band(seed, STREAM_B, N, m, hb, 0.5, 2.0).astype(np.complex128)
+    C = -_band(seed, STREAM_C, N, m, hb, 0.5, 2.0)
+    C = C.astype(np.complex128)
+    A[-1] -= 1j * _band(seed, STREAM_A + STREAM_IM, 1, m, hb, 0.5, 2.0)[0]
+    B[-1] += 1j * _band(seed, STREAM_B + STREAM_IM, 1, m, hb, 0.5, 2.0)[0]
+    A[0] = 0.0
+    C[N - 1] = 0.0
+    _dominance_shift(A, B, C)
+    x = (normal(seed, STREAM_X, N * m * nrhs) + 1j * normal(seed, STREAM_X + STREAM_IM, N * m * nrhs)).reshape(N, m, nrhs)
+    return System(A, B, C, manufacture_rhs(A, B, C, x), x,
+                  f"pde-banded-complex N={N} m={m} nrhs={nrhs} hb={hb} seed={seed}")
 
 
 def laplace_fill_system(N: int, m: int, nrhs: int, seed: int, eps: float = 1e-2) -> System:

@@ -102,3 +102,10 @@ def test_dm_inside_arguments_rejected_without_gpu(dm):
         with pytest.raises(dm.DMError) as e:
             dm.dm_plan_inside(*args)
         assert e.value.code == dm.DM_EINVAL, args
+
+
+def test_complex_plan_limits_without_gpu(dm):
+    for args in [(10, 300, 1, 2, 1, "fp64"), (10, 200, 1, 2, 1, "bf16x3"), (10, 0, 1, 2, 1, "fp64")]:
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_plan_complex(*args)
+        assert e.value.code == dm.DM_EINVAL, args

@@ -469,3 +469,37 @@ def test_dm_inside_subsystems(dm, N, m, r, M, J, outer, prec):
     xo = o.dm(s.A, s.B, s.C, s.b, M, levels=outer, J=J)
     check(x, xo, TOL64 if prec == "fp64" else TOLMIX)
     assert rel < 1e-13
+
+
+@pytest.mark.parametrize("gen,N,m,r,P,levels,prec", [("dominant", 64, 16, 1, 4, 1, "fp64"),
+                                                     ("dominant", 97, 20, 3, 7, 2, "fp64"),
+                                                     ("pde", 130, 64, 1, 16, 2, "fp64"),
+                                                     ("pde", 257, 128, 2, 32, 3, "fp64"),
+                                                     ("dominant", 60, 32, 2, 6, 1, "bf16x3"),
+                                                     ("pde", 130, 64, 1, 16, 2, "tf32"),
+                                                     ("dominant", 41, 8, 4, 5, 1, "fp32")])
+def test_complex_systems(dm, gen, N, m, r, P, levels, prec):
+    """Complex systems (the paper's application has complex boundary
+    conditions) through the real embedding of block size 2m, against the
+    complex128 oracle: host arrays, and device tensors for the right-hand side."""
+    import torch
+    s = (w.dominant_system_complex(N, m, r, 300 + N) if gen == "dominant"
+         else w.pde_banded_system_complex(N, m, r, 301 + N))
+    plan = dm.dm_plan_complex(N, m, r, P, levels, prec)
+    try:
+        dm.dm_factor_complex(plan, s.A, s.B, s.C)
+        x = np.zeros_like(s.b)
+        rel = dm.dm_solve_complex(plan, s.b, x)
+        bd = torch.from_numpy(s.b).cuda()
+        xd = torch.zeros_like(bd)
+        dm.dm_solve_complex(plan, bd, xd)
+        torch.cuda.synchronize()
+        q = dm.dm_plan_query(plan)
+    finally:
+        dm.dm_destroy(plan)
+    xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=q["P2"] if q["P2"] > 1 else None)
+    tol = TOL64 if prec == "fp64" else TOLMIX
+    assert o.rel_err(x, xo) <= tol and o.rel_err(xd.cpu().numpy(), xo) <= tol
+    scale = np.max(np.abs(xo), axis=(0, 1))
+    assert np.all(np.max(np.abs(x - xo), axis=(0, 1)) <= tol * scale)
+    assert rel < 1e-13 and q["m"] == 2 * m

@@ -335,6 +335,43 @@ def test_dm_inside_equals_aligned_form(N, m, l, M, J, outer, seed):
     assert c2.total() < c1.total() if M > 1 else c2.total() == c1.total()
 
 
+# ---------------------------------------------------------------- complex systems (Section 7's boundary conditions)
+def test_complex_dense_ge_matches_lapack():
+    rng = np.random.default_rng(3)
+    for n in (1, 3, 8):
+        T = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + n * np.eye(n)
+        b = rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2))
+        np.testing.assert_allclose(o.dense_ge(T, b), np.linalg.solve(T, b), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("gen", ["dominant", "pde"])
+def test_complex_dm_matches_dense_ge(gen):
+    N, m, l = 13, 3, 2
+    s = (w.dominant_system_complex(N, m, l, 22) if gen == "dominant" else w.pde_banded_system_complex(N, m, l, 23))
+    assert np.iscomplexobj(s.A) and np.abs(s.B[-1].imag).max() > 0
+    xd = o.dense_ge(o.dense_from_blocks(s.A, s.B, s.C), s.b.reshape(-1, l)).reshape(N, m, l)
+    assert o.rel_err(xd, s.x_true) < 1e-13
+    for P, lv, J in ((1, 1, None), (3, 1, None), (4, 2, None), (2, 1, 2), (3, 2, 2)):
+        x = o.dm(s.A, s.B, s.C, s.b, P, levels=lv, J=J)
+        assert np.iscomplexobj(x) and o.rel_err(x, xd) < 1e-13, (P, lv, J)
+    xt = o.refine_truth(s.A, s.B, s.C, s.b)
+    assert o.rel_err(xt, s.x_true) < 1e-14
+
+
+def test_real_embedding_identity():
+    """The identity the complex path of the library relies on: with
+    X + iY -> [[X, -Y], [Y, X]] for every block and u + iv -> [u; v] for every
+    right-hand-side block, the real system's solution is [Re x; Im x] of the
+    complex system's (written out here, independently of the library)."""
+    s = w.dominant_system_complex(11, 4, 3, 24)
+    emb = lambda M: np.block([[M.real, -M.imag], [M.imag, M.real]])
+    E = lambda Ms: np.stack([emb(M) for M in Ms])
+    bR = np.concatenate([s.b.real, s.b.imag], axis=1)
+    xR = o.dm(E(s.A), E(s.B), E(s.C), bR, 3)
+    xc = o.dm(s.A, s.B, s.C, s.b, 3)
+    np.testing.assert_allclose(xR[:, :4] + 1j * xR[:, 4:], xc, rtol=0, atol=1e-13 * np.abs(xc).max())
+
+
 # ---------------------------------------------------------------- Section 5.1 speedups from counted runs
 def _serial_count(ctr, ks):
     return sum(ctr.total(f"{st}/{k}") for k in ks for st in ("solve", "wing", "back")) + ctr.total("supp")
