@@ -758,15 +758,63 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Copy between device memory and page-locked host memory by a kernel that
+// reads (or writes) the host buffer through its device mapping: on a
+// coherent CPU-GPU link this runs at the link's bandwidth (measured about
+// 210 GB/s on GB300), where the copy engines reached about 25 GB/s.
+__global__ void k_copy_mapped(uint4* __restrict__ dst, const uint4* __restrict__ src, long long n16) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
+}
+
+// Device address of page-locked, mapped host memory (nullptr otherwise).
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+static int copy_mapped(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const size_t n16 = bytes / 16, tail = bytes - n16 * 16;
+  if (n16) {
+    const int grid = (int)std::min<size_t>((n16 + 255) / 256, 152 * 8);
+    k_copy_mapped<<<grid, 256, 0, st>>>(static_cast<uint4*>(dst), static_cast<const uint4*>(src), (long long)n16);
+    DM_CUDA(cudaGetLastError());
+  }
+  if (tail)
+    DM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + n16 * 16, static_cast<const char*>(src) + n16 * 16, tail,
+                            cudaMemcpyDefault, st));
+  return DM_OK;
+}
+
+static bool aligned16(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return DM_OK;
-  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (is_device_ptr(src)) {
+    DM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return DM_OK;
+  }
+  void* ms = mapped_host(src);
+  if (ms && aligned16(dst, ms)) return copy_mapped(dst, ms, bytes, st);
+  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
   return DM_OK;
 }
 
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return DM_OK;
-  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (is_device_ptr(dst)) {
+    DM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return DM_OK;
+  }
+  void* md = mapped_host(dst);
+  if (md && aligned16(md, src)) return copy_mapped(md, src, bytes, st);
+  DM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
   return DM_OK;
 }
 

@@ -503,3 +503,26 @@ def test_complex_systems(dm, gen, N, m, r, P, levels, prec):
     scale = np.max(np.abs(xo), axis=(0, 1))
     assert np.all(np.max(np.abs(x - xo), axis=(0, 1)) <= tol * scale)
     assert rel < 1e-13 and q["m"] == 2 * m
+
+
+def test_pinned_host_inputs(dm):
+    """Page-locked host arrays are copied by a kernel through their device
+    mapping (and outputs written back the same way): the same x as with
+    pageable host arrays and with device arrays, also for a length that is
+    not a multiple of 16 bytes."""
+    import torch
+    s = w.dominant_system(37, 9, 3, 17)
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    plan = dm.dm_plan(37, 9, 3, 4, 1, "fp64")
+    try:
+        dm.dm_factor(plan, pin(s.A), pin(s.B), pin(s.C))
+        xp = torch.zeros(s.b.shape, dtype=torch.float64).pin_memory()
+        dm.dm_solve(plan, pin(s.b), xp)
+        x = np.zeros_like(s.b)
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        dm.dm_solve(plan, s.b, x)
+    finally:
+        dm.dm_destroy(plan)
+    assert (37 * 9 * 3 * 8) % 16 != 0
+    np.testing.assert_array_equal(xp.numpy(), x)
+    check(x, o.dm(s.A, s.B, s.C, s.b, 4), TOL64)
