@@ -110,6 +110,15 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
  * the longest subsystem sets the step count: equal sizes (flags = 0) are
  * normally faster there. */
 #define DM_PLAN_EQUAL_TIME 1
+/* Float64 block products (DM_FP64 plans and every supplementary level) are by
+ * default computed on the tensor cores by exact digit slicing where the level
+ * has one block size m with m % 8 == 0 and m <= 256: every float64 operand is
+ * cut into nine 6-bit digit slices (bf16) with a power-of-two scale per row
+ * (left operand) or column (right operand), the 53 digit products with
+ * s + t <= 11 are accumulated exactly (integers below 2^24 in float32), and
+ * the sums are combined in float64 -- an error bound of the size of the
+ * float64 dot product's.  DM_PLAN_FP64_FMA keeps them on the float64 pipe. */
+#define DM_PLAN_FP64_FMA 2
 int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags);
 
 /* DM inside the subsystems (Section 4.2.2; counts Eqs. DMrec121, DMrec1212,

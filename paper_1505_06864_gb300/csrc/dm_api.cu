@@ -92,6 +92,7 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
   if (!sub.empty()) {
     supp.reset(new Level());
     supp->depth = depth + 1;
+    supp->fp64_fma = fp64_fma;
     int rc = supp->build(sub, false);
     if (rc) return rc;
   }
@@ -298,10 +299,25 @@ static bool tc2_wanted(const Level& L) {
   return L.tc_mode >= 0 && !(e && e[0] == '0') && uniform_m(L.spec, L.max_m) && tc2_eligible(L.max_m);
 }
 
+// Float64 products by digit slicing on the tensor cores: float64 levels
+// with one block size m % 8 == 0, m <= 256, unless the plan asked for the
+// FP64 pipe (DM_PLAN_FP64_FMA) or DM_FP64_PRODUCTS=fma is set.
+static bool oz_wanted(const Level& L) {
+  const char* e = std::getenv("DM_FP64_PRODUCTS");
+  return !L.f32 && !L.fp64_fma && !(e && std::strcmp(e, "fma") == 0) && uniform_m(L.spec, L.max_m) &&
+         oz_eligible(L.max_m);
+}
+
+static size_t oz_bytes(long long nblk, int nparts, int m) {
+  const size_t mm = (size_t)m * m, sl = (size_t)oz_slice_blocks_bytes(m), nb = nblk / mm, np = std::max(1, nparts);
+  return (3 * nb + 7 * np) * (sl + m * sizeof(int)) + np * mm * sizeof(double);
+}
+
 size_t Level::bytes_needed() const {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   size_t b = 3 * nblk * sizeof(double);     // A, B, C
   if (tc2_wanted(*this)) b += tc2_bytes(tc_mode, nblk, nparts, max_m);
+  else if (oz_wanted(*this)) b += oz_bytes(nblk, nparts, max_m);
   else if (tc_mode >= 0) b += 3 * nblk * sizeof(float);
   b += 4 * nblk * es;                       // G, Acal, ZL, ZR
   b += nvec * es;                           // z
@@ -382,6 +398,38 @@ int Level::allocate() {
     for (int i = 0; ok && i < 5; ++i) ok = tc2_make_map(mode, rbase[i], rblk[i], m, nt, T.maps[3 + i]);
     if (!ok) return set_error(DM_ECUDA, "tensor map creation for the tensor-core step kernels failed (m = %d)", m);
     T.on = true;
+  } else if (oz_wanted(*this)) {
+    // digit slices, exponents and tensor maps of the float64 tensor-core products
+    OzLevel& Z = oz;
+    const int m = max_m, np = std::max(1, nparts);
+    const long long mm = (long long)m * m, nb = nblk / mm;
+    const size_t sl = (size_t)oz_slice_blocks_bytes(m), ex = (size_t)m * sizeof(int);
+    DM_ALLOC(Z.A, nb * sl);
+    DM_ALLOC(Z.CT, nb * sl);
+    DM_ALLOC(Z.Acal, nb * sl);
+    DM_ALLOC(Z.G, np * sl);
+    DM_ALLOC(Z.AcalT, np * sl);
+    DM_ALLOC(Z.YT, np * sl);
+    DM_ALLOC(Z.ZLT, 2 * np * sl);
+    DM_ALLOC(Z.ZRT, 2 * np * sl);
+    DM_ALLOC(Z.eA, nb * ex);
+    DM_ALLOC(Z.eCT, nb * ex);
+    DM_ALLOC(Z.eAcal, nb * ex);
+    DM_ALLOC(Z.eG, np * ex);
+    DM_ALLOC(Z.eAcalT, np * ex);
+    DM_ALLOC(Z.eYT, np * ex);
+    DM_ALLOC(Z.eZLT, 2 * np * ex);
+    DM_ALLOC(Z.eZRT, 2 * np * ex);
+    DM_ALLOC(Z.Y, np * mm * sizeof(double));
+    const void* lbase[3] = {Z.G, Z.A, Z.Acal};
+    const long long lblk[3] = {np, nb, nb};
+    const void* rbase[5] = {Z.CT, Z.YT, Z.AcalT, Z.ZLT, Z.ZRT};
+    const long long rblk[5] = {nb, np, np, 2 * np, 2 * np};
+    bool ok = true;
+    for (int i = 0; ok && i < 3; ++i) ok = oz_make_map(lbase[i], lblk[i], m, oz_box_rows_left(), Z.maps[i]);
+    for (int i = 0; ok && i < 5; ++i) ok = oz_make_map(rbase[i], rblk[i], m, oz_box_rows_right(), Z.maps[3 + i]);
+    if (!ok) return set_error(DM_ECUDA, "tensor map creation for the float64 slice products failed (m = %d)", m);
+    Z.on = true;
   } else if (tc_mode >= 0) {
     DM_ALLOC(A32, nblk * sizeof(float));
     DM_ALLOC(B32, nblk * sizeof(float));
@@ -568,6 +616,83 @@ static void factor_level_tc2(Level& L, cudaStream_t st, Prof& pf) {
               launch_tc2_step(mode, 2, L.d_parts, L.active_back[s], s, m, lo[2], out, maps[2], L.d_err, st));
 }
 
+// Forward and backward sweeps of a float64 level with its block products on
+// the tensor cores by digit slicing (dm_oz.cu): slices of A (rows), C^T and
+// Y_0 = A_first^T (columns), then per step the float64 inversion, the row
+// slices of G_t, launch A = G_t [C_t | Y_t], slices of its results (Acal_t
+// rows and columns, Bcal_t columns, the right spike's seed), launch B =
+// A_{t+1} [Acal_t | Bcal_t] and the column slices of Y_{t+1}; then the
+// backward steps, each followed by the column slices of its spikes.
+static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
+  OzLevel& Z = L.oz;
+  const int m = L.max_m;
+  const long long nb = L.nblk / ((long long)m * m);
+  double* G = static_cast<double*>(L.G);
+  OzOut out;
+  out.B = L.B;
+  out.G = G;
+  out.Acal = static_cast<double*>(L.Acal);
+  out.ZL = static_cast<double*>(L.ZL);
+  out.ZR = static_cast<double*>(L.ZR);
+  out.Y = Z.Y;
+  alignas(64) unsigned char maps[3][3][128];
+  const int sel[3][3] = {{0, 3, 4}, {1, 5, 6}, {2, 6, 7}};
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i) std::memcpy(maps[k][i], Z.maps[sel[k][i]], 128);
+  const int* lexp[3] = {Z.eG, Z.eA, Z.eAcal};
+  const int* r0exp[3] = {Z.eCT, Z.eAcalT, Z.eZLT};
+  const int* r1exp[3] = {Z.eYT, Z.eZLT, Z.eZRT};
+  auto job = [](const double* src, void* dst, int* e, int kind) { return OzSliceJob{src, dst, e, kind}; };
+  auto slice_inputs = [&] {
+    launch_oz_slice_all(false, L.A, (int)nb, m, Z.A, Z.eA, st);
+    launch_oz_slice_all(true, L.C, (int)nb, m, Z.CT, Z.eCT, st);
+    OzSliceJobs j0;
+    j0.job[0] = job(L.A, Z.YT, Z.eYT, 8);
+    launch_oz_slice_jobs(L.d_parts, L.nparts, 0, m, j0, 1, st);
+  };
+  Cost cslice = L.c_cvt;
+  DM_LAUNCH(pf, st, K_TC_CONVERT, cslice, 1, slice_inputs());
+  Cost cs;
+  cs.bytes = 26.0 * m * m;  // one block: float64 read, nine bf16 slices written
+  for (int t = 0; t < L.Lmax; ++t) {
+    const int np = L.active_fwd[t], nbk = L.active_back[t];
+    DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<double>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
+    OzSliceJobs jg;
+    jg.job[0] = job(G, Z.G, Z.eG, 0);
+    Cost c0 = cs;
+    c0.bytes *= np;
+    DM_LAUNCH(pf, st, K_TC_CONVERT, c0, np, launch_oz_slice_jobs(L.d_parts, np, t, m, jg, 1, st));
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdA[t], np,
+              launch_oz_step(0, L.d_parts, np, t, m, out, lexp[0], r0exp[0], r1exp[0], maps[0], L.d_err, st));
+    OzSliceJobs ja;
+    ja.job[0] = job(out.Acal, Z.Acal, Z.eAcal, 1);
+    ja.job[1] = job(out.Acal, Z.AcalT, Z.eAcalT, 2);
+    ja.job[2] = job(out.ZL, Z.ZLT, Z.eZLT, 3);
+    ja.job[3] = job(out.ZR, Z.ZRT, Z.eZRT, 4);
+    Cost c1 = cs;
+    c1.bytes *= 4.0 * np;
+    DM_LAUNCH(pf, st, K_TC_CONVERT, c1, np, launch_oz_slice_jobs(L.d_parts, np, t, m, ja, 4, st));
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdB[t], nbk,
+              launch_oz_step(1, L.d_parts, nbk, t, m, out, lexp[1], r0exp[1], r1exp[1], maps[1], L.d_err, st));
+    OzSliceJobs jy;
+    jy.job[0] = job(Z.Y, Z.YT, Z.eYT, 5);
+    Cost c2 = cs;
+    c2.bytes *= nbk;
+    DM_LAUNCH(pf, st, K_TC_CONVERT, c2, nbk, launch_oz_slice_jobs(L.d_parts, nbk, t, m, jy, 1, st));
+  }
+  for (int s = 0; s + 1 < L.Lmax; ++s) {
+    const int nbk = L.active_back[s];
+    DM_LAUNCH(pf, st, K_BACK_FACTOR, L.c_back[s], nbk,
+              launch_oz_step(2, L.d_parts, nbk, s, m, out, lexp[2], r0exp[2], r1exp[2], maps[2], L.d_err, st));
+    OzSliceJobs jb;
+    jb.job[0] = job(out.ZL, Z.ZLT, Z.eZLT, 6);
+    jb.job[1] = job(out.ZR, Z.ZRT, Z.eZRT, 7);
+    Cost c3 = cs;
+    c3.bytes *= 2.0 * nbk;
+    DM_LAUNCH(pf, st, K_TC_CONVERT, c3, nbk, launch_oz_slice_jobs(L.d_parts, nbk, s, m, jb, 2, st));
+  }
+}
+
 // Forward and backward spike sweeps, assembly, and the factorisation of the
 // supplementary level (recursively).  A, B, C must hold the level's blocks.
 template <typename T>
@@ -578,6 +703,16 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   T* ZR = static_cast<T*>(L.ZR);
   // With a side stream, the left-spike tiles of step t (type 1) run there,
   // overlapping the next inversion, which depends only on the type-0 tiles.
+  if constexpr (std::is_same<T, double>::value) {
+    if (L.oz.on) {
+      factor_level_oz(L, st, pf);
+      if (L.supp)
+        DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
+                  launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
+                                       L.supp->C, st));
+      return;
+    }
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (L.tc2.on) {
       factor_level_tc2(L, st, pf);
@@ -859,6 +994,7 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   precision = prec;
   DM_CUDA(cudaGetDevice(&device));
   top.lazy_inputs = true;
+  top.fp64_fma = !specs.empty() && (specs[0].flags & DM_PLAN_FP64_FMA) != 0;
   int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
   {
@@ -1286,7 +1422,7 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
 
 int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths) {
   if (!lengths) return set_error(DM_EINVAL, "NULL lengths");
-  if (flags & ~DM_PLAN_EQUAL_TIME) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
+  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA)) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, 1, &s);
   if (rc) return rc;
@@ -1298,7 +1434,7 @@ int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths) {
 
 int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags) {
   if (!out) return set_error(DM_EINVAL, "out is NULL");
-  if (flags & ~DM_PLAN_EQUAL_TIME) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
+  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA)) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
   if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
     return set_error(DM_EINVAL, "unknown precision %d", precision);
   if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)

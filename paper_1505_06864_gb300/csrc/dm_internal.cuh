@@ -136,6 +136,33 @@ struct Tc2Out {
   long long cap_acal_l, cap_acalT, cap_yT, cap_zlT, cap_zrT;
 };
 bool tc2_eligible(int m);
+
+// Float64 products on the tensor cores by exact digit slicing (dm_oz.cu):
+// the step kernels' products with float64 operands and results, the operands
+// as nine bf16 digit slices with per-row (left) / per-column (right) scales.
+struct OzOut {
+  const double* B;
+  double *G, *Acal, *ZL, *ZR, *Y;  // Y: Y_{t+1} per subsystem (rolling, float64)
+};
+bool oz_eligible(int m);
+int oz_slice_blocks_bytes(int m);
+bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out);
+int oz_box_rows_left();
+int oz_box_rows_right();
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st);
+struct OzSliceJob {
+  const double* src;
+  void* dst;
+  int* exps;
+  int kind;  // see k_oz_slice_jobs
+};
+struct OzSliceJobs {
+  OzSliceJob job[4];
+};
+void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
+                          cudaStream_t st);
+void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
+                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st);
 int tc2_ntile(int m);
 bool tc2_make_map(int mode, const void* base, long long blocks, int m, int box_rows, void* out);
 int tc2_map_bytes();

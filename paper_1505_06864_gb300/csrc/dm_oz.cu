@@ -1,0 +1,514 @@
+// Float64 block products of the factor sweeps on the bf16 tensor cores by
+// exact digit slicing (Ozaki's error-free splitting of matrix products; the
+// digit extraction, accumulator grouping and pipeline are this library's).
+//
+// The products are the ones of the tensor-core step kernels (dm_tc2.cu):
+// launch A = G_t [C_t | Y_t], launch B = A_{t+1} [Acal_t | Bcal_t], backward
+// Acal_t [ZL_{t+1} | ZR_{t+1}] (Section 3 applied to Eq. e231), here with
+// float64 operands and results.  Every operand block is cut into nine digit
+// slices (dm_slices.cuh): a left operand L with one power-of-two scale per
+// row r (|L[r][k]| < 2^e_r), a right operand R with one per column n
+// (|R[k][n]| < 2^f_n), stored transposed (row n of the copy is column n of
+// R).  Then
+//
+//   (L R)[r][n] = 2^(e_r + f_n) sum_{d=2..11} 2^(-6d) acc_d[r][n],
+//   acc_d = sum_{s+t=d} Lslice_s Rslice_t,
+//
+// keeping the 53 slice pairs with s + t <= 11.  Each acc_d sums at most nine
+// slice products over K = m <= 256 terms of magnitude <= 63^2: integers below
+// 9 * 256 * 3969 < 2^24, so the float32 accumulation in tensor memory is
+// exact.  The dropped pairs and the digit truncation bound the error of an
+// entry by about K 2^-50 max_k |L[r][k]| max_k |R[k][n]|, the size of the
+// float64 dot product's own bound.
+//
+// A CTA computes a 128 x 48 tile of one product: ten accumulators of 48
+// columns (480 tensor-memory columns), a two-stage ring of 32-wide K slabs
+// (nine left slices 72 KB + nine right slices 27 KB + a zero slice), one CTA
+// per SM.  Per 16-wide K step one thread issues 14 MMAs: left slice s
+// against right slices t = 1 .. T_s at once (stored consecutively, N = 48 per
+// slice, at most five per instruction), into accumulators d = s + t.  With
+// s = 1 the right slices run to a tenth, all-zero slice, so that the first
+// K step's two instructions for s = 1 initialise all ten accumulators.  The
+// epilogue combines the accumulators in 64-bit integers and scales once in
+// float64 (GB300's float64 pipe is narrow).  Operand slices of results are
+// made by separate slicing launches, which see whole rows and columns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "dm_internal.cuh"
+#include "dm_slices.cuh"
+#include "dm_tcgen05.cuh"
+
+namespace dm {
+namespace oz {
+using namespace ptx;
+
+constexpr int kThreads = 128;
+constexpr int MT = 128;          // rows per tile
+constexpr int NT = 48;           // columns per tile
+constexpr int KS = 32;           // K elements per stage (64-byte rows, 64-byte swizzle)
+constexpr int kStages = 2;
+constexpr int S = kRsSlices;     // 9 slices
+constexpr int NACC = 10;         // accumulators d = 2 .. 11
+constexpr int ROWB = KS * 2;     // 64 bytes
+constexpr int LSL = MT * ROWB;   // one left slice in a stage: 8 KB
+constexpr int RSL = NT * ROWB;   // one right slice: 3 KB
+constexpr int LBYTES = S * LSL;  // 72 KB
+constexpr int RBYTES = (S + 1) * RSL;  // 30 KB with the zero slice
+constexpr int STAGE = LBYTES + RBYTES;
+constexpr int SMEM = 1024 + kStages * STAGE;
+constexpr uint32_t kCols = 512;
+constexpr uint32_t kSbo = 8 * ROWB;  // 512-byte swizzle atoms
+constexpr uint64_t kLayout = 4;       // 64-byte swizzle
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 2^k as a float64 for -1022 <= k <= 1023.
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+}  // namespace oz
+
+struct OzMaps {
+  CUtensorMap L, R0, R1;
+};
+
+namespace oz {
+
+// KIND 0: launch A, 1: launch B (forward step `step`), 2: backward step
+// `step`.  blockIdx.y = subsystem; blockIdx.x = ((2 * M-tile + product) *
+// ntn + N-tile).  Exponent arrays: [block][m] ints, indexed like the slices.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_oz_step(const PartDesc* __restrict__ parts, int step, int m, int ntn, OzOut out, const int* __restrict__ lexp,
+              const int* __restrict__ rexp0, const int* __restrict__ rexp1, int* __restrict__ errflag,
+              const __grid_constant__ OzMaps maps) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ uint64_t full[kStages], empty[kStages], accb;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int err, nissued, ncons;
+  const int pidx = blockIdx.y;
+  const PartDesc p = parts[pidx];
+  const int tn = blockIdx.x % ntn, rest = blockIdx.x / ntn, j = rest & 1, tm = rest >> 1;
+  if (tm * MT >= m || tn * NT >= m) return;
+  int t;
+  bool act;
+  if (KIND == 0) {
+    t = step;
+    act = t < p.L && (j == 0 ? (t < p.L - 1 || (p.flags & HAS_RIGHT) != 0) : (p.flags & HAS_LEFT) != 0);
+  } else if (KIND == 1) {
+    t = step;
+    act = t < p.L - 1 && (j == 0 || (p.flags & HAS_LEFT) != 0);
+  } else {
+    t = p.L - 2 - step;
+    act = t >= 0 && (j == 0 ? (p.flags & HAS_LEFT) != 0 : (p.flags & HAS_RIGHT) != 0);
+  }
+  if (!act) return;
+  const long long mm = (long long)m * m;
+  const int b0 = (int)(p.blk / mm);
+  int zl, zr;
+  if (KIND == 0) {
+    zl = pidx;                   // G_t slices (rolling)
+    zr = j == 0 ? b0 + t : pidx;  // C_t^T (all blocks) / Y_t^T (rolling)
+  } else if (KIND == 1) {
+    zl = b0 + t + 1;                          // A_{t+1}
+    zr = j == 0 ? pidx : 2 * pidx + (t & 1);  // Acal_t^T / Bcal_t^T
+  } else {
+    zl = b0 + t;                    // Acal_t
+    zr = 2 * pidx + ((t + 1) & 1);  // ZL_{t+1}^T / ZR_{t+1}^T
+  }
+  const CUtensorMap* mr = j == 0 ? &maps.R0 : &maps.R1;
+  const int* rexp = j == 0 ? rexp0 : rexp1;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the zero right slice of both stages (never written by the copies)
+  for (int st = 0; st < kStages; ++st)
+    for (int i = threadIdx.x; i < RSL / 16; i += kThreads)
+      reinterpret_cast<uint4*>(base + st * STAGE + LBYTES + S * RSL)[i] = make_uint4(0u, 0u, 0u, 0u);
+  fence_async_shared();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accb, 1);
+    err = 0;
+    nissued = 0;
+    ncons = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int nslab = (m + KS - 1) / KS;
+  constexpr uint32_t tx = (uint32_t)(S * (MT + NT) * ROWB);
+
+  if (warp == 0 && lane == 0) {
+    uint32_t ph[kStages] = {0u, 0u};
+    int s = 0;
+    for (; s < nslab; ++s) {
+      const int st = s & 1;
+      if (s >= kStages) {
+        if (!mbar_wait(&empty[st], ph[st])) {
+          err = 1;
+          break;
+        }
+        ph[st] ^= 1u;
+      }
+      const uint32_t sb = smem_u32(base + st * STAGE);
+      mbar_expect_tx(&full[st], tx);
+      tma_load_4d(sb, &maps.L, s * KS, tm * MT, 0, zl, &full[st]);
+      tma_load_4d(sb + LBYTES, mr, s * KS, tn * NT, 0, zr, &full[st]);
+    }
+    nissued = s;
+  } else if (warp == 1 && lane == 0) {
+    int s = 0;
+    for (; s < nslab; ++s) {
+      const int st = s & 1;
+      if (!mbar_wait(&full[st], (uint32_t)((s >> 1) & 1))) {
+        err = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t la = smem_u32(base + st * STAGE), ra = la + LBYTES;
+#pragma unroll
+      for (int k = 0; k < KS / 16; ++k) {
+        const uint32_t off = (uint32_t)(k * 32);
+#pragma unroll
+        for (int sl = 1; sl <= S; ++sl) {
+          const int T = sl == 1 ? S + 1 : min(S, 11 - sl);  // s = 1 runs into the zero slice
+          const uint64_t ad = kmajor_desc(la + (sl - 1) * LSL + off, kSbo, kLayout);
+#pragma unroll
+          for (int ta = 1; ta <= T; ta += 5) {
+            const int cnt = min(5, T - ta + 1);
+            const uint64_t bd = kmajor_desc(ra + (ta - 1) * RSL + off, kSbo, kLayout);
+            const uint32_t dcol = (uint32_t)((sl + ta - 2) * NT);
+            const uint32_t acc = (s == 0 && k == 0 && sl == 1) ? 0u : 1u;
+            mma<1>(tmem + dcol, ad, bd, make_idesc(1u, MT, NT * cnt), acc);
+          }
+        }
+      }
+      mma_commit(&empty[st]);
+    }
+    ncons = s;
+    mma_commit(&accb);
+  }
+  if (warp < 2) __syncwarp();
+  bool ok = mbar_wait(&accb, 0u);
+  tc_fence_after();
+  ok = __syncthreads_and(ok) && !err;
+
+  if (ok) {
+    // Accumulators of this thread's row (tensor-memory lane) for 16 columns
+    // at a time, combined exactly: ih = sum_{d=2..6} acc_d 2^(6(6-d)),
+    // il = sum_{d=7..11} acc_d 2^(6(11-d)); value = (ih 2^30 + il) 2^(e_r + f_n - 66).
+    // Results are staged through a per-warp 32 x 33 float64 tile so that row-
+    // major writes are coalesced.
+    double* stg = reinterpret_cast<double*>(base) + warp * (32 * 17);
+    const int rbase = tm * MT + warp * 32, row = rbase + lane;
+    const int er = row < m ? lexp[(long long)zl * m + row] : 0;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const long long o = p.blk + (long long)t * mm;
+    for (int ch = 0; ch < NT; ch += 16) {
+      long long ih[16], il[16];
+      uint32_t nanc = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) ih[c] = il[c] = 0;
+#pragma unroll
+      for (int dd = 0; dd < NACC; ++dd) {
+        float v[16];
+        tmem_ld16(tl + (uint32_t)(dd * NT + ch), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          if (v[c] != v[c]) nanc |= 1u << c;
+          const long long a = (long long)__float2int_rn(v[c]);
+          if (dd < 5)
+            ih[c] += a << (6 * (4 - dd));
+          else
+            il[c] += a << (6 * (9 - dd));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int n = tn * NT + ch + c;
+        double val = 0.0;
+        if (row < m && n < m) {
+          const int k = er + rexp[(long long)zr * m + n];
+          if ((nanc >> c) & 1u)
+            val = __longlong_as_double(0x7ff8000000000000ll);
+          else if (k - 66 >= -1022 && k - 36 <= 1023)
+            val = fma((double)il[c], pow2(k - 66), (double)ih[c] * pow2(k - 36));
+          else
+            val = ldexp(fma((double)il[c], 0x1p-30, (double)ih[c]), k - 36);
+        }
+        stg[lane * 17 + c] = val;
+      }
+      __syncwarp();
+      // row-major float64 results: lane = (row parity, column), 16 row pairs;
+      // the loads an update needs are gathered before any store
+      const int cl = lane & 15, r0 = lane >> 4, n = tn * NT + ch + cl;
+      if (n < m) {
+        const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0;
+        double in[16];
+        if (rmw || dnext) {
+          const double* src = rmw ? out.ZL + o : out.B + o + mm;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int rr = rbase + r0 + 2 * i;
+            in[i] = rr < m ? src[(long long)rr * m + n] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = r0 + 2 * i, rr = rbase + r;
+          if (rr >= m) continue;
+          const double w = stg[r * 17 + cl];
+          const long long e = (long long)rr * m + n;
+          if (KIND == 0) {
+            double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
+            d[o + e] = w;
+          } else if (dnext) {
+            out.G[o + mm + e] = in[i] - w;                // D_{t+1} = B_{t+1} - A_{t+1} Acal_t
+          } else if (KIND == 1) {
+            out.Y[(long long)pidx * mm + e] = -w;         // Y_{t+1} = -A_{t+1} Bcal_t
+          } else if (rmw) {
+            out.ZL[o + e] = in[i] - w;                    // ZL_t -= Acal_t ZL_{t+1}
+          } else {
+            out.ZR[o + e] = -w;                           // ZR_t = -Acal_t ZR_{t+1}
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (threadIdx.x == 0)
+    for (int s = ncons; s < nissued; ++s) mbar_wait(&full[s & 1], (uint32_t)((s >> 1) & 1));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kCols);
+  if (threadIdx.x == 0 && !ok && errflag) atomicExch(errflag, 1);
+}
+
+// ---------------------------------------------------------------- slicing
+// Row slices of one float64 m x m block (left operands): exps[r] = e with
+// |v| < 2^e for the row's largest |v|, slice s element (r, k) at
+// (q * 9 + s) m^2 + r m + k.  One warp per row, eight consecutive columns per
+// lane (m % 8 == 0).
+__device__ __forceinline__ void slice_rows_block(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 long long qdst, int* __restrict__ exps, int m) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long mm = (long long)m * m;
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
+  for (int r = warp; r < m; r += nw) {
+    uint32_t hmax = 0;
+    for (int c = lane; c < m; c += 32) hmax = max(hmax, (uint32_t)(bits[(long long)r * m + c] >> 32) & 0x7fffffffu);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    const int e = scale_exponent(hmax);
+    if (lane == 0) exps[qdst * m + r] = e;
+    for (int c0 = lane * 8; c0 < m; c0 += 256) {
+      uint32_t q[8][S];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) digits9(bits[(long long)r * m + c0 + u], e, q[u]);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        uint4 w;
+        w.x = (q[0][sl] >> 16) | (q[1][sl] & 0xffff0000u);
+        w.y = (q[2][sl] >> 16) | (q[3][sl] & 0xffff0000u);
+        w.z = (q[4][sl] >> 16) | (q[5][sl] & 0xffff0000u);
+        w.w = (q[6][sl] >> 16) | (q[7][sl] & 0xffff0000u);
+        *reinterpret_cast<uint4*>(dst + (qdst * S + sl) * mm + (long long)r * m + c0) = w;
+      }
+    }
+  }
+}
+
+// Column slices, transposed (right operands): exps[n] for column n, slice s
+// element (n, k) = digit s of src[k][n] at (q * 9 + s) m^2 + n m + k.
+// Column maxima first, then 32 x 32 tiles through shared memory.
+__device__ __forceinline__ void slice_cols_block(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 long long qdst, int* __restrict__ exps, int m, int* s_exp,
+                                                 unsigned long long (*tile)[33]) {
+  const long long mm = (long long)m * m;
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
+  for (int n = threadIdx.x; n < m; n += blockDim.x) {
+    uint32_t hmax = 0;
+    for (int k = 0; k < m; ++k) hmax = max(hmax, (uint32_t)(bits[(long long)k * m + n] >> 32) & 0x7fffffffu);
+    const int e = scale_exponent(hmax);
+    s_exp[n] = e;
+    exps[qdst * m + n] = e;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int k0 = 0; k0 < m; k0 += 32)
+    for (int n0 = 0; n0 < m; n0 += 32) {
+      for (int y = ty; y < 32; y += ny) {
+        const int k = k0 + y, n = n0 + tx;
+        tile[y][tx] = (k < m && n < m) ? bits[(long long)k * m + n] : 0ull;
+      }
+      __syncthreads();
+      for (int y = ty; y < 32; y += ny) {
+        const int n = n0 + y, k = k0 + tx;  // output row n, column k = tile[tx][y]
+        if (n < m && k < m) {
+          uint32_t q[S];
+          digits9(tile[tx][y], s_exp[n], q);
+#pragma unroll
+          for (int sl = 0; sl < S; ++sl)
+            dst[(qdst * S + sl) * mm + (long long)n * m + k] = __ushort_as_bfloat16((unsigned short)(q[sl] >> 16));
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// Slices of every block of a level's array (A as rows, C as transposed columns).
+template <bool COLS>
+__global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__ src, int nblocks, int m,
+                                                      __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
+  __shared__ int s_exp[kMaxMTensor];
+  __shared__ unsigned long long tile[32][33];
+  const long long mm = (long long)m * m;
+  for (int q = blockIdx.x; q < nblocks; q += gridDim.x) {
+    if (COLS)
+      slice_cols_block(src + q * mm, dst, q, exps, m, s_exp, tile);
+    else
+      slice_rows_block(src + q * mm, dst, q, exps, m);
+    __syncthreads();
+  }
+}
+
+// Per-subsystem slicing jobs (k_oz_slice_jobs, blockIdx.x = subsystem), kind:
+//   0 G_t rows -> rolling (q);            1 Acal_t rows -> all blocks (b0 + t);
+//   2 Acal_t columns -> rolling (q);      3 ZL_t columns -> rolling slot (2q + t%2);
+//   4 ZR_{L-1} columns (last row, right spike) -> slot;  5 Y_{t+1} columns -> rolling (q);
+//   6 ZL_t columns, backward step;        7 ZR_t columns, backward step;
+//   8 Y_0 = A_first columns -> rolling (q), at the start of a factorisation.
+// Several per-subsystem slicing jobs in one launch (blockIdx.y = job).
+__global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restrict__ parts, int step, int m,
+                                                       OzSliceJobs jobs) {
+  __shared__ int s_exp[kMaxMTensor];
+  __shared__ unsigned long long tile[32][33];
+  const OzSliceJob& jb = jobs.job[blockIdx.y];
+  const int q = blockIdx.x;
+  const PartDesc p = parts[q];
+  const long long mm = (long long)m * m;
+  const bool hl = (p.flags & HAS_LEFT) != 0, hr = (p.flags & HAS_RIGHT) != 0;
+  int t = step;
+  bool act;
+  long long sblk, dq;
+  switch (jb.kind) {
+    case 0: act = t < p.L; sblk = p.blk / mm + t; dq = q; break;
+    case 1: act = t < p.L - 1; sblk = p.blk / mm + t; dq = p.blk / mm + t; break;
+    case 2: act = t < p.L - 1; sblk = p.blk / mm + t; dq = q; break;
+    case 3: act = t < p.L && hl; sblk = p.blk / mm + t; dq = 2 * q + (t & 1); break;
+    case 4: act = t == p.L - 1 && hr; sblk = p.blk / mm + t; dq = 2 * q + (t & 1); break;
+    case 5: act = t < p.L - 1 && hl; sblk = q; dq = q; break;
+    case 6: t = p.L - 2 - step; act = t >= 0 && hl; sblk = p.blk / mm + t; dq = 2 * q + (t & 1); break;
+    case 7: t = p.L - 2 - step; act = t >= 0 && hr; sblk = p.blk / mm + t; dq = 2 * q + (t & 1); break;
+    default: act = hl; sblk = p.blk / mm; dq = q; break;
+  }
+  if (!act) return;
+  __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(jb.dst);
+  if (jb.kind == 0 || jb.kind == 1)
+    slice_rows_block(jb.src + sblk * mm, dst, dq, jb.exps, m);
+  else
+    slice_cols_block(jb.src + sblk * mm, dst, dq, jb.exps, m, s_exp, tile);
+}
+
+}  // namespace oz
+
+// ---------------------------------------------------------------- host side
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                              const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn oz_encoder() {
+  static EncodeFn enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    enc = reinterpret_cast<EncodeFn>(fn);
+  }
+  return enc;
+}
+}  // namespace
+
+bool oz_eligible(int m) { return m >= 8 && m <= kMaxMTensor && m % 8 == 0; }
+
+int oz_slice_blocks_bytes(int m) { return oz::S * m * m * 2; }
+
+// 4-D map [block][slice][row][column] of a slice array, box 32 x box_rows x 9 x 1.
+bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out) {
+  EncodeFn enc = oz_encoder();
+  if (!enc || blocks <= 0 || !oz_eligible(m)) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)oz::S, (cuuint64_t)blocks};
+  cuuint64_t strides[3] = {(cuuint64_t)m * 2, (cuuint64_t)m * m * 2, (cuuint64_t)oz::S * m * m * 2};
+  cuuint32_t box[4] = {(cuuint32_t)oz::KS, (cuuint32_t)box_rows, (cuuint32_t)oz::S, 1u};
+  cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  CUresult r = enc(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int oz_box_rows_left() { return oz::MT; }
+int oz_box_rows_right() { return oz::NT; }
+
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  const int grid = std::min(nblocks, 152 * 8);
+  if (cols)
+    oz::k_oz_slice_all<true><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps);
+  else
+    oz::k_oz_slice_all<false><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps);
+}
+
+void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
+                          cudaStream_t st) {
+  if (nparts <= 0 || njobs <= 0) return;
+  oz::k_oz_slice_jobs<<<dim3(nparts, njobs), 256, 0, st>>>(parts, step, m, jobs);
+}
+
+void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
+                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st) {
+  if (nparts <= 0) return;
+  OzMaps mp;
+  std::memcpy(&mp, maps3, sizeof mp);
+  const int ntm = (m + oz::MT - 1) / oz::MT, ntn = (m + oz::NT - 1) / oz::NT;
+  const dim3 grid(2 * ntm * ntn, nparts);
+#define DM_OZ(KIND_)                                                                                              \
+  do {                                                                                                           \
+    static bool set = false;                                                                                     \
+    if (!set) {                                                                                                  \
+      cudaFuncSetAttribute(oz::k_oz_step<KIND_>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM);        \
+      set = true;                                                                                                \
+    }                                                                                                            \
+    oz::k_oz_step<KIND_><<<grid, oz::kThreads, oz::SMEM, st>>>(parts, step, m, ntn, out, lexp, rexp0, rexp1,     \
+                                                               errflag, mp);                                     \
+  } while (0)
+  if (kind == 0) DM_OZ(0);
+  else if (kind == 1) DM_OZ(1);
+  else DM_OZ(2);
+#undef DM_OZ
+}
+
+}  // namespace dm

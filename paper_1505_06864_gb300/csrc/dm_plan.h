@@ -85,6 +85,23 @@ struct Tc2Level {
   alignas(64) unsigned char maps[8][128];
 };
 
+// Digit slices of a float64 level with one block size m (m % 8 == 0,
+// m <= 256) for the products on the tensor cores (dm_oz.cu): nine bf16
+// slices per block ([block][slice][row][column]) and one exponent per row
+// ([block][m] ints).  Full copies: A (rows), C^T (columns of C), Acal (rows);
+// rolling, per subsystem: G_t (rows), Acal_t^T, Y_t^T, and two slots each of
+// ZL^T, ZR^T (columns); Y: Y_{t+1} per subsystem in float64.
+struct OzLevel {
+  bool on = false;
+  void *A = nullptr, *CT = nullptr, *Acal = nullptr, *G = nullptr;
+  void *AcalT = nullptr, *YT = nullptr, *ZLT = nullptr, *ZRT = nullptr;
+  int *eA = nullptr, *eCT = nullptr, *eAcal = nullptr, *eG = nullptr;
+  int *eAcalT = nullptr, *eYT = nullptr, *eZLT = nullptr, *eZRT = nullptr;
+  double* Y = nullptr;
+  // tensor maps: left G, A, Acal; right CT, YT, AcalT, ZLT, ZRT
+  alignas(64) unsigned char maps[8][128];
+};
+
 // One level of the recursion: a set of independent systems, each split into
 // subsystems, with the float64 supplementary systems one level down.
 struct Level {
@@ -95,6 +112,8 @@ struct Level {
   alignas(64) unsigned char tmaps[3 * 128];  // TMA tensor maps of G, A32, Acal (TF32 level, one block size)
   bool has_tma = false;
   Tc2Level tc2;
+  OzLevel oz;
+  bool fp64_fma = false;  // float64 products on the FP64 pipe even where digit slicing applies
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0

@@ -174,6 +174,7 @@ def dm_plan(N, m, nrhs, P=0, levels=0, precision=DM_FP64):
 
 
 DM_PLAN_EQUAL_TIME = 1
+DM_PLAN_FP64_FMA = 2
 
 
 def dm_plan_ex(N, m, nrhs, P=0, levels=0, precision=DM_FP64, flags=0):

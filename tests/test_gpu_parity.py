@@ -526,3 +526,40 @@ def test_pinned_host_inputs(dm):
     assert (37 * 9 * 3 * 8) % 16 != 0
     np.testing.assert_array_equal(xp.numpy(), x)
     check(x, o.dm(s.A, s.B, s.C, s.b, 4), TOL64)
+
+
+@pytest.mark.parametrize("N,m,r,P,levels", [(64, 16, 1, 4, 1), (97, 40, 3, 7, 2), (40, 64, 4, 6, 1),
+                                            (12, 256, 2, 3, 1), (200, 8, 1, 30, 3), (33, 128, 16, 4, 2)])
+def test_fp64_products_sliced_and_fma(dm, N, m, r, P, levels):
+    """Float64 block products on the tensor cores by exact digit slicing (the
+    default where a level has one block size m % 8 == 0) and on the FP64 pipe
+    (DM_PLAN_FP64_FMA): both against the oracle at the float64 tolerance and
+    against each other."""
+    s = w.dominant_system(N, m, r, 700 + N + m)
+    out = {}
+    for flags in (0, dm.DM_PLAN_FP64_FMA):
+        plan = dm.dm_plan_ex(N, m, r, P, levels, "fp64", flags)
+        try:
+            dm.dm_factor(plan, s.A, s.B, s.C)
+            x = np.zeros_like(s.b)
+            rel = dm.dm_solve(plan, s.b, x)
+            P2 = dm.dm_plan_query(plan)["P2"]
+        finally:
+            dm.dm_destroy(plan)
+        assert rel < 1e-14
+        out[flags] = x
+    xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=P2 if P2 > 1 else None)
+    check(out[0], xo, TOL64)
+    check(out[dm.DM_PLAN_FP64_FMA], xo, TOL64)
+    check(out[0], out[dm.DM_PLAN_FP64_FMA], TOL64)
+
+
+def test_fp64_sliced_products_conditioned_blocks(dm):
+    """Dense nonsymmetric blocks with cond(B_i) = 1e4 (pivoting inside the
+    blocks, entries of widely different size in G_i): the digit-sliced
+    products against the extended-precision truth."""
+    s = w.conditioned_system(60, 64, 3, 19, cond=1e4)
+    xt = o.refine_truth(s.A, s.B, s.C, s.b)
+    for P, lv in ((1, 1), (6, 1), (15, 2)):
+        x, rel, _ = solve(dm, s, P, lv)
+        check(x, xt, 1e-11)
