@@ -447,19 +447,32 @@ def timed(fn, reps=1):
 
 
 def sweep_leg(dm, A, B, C, b, stream):
-    """P in {4, 16, 64} x recursion depth {1, 2, 3}: one warm-up and one timed step each."""
+    """P in {4, 16, 64} x recursion depth {1, 2, 3} (the workload's stated
+    sweep), then outside it: P = 128 and 152, DM inside the subsystems
+    (M subsystems of J sub-subsystems, Section 4.2.2), and P = 64 with the
+    float64 products on the FP64 pipe.  One warm-up and one timed step each."""
     import torch
     out = []
     x = torch.empty_like(b)
+
+    def run(plan, rec):
+        dm.dm_set_stream(plan, stream)
+        q = dm.dm_plan_query(plan)
+        dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x))[1])
+        rec.update({"P": q["P"], "levels": q["levels"], "P2": q["P2"], "systems_per_s": 1.0 / dt,
+                    "ms": 1e3 * dt, "relres": rel})
+        out.append(rec)
+        dm.dm_destroy(plan)
+
     for P in (4, 16, 64):
         for lv in (1, 2, 3):
-            plan = dm.dm_plan(N_, M_, R_, P, lv, dm.DM_FP64)
-            dm.dm_set_stream(plan, stream)
-            q = dm.dm_plan_query(plan)
-            dt, rel = timed(lambda: (dm.dm_factor(plan, A, B, C), dm.dm_solve(plan, b, x))[1])
-            out.append({"P": P, "levels": q["levels"], "P2": q["P2"], "systems_per_s": 1.0 / dt,
-                        "ms": 1e3 * dt, "relres": rel})
-            dm.dm_destroy(plan)
+            run(dm.dm_plan(N_, M_, R_, P, lv, dm.DM_FP64), {})
+    for P in (128, 152):
+        run(dm.dm_plan(N_, M_, R_, P, 3, dm.DM_FP64), {"outside_stated_set": True})
+    for M, J, outer in ((16, 4, 2), (32, 2, 2), (64, 2, 2)):
+        run(dm.dm_plan_inside(N_, M_, R_, M, J, outer, dm.DM_FP64),
+            {"inside": {"M": M, "J": J, "outer_levels": outer}, "outside_stated_set": True})
+    run(dm.dm_plan_ex(N_, M_, R_, 64, 3, dm.DM_FP64, dm.DM_PLAN_FP64_FMA), {"products": "FP64 pipe"})
     return out
 
 

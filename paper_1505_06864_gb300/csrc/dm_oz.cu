@@ -304,16 +304,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------- slicing
-// Row slices of one float64 m x m block (left operands): exps[r] = e with
-// |v| < 2^e for the row's largest |v|, slice s element (r, k) at
-// (q * 9 + s) m^2 + r m + k.  One warp per row, eight consecutive columns per
-// lane (m % 8 == 0).
-__device__ __forceinline__ void slice_rows_block(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                                 long long qdst, int* __restrict__ exps, int m) {
+// A CTA slices one group of 32 rows (left operands) or 32 columns (right
+// operands) of one float64 m x m block; a block takes ceil(m / 32) CTAs.
+
+// Row slices (left operands): exps[r] = e with |v| < 2^e for the row's
+// largest |v|; slice s element (r, k) at (q * 9 + s) m^2 + r m + k.  One
+// warp per row, eight consecutive columns per lane (m % 8 == 0).
+__device__ __forceinline__ void slice_rows_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 long long qdst, int* __restrict__ exps, int m, int g) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
-  for (int r = warp; r < m; r += nw) {
+  const int rend = min(m, 32 * g + 32);
+  for (int r = 32 * g + warp; r < rend; r += nw) {
     uint32_t hmax = 0;
     for (int c = lane; c < m; c += 32) hmax = max(hmax, (uint32_t)(bits[(long long)r * m + c] >> 32) & 0x7fffffffu);
 #pragma unroll
@@ -338,55 +341,71 @@ __device__ __forceinline__ void slice_rows_block(const double* __restrict__ src,
 }
 
 // Column slices, transposed (right operands): exps[n] for column n, slice s
-// element (n, k) = digit s of src[k][n] at (q * 9 + s) m^2 + n m + k.
-// Column maxima first, then 32 x 32 tiles through shared memory.
-__device__ __forceinline__ void slice_cols_block(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                                 long long qdst, int* __restrict__ exps, int m, int* s_exp,
-                                                 unsigned long long (*tile)[33]) {
+// element (n, k) = digit s of src[k][n] at (q * 9 + s) m^2 + n m + k.  The
+// group's 32 column maxima first (eight warps over the rows), then 32 x 32
+// tiles through shared memory; a thread writes four consecutive k of one n
+// per slice (8-byte stores).  256 threads.
+__device__ __forceinline__ void slice_cols_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 long long qdst, int* __restrict__ exps, int m, int g,
+                                                 uint32_t (*red)[32], int* s_e, unsigned long long (*tile)[33]) {
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
-  for (int n = threadIdx.x; n < m; n += blockDim.x) {
-    uint32_t hmax = 0;
-    for (int k = 0; k < m; ++k) hmax = max(hmax, (uint32_t)(bits[(long long)k * m + n] >> 32) & 0x7fffffffu);
-    const int e = scale_exponent(hmax);
-    s_exp[n] = e;
-    exps[qdst * m + n] = e;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = 32 * g + lane;
+  uint32_t hmax = 0;
+  if (n < m)
+    for (int k = warp; k < m; k += 8) hmax = max(hmax, (uint32_t)(bits[(long long)k * m + n] >> 32) & 0x7fffffffu);
+  red[warp][lane] = hmax;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t h = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) h = max(h, red[w][lane]);
+    const int e = scale_exponent(h);
+    s_e[lane] = e;
+    if (n < m) exps[qdst * m + n] = e;
   }
   __syncthreads();
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
-  for (int k0 = 0; k0 < m; k0 += 32)
-    for (int n0 = 0; n0 < m; n0 += 32) {
-      for (int y = ty; y < 32; y += ny) {
-        const int k = k0 + y, n = n0 + tx;
-        tile[y][tx] = (k < m && n < m) ? bits[(long long)k * m + n] : 0ull;
-      }
-      __syncthreads();
-      for (int y = ty; y < 32; y += ny) {
-        const int n = n0 + y, k = k0 + tx;  // output row n, column k = tile[tx][y]
-        if (n < m && k < m) {
-          uint32_t q[S];
-          digits9(tile[tx][y], s_exp[n], q);
-#pragma unroll
-          for (int sl = 0; sl < S; ++sl)
-            dst[(qdst * S + sl) * mm + (long long)n * m + k] = __ushort_as_bfloat16((unsigned short)(q[sl] >> 16));
-        }
-      }
-      __syncthreads();
+  const int nl = threadIdx.x >> 3, kq = (threadIdx.x & 7) * 4;
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    for (int y = warp; y < 32; y += 8) {
+      const int k = k0 + y;
+      tile[y][lane] = (k < m && n < m) ? bits[(long long)k * m + n] : 0ull;
     }
+    __syncthreads();
+    const int nn = 32 * g + nl, k = k0 + kq;
+    if (nn < m && k < m) {  // m % 8 == 0: four consecutive k are all inside
+      uint32_t q[4][S];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) digits9(tile[kq + u][nl], s_e[nl], q[u]);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        uint2 w;
+        w.x = (q[0][sl] >> 16) | (q[1][sl] & 0xffff0000u);
+        w.y = (q[2][sl] >> 16) | (q[3][sl] & 0xffff0000u);
+        *reinterpret_cast<uint2*>(dst + (qdst * S + sl) * mm + (long long)nn * m + k) = w;
+      }
+    }
+    __syncthreads();
+  }
 }
 
-// Slices of every block of a level's array (A as rows, C as transposed columns).
+// Slices of every block of a level's array (A as rows, C as transposed
+// columns): blockIdx.x = block * groups + group, looping past the grid.
 template <bool COLS>
 __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__ src, int nblocks, int m,
                                                       __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
-  __shared__ int s_exp[kMaxMTensor];
+  __shared__ uint32_t red[8][32];
+  __shared__ int s_e[32];
   __shared__ unsigned long long tile[32][33];
   const long long mm = (long long)m * m;
-  for (int q = blockIdx.x; q < nblocks; q += gridDim.x) {
+  const int groups = (m + 31) / 32;
+  for (long long i = blockIdx.x; i < (long long)nblocks * groups; i += gridDim.x) {
+    const int q = (int)(i / groups), g = (int)(i - (long long)q * groups);
     if (COLS)
-      slice_cols_block(src + q * mm, dst, q, exps, m, s_exp, tile);
+      slice_cols_group(src + q * mm, dst, q, exps, m, g, red, s_e, tile);
     else
-      slice_rows_block(src + q * mm, dst, q, exps, m);
+      slice_rows_group(src + q * mm, dst, q, exps, m, g);
     __syncthreads();
   }
 }
@@ -400,10 +419,12 @@ __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__
 // Several per-subsystem slicing jobs in one launch (blockIdx.y = job).
 __global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restrict__ parts, int step, int m,
                                                        OzSliceJobs jobs) {
-  __shared__ int s_exp[kMaxMTensor];
+  __shared__ uint32_t red[8][32];
+  __shared__ int s_e[32];
   __shared__ unsigned long long tile[32][33];
   const OzSliceJob& jb = jobs.job[blockIdx.y];
-  const int q = blockIdx.x;
+  const int groups = (m + 31) / 32;
+  const int q = blockIdx.x / groups, g = blockIdx.x - q * groups;
   const PartDesc p = parts[q];
   const long long mm = (long long)m * m;
   const bool hl = (p.flags & HAS_LEFT) != 0, hr = (p.flags & HAS_RIGHT) != 0;
@@ -424,9 +445,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restric
   if (!act) return;
   __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(jb.dst);
   if (jb.kind == 0 || jb.kind == 1)
-    slice_rows_block(jb.src + sblk * mm, dst, dq, jb.exps, m);
+    slice_rows_group(jb.src + sblk * mm, dst, dq, jb.exps, m, g);
   else
-    slice_cols_block(jb.src + sblk * mm, dst, dq, jb.exps, m, s_exp, tile);
+    slice_cols_group(jb.src + sblk * mm, dst, dq, jb.exps, m, g, red, s_e, tile);
 }
 
 }  // namespace oz
@@ -475,7 +496,8 @@ int oz_box_rows_right() { return oz::NT; }
 
 void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st) {
   if (nblocks <= 0) return;
-  const int grid = std::min(nblocks, 152 * 8);
+  const long long work = (long long)nblocks * ((m + 31) / 32);
+  const int grid = (int)std::min<long long>(work, 152LL * 16);
   if (cols)
     oz::k_oz_slice_all<true><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps);
   else
@@ -485,7 +507,7 @@ void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void*
 void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
                           cudaStream_t st) {
   if (nparts <= 0 || njobs <= 0) return;
-  oz::k_oz_slice_jobs<<<dim3(nparts, njobs), 256, 0, st>>>(parts, step, m, jobs);
+  oz::k_oz_slice_jobs<<<dim3(nparts * ((m + 31) / 32), njobs), 256, 0, st>>>(parts, step, m, jobs);
 }
 
 void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
