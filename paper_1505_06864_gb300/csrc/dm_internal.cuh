@@ -146,7 +146,7 @@ struct OzOut {
 };
 bool oz_eligible(int m);
 int oz_slice_blocks_bytes(int m);
-bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out);
+bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out, int kdim = 0);
 int oz_box_rows_left();
 int oz_box_rows_right();
 void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st);
@@ -162,7 +162,15 @@ struct OzSliceJobs {
 void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
                           cudaStream_t st);
 void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
-                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st);
+                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st,
+                    int aux = 0);
+// Blocked Gauss-Jordan inversion with the rank-32 updates as digit-sliced
+// tensor-core products; maps2 = the panel-slice maps (U with 128-row boxes,
+// V with 48-row boxes), piv [nparts][m], Us / Vs [nparts][9][m][32] bf16,
+// Uexp / Vexp [nparts][m].
+void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
+                       void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
+                       cudaStream_t st);
 int tc2_ntile(int m);
 bool tc2_make_map(int mode, const void* base, long long blocks, int m, int box_rows, void* out);
 int tc2_map_bytes();

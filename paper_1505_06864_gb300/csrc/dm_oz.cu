@@ -32,6 +32,7 @@
 // epilogue combines the accumulators in 64-bit integers and scales once in
 // float64 (GB300's float64 pipe is narrow).  Operand slices of results are
 // made by separate slicing launches, which see whole rows and columns.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -89,11 +90,15 @@ namespace oz {
 // KIND 0: launch A, 1: launch B (forward step `step`), 2: backward step
 // `step`.  blockIdx.y = subsystem; blockIdx.x = ((2 * M-tile + product) *
 // ntn + N-tile).  Exponent arrays: [block][m] ints, indexed like the slices.
+// KIND 3: the trailing update of panel `step` (columns K = [32 step, 32 step
+// + 32)) of the blocked Gauss-Jordan inversion of block row `aux`:
+// M[:, J] = (M[:, J] with the rows K zeroed) + U V, U the eliminated panel,
+// V = M[K, J] before the update (both as slices, K = 32), J the other columns.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_oz_step(const PartDesc* __restrict__ parts, int step, int m, int ntn, OzOut out, const int* __restrict__ lexp,
-              const int* __restrict__ rexp0, const int* __restrict__ rexp1, int* __restrict__ errflag,
-              const __grid_constant__ OzMaps maps) {
+    k_oz_step(const PartDesc* __restrict__ parts, int step, int aux, int m, int ntn, OzOut out,
+              const int* __restrict__ lexp, const int* __restrict__ rexp0, const int* __restrict__ rexp1,
+              int* __restrict__ errflag, const __grid_constant__ OzMaps maps) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t full[kStages], empty[kStages], accb;
   __shared__ uint32_t tmem_slot;
@@ -110,15 +115,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (KIND == 1) {
     t = step;
     act = t < p.L - 1 && (j == 0 || (p.flags & HAS_LEFT) != 0);
-  } else {
+  } else if (KIND == 2) {
     t = p.L - 2 - step;
     act = t >= 0 && (j == 0 ? (p.flags & HAS_LEFT) != 0 : (p.flags & HAS_RIGHT) != 0);
+  } else {
+    t = aux;
+    act = t < p.L && j == 0;
   }
   if (!act) return;
   const long long mm = (long long)m * m;
   const int b0 = (int)(p.blk / mm);
   int zl, zr;
-  if (KIND == 0) {
+  if (KIND == 3) {
+    zl = pidx;  // U slices (rolling)
+    zr = pidx;  // V^T slices (rolling)
+  } else if (KIND == 0) {
     zl = pidx;                   // G_t slices (rolling)
     zr = j == 0 ? b0 + t : pidx;  // C_t^T (all blocks) / Y_t^T (rolling)
   } else if (KIND == 1) {
@@ -153,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const int nslab = (m + KS - 1) / KS;
+  const int nslab = KIND == 3 ? 1 : (m + KS - 1) / KS;
   constexpr uint32_t tx = (uint32_t)(S * (MT + NT) * ROWB);
 
   if (warp == 0 && lane == 0) {
@@ -260,15 +271,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       // row-major float64 results: lane = (row parity, column), 16 row pairs;
       // the loads an update needs are gathered before any store
       const int cl = lane & 15, r0 = lane >> 4, n = tn * NT + ch + cl;
-      if (n < m) {
-        const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0;
+      const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
+      const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
+      if (n < m && outside) {
+        const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3;
         double in[16];
-        if (rmw || dnext) {
-          const double* src = rmw ? out.ZL + o : out.B + o + mm;
+        if (rmw || dnext || gj) {
+          const double* src = rmw ? out.ZL + o : (gj ? out.G + o : out.B + o + mm);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int rr = rbase + r0 + 2 * i;
-            in[i] = rr < m ? src[(long long)rr * m + n] : 0.0;
+            in[i] = (rr < m && !(gj && rr >= k0 && rr < k0 + 32)) ? src[(long long)rr * m + n] : 0.0;
           }
         }
 #pragma unroll
@@ -286,6 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             out.Y[(long long)pidx * mm + e] = -w;         // Y_{t+1} = -A_{t+1} Bcal_t
           } else if (rmw) {
             out.ZL[o + e] = in[i] - w;                    // ZL_t -= Acal_t ZL_{t+1}
+          } else if (gj) {
+            out.G[o + e] = in[i] + w;                     // Gauss-Jordan trailing update
           } else {
             out.ZR[o + e] = -w;                           // ZR_t = -Acal_t ZR_{t+1}
           }
@@ -416,6 +431,238 @@ __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__
 //   4 ZR_{L-1} columns (last row, right spike) -> slot;  5 Y_{t+1} columns -> rolling (q);
 //   6 ZL_t columns, backward step;        7 ZR_t columns, backward step;
 //   8 Y_0 = A_first columns -> rolling (q), at the start of a factorisation.
+// ---------------------------------------------------------------- blocked Gauss-Jordan inversion
+// The float64 block inverse G_t = D_t^{-1} with partial pivoting (the
+// paper's inversion, Section 4; Gauss-Jordan as in the library's other
+// inverses), blocked by panels of 32 columns so that 15/16 of its float64
+// multiply-adds (the rank-32 trailing updates) run on the tensor cores as
+// digit-sliced products (KIND 3 above).  For panel K = [k0, k0 + 32):
+//   1. k_gj_panel (float64, one CTA per block, a thread per row holding the
+//      panel's 32 values): for each k in K, the pivot row r = argmax_{i >= k}
+//      |M[i][k]| (ties to the lowest row) is exchanged with row k (whole rows),
+//      then in-place Gauss-Jordan restricted to the panel's columns: row k
+//      scaled by 1/M[k][k] with 1/M[k][k] in column k, every other row i
+//      minus M[i][k] times row k with -M[i][k]/M[k][k] in column k.  The panel
+//      then holds U = [W; -M_RK W] (W = M_KK^{-1}); the kernel writes U's row
+//      slices and the column slices of V = M[K, J] (the pivot rows outside K).
+//   2. k_oz_step<3>: M[:, J] = (M[:, J], rows K zeroed) + U V.
+// After the last panel, k_gj_unscramble undoes the row exchanges on the
+// columns (column c of the working matrix is column inv_idx[c] of D^{-1}).
+__global__ void __launch_bounds__(256) k_gj_copy_b0(const PartDesc* __restrict__ parts, int m,
+                                                    const double* __restrict__ B, double* __restrict__ G) {
+  const PartDesc p = parts[blockIdx.x];
+  const long long mm = (long long)m * m;
+  for (long long e = threadIdx.x; e < mm; e += blockDim.x) G[p.blk + e] = B[p.blk + e];
+}
+
+// One panel, one cluster of kGjCS CTAs per block: CTA `rank` holds rows
+// [rank R, rank R + R) (R = ceil(m / kGjCS)), a thread per row with the
+// panel's 32 values in registers.  Per pivot: each CTA finds its best
+// candidate row and publishes it (and row k, by its owner) in shared memory;
+// one cluster barrier; every CTA reads the kGjCS candidates and the two rows
+// through distributed shared memory, and updates its own rows.  Rank 0
+// exchanges the rows outside the panel in global memory and records the pivot.
+constexpr int kGjCS = 4;
+constexpr int kGjThreads = 64;
+__global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restrict__ parts, int t, int m, int panel,
+                                                        double* __restrict__ G, int* __restrict__ piv,
+                                                        __nv_bfloat16* __restrict__ Us, int* __restrict__ Uexp,
+                                                        __nv_bfloat16* __restrict__ Vs, int* __restrict__ Vexp,
+                                                        int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double cand_row[2][32], rowk_buf[2][32], cand_val[2];
+  __shared__ int cand_idx[2];
+  __shared__ double wv[2], prow[32], xrow[32], sprow[32], s_inv;
+  __shared__ int wi[2], s_r, s_bad;
+  const int rank = (int)cl.block_rank();
+  const int q = blockIdx.x / kGjCS;
+  const PartDesc p = parts[q];
+  if (t >= p.L) return;  // the same for every CTA of the cluster
+  const long long mm = (long long)m * m;
+  double* M = G + p.blk + (long long)t * mm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = (m + kGjCS - 1) / kGjCS, i = rank * R + tid;
+  const bool valid = tid < R && i < m;
+  const int k0 = 32 * panel, kw = min(32, m - k0);
+  double reg[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) reg[c] = (valid && c < kw) ? M[(long long)i * m + k0 + c] : 0.0;
+  if (tid == 0) s_bad = 0;
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    if (kk >= kw) break;
+    const int k = k0 + kk, buf = kk & 1;
+    // this CTA's candidate: rows i >= k, largest modulus, ties to the lowest row
+    double v = (valid && i >= k) ? fabs(reg[kk]) : -1.0;
+    int vi = valid ? i : m;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, v, off);
+      const int oi = __shfl_down_sync(0xffffffffu, vi, off);
+      if (ov > v || (ov == v && oi < vi)) v = ov, vi = oi;
+    }
+    if (lane == 0) wv[warp] = v, wi[warp] = vi;
+    __syncthreads();
+    if (tid == 0) {
+      const bool second = wv[1] > wv[0] || (wv[1] == wv[0] && wi[1] < wi[0]);
+      cand_val[buf] = second ? wv[1] : wv[0];
+      cand_idx[buf] = second ? wi[1] : wi[0];
+    }
+    __syncthreads();
+    if (valid && i == cand_idx[buf])
+#pragma unroll
+      for (int c = 0; c < 32; ++c) cand_row[buf][c] = reg[c];
+    if (valid && i == k)
+#pragma unroll
+      for (int c = 0; c < 32; ++c) rowk_buf[buf][c] = reg[c];
+    cl.sync();  // every CTA's candidate and row k are published
+    if (tid == 0) {
+      double bv = -2.0;
+      int bi = m, bo = 0;
+      for (int rr = 0; rr < kGjCS; ++rr) {
+        const double cv = *cl.map_shared_rank(&cand_val[buf], rr);
+        const int ci = *cl.map_shared_rank(&cand_idx[buf], rr);
+        if (cv > bv || (cv == bv && ci < bi)) bv = cv, bi = ci, bo = rr;
+      }
+      s_r = bi;
+      (void)bo;
+    }
+    __syncthreads();
+    const int r = s_r, owner_r = r / R, owner_k = k / R;
+    if (tid < 32) {
+      prow[tid] = cl.map_shared_rank(&cand_row[buf][0], owner_r)[tid];
+      xrow[tid] = cl.map_shared_rank(&rowk_buf[buf][0], owner_k)[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double inv = 1.0 / prow[kk];
+      if (!(fabs(prow[kk]) > 0.0) || !isfinite(inv)) {
+        inv = 0.0;
+        if (rank == owner_k) s_bad = 1;
+      }
+      s_inv = inv;
+    }
+    __syncthreads();
+    if (tid < 32) sprow[tid] = tid == kk ? s_inv : prow[tid] * s_inv;  // the scaled pivot row
+    if (rank == 0) {
+      if (r != k)
+        for (int c = tid; c < m; c += kGjThreads)
+          if (c < k0 || c >= k0 + kw) {
+            const double a = M[(long long)k * m + c];
+            M[(long long)k * m + c] = M[(long long)r * m + c];
+            M[(long long)r * m + c] = a;
+          }
+      if (tid == 0) piv[(long long)q * m + k] = r;
+    }
+    __syncthreads();
+    if (valid) {
+      if (i == k) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) reg[c] = sprow[c];
+      } else {
+        if (i == r && r != k)
+#pragma unroll
+          for (int c = 0; c < 32; ++c) reg[c] = xrow[c];  // row r takes the old row k
+        const double f = reg[kk];
+        reg[kk] = 0.0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) reg[c] = fma(-f, sprow[c], reg[c]);
+      }
+    }
+  }
+  cl.sync();  // rank 0's exchanges outside the panel are visible to the cluster
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < kw) M[(long long)i * m + k0 + c] = reg[c];
+    // row slices of U (scale per row over the panel's 32 values)
+    uint32_t hmax = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) hmax = max(hmax, (uint32_t)(__double_as_longlong(reg[c]) >> 32) & 0x7fffffffu);
+    const int e = scale_exponent(hmax);
+    Uexp[(long long)q * m + i] = e;
+    __nv_bfloat16* u = Us + (long long)q * S * m * 32 + (long long)i * 32;
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+      uint32_t d[8][S];
+#pragma unroll
+      for (int uu = 0; uu < 8; ++uu) digits9((unsigned long long)__double_as_longlong(reg[c0 + uu]), e, d[uu]);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        uint4 w;
+        w.x = (d[0][sl] >> 16) | (d[1][sl] & 0xffff0000u);
+        w.y = (d[2][sl] >> 16) | (d[3][sl] & 0xffff0000u);
+        w.z = (d[4][sl] >> 16) | (d[5][sl] & 0xffff0000u);
+        w.w = (d[6][sl] >> 16) | (d[7][sl] & 0xffff0000u);
+        *reinterpret_cast<uint4*>(u + (long long)sl * m * 32 + c0) = w;
+      }
+    }
+  }
+  // column slices of V = the pivot rows K outside the panel (zero inside it),
+  // transposed: row j of the copy holds V[0..31][j]; a thread per column,
+  // the columns shared among the cluster's CTAs
+  for (int jcol = rank * kGjThreads + tid; jcol < m; jcol += kGjCS * kGjThreads) {
+    const bool inK = jcol >= k0 && jcol < k0 + kw;
+    double vv[32];
+    uint32_t hmax = 0;
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      vv[kk] = (!inK && kk < kw) ? M[(long long)(k0 + kk) * m + jcol] : 0.0;
+      hmax = max(hmax, (uint32_t)(__double_as_longlong(vv[kk]) >> 32) & 0x7fffffffu);
+    }
+    const int e = scale_exponent(hmax);
+    Vexp[(long long)q * m + jcol] = e;
+    __nv_bfloat16* vdst = Vs + (long long)q * S * m * 32 + (long long)jcol * 32;
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+      uint32_t d[8][S];
+#pragma unroll
+      for (int uu = 0; uu < 8; ++uu) digits9((unsigned long long)__double_as_longlong(vv[c0 + uu]), e, d[uu]);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        uint4 w;
+        w.x = (d[0][sl] >> 16) | (d[1][sl] & 0xffff0000u);
+        w.y = (d[2][sl] >> 16) | (d[3][sl] & 0xffff0000u);
+        w.z = (d[4][sl] >> 16) | (d[5][sl] & 0xffff0000u);
+        w.w = (d[6][sl] >> 16) | (d[7][sl] & 0xffff0000u);
+        *reinterpret_cast<uint4*>(vdst + (long long)sl * m * 32 + c0) = w;
+      }
+    }
+  }
+  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+__global__ void __launch_bounds__(256) k_gj_unscramble(const PartDesc* __restrict__ parts, int t, int m,
+                                                       double* __restrict__ G, const int* __restrict__ piv) {
+  __shared__ int idx[kMaxMTensor], inv_idx[kMaxMTensor];
+  __shared__ double rowbuf[8][kMaxMTensor];
+  const int q = blockIdx.x;
+  const PartDesc p = parts[q];
+  if (t >= p.L) return;
+  const long long mm = (long long)m * m;
+  double* M = G + p.blk + (long long)t * mm;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < m; ++c) idx[c] = c;
+    for (int k = m - 1; k >= 0; --k) {
+      const int r = piv[(long long)q * m + k];
+      const int tmp = idx[k];
+      idx[k] = idx[r];
+      idx[r] = tmp;
+    }
+    for (int c = 0; c < m; ++c) inv_idx[idx[c]] = c;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < m; r += 8) {
+    for (int c = lane; c < m; c += 32) rowbuf[warp][c] = M[(long long)r * m + c];
+    __syncwarp();
+    for (int c = lane; c < m; c += 32) M[(long long)r * m + inv_idx[c]] = rowbuf[warp][c];
+    __syncwarp();
+  }
+}
+
 // Several per-subsystem slicing jobs in one launch (blockIdx.y = job).
 __global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restrict__ parts, int step, int m,
                                                        OzSliceJobs jobs) {
@@ -477,12 +724,15 @@ bool oz_eligible(int m) { return m >= 8 && m <= kMaxMTensor && m % 8 == 0; }
 
 int oz_slice_blocks_bytes(int m) { return oz::S * m * m * 2; }
 
-// 4-D map [block][slice][row][column] of a slice array, box 32 x box_rows x 9 x 1.
-bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out) {
+// 4-D map [block][slice][row][column] of a slice array (rows x kdim per
+// slice; kdim = m for the sweeps' blocks, 32 for the inversion's panels),
+// box 32 x box_rows x 9 x 1.
+bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out, int kdim) {
   EncodeFn enc = oz_encoder();
+  if (kdim <= 0) kdim = m;
   if (!enc || blocks <= 0 || !oz_eligible(m)) return false;
-  cuuint64_t dims[4] = {(cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)oz::S, (cuuint64_t)blocks};
-  cuuint64_t strides[3] = {(cuuint64_t)m * 2, (cuuint64_t)m * m * 2, (cuuint64_t)oz::S * m * m * 2};
+  cuuint64_t dims[4] = {(cuuint64_t)kdim, (cuuint64_t)m, (cuuint64_t)oz::S, (cuuint64_t)blocks};
+  cuuint64_t strides[3] = {(cuuint64_t)kdim * 2, (cuuint64_t)m * kdim * 2, (cuuint64_t)oz::S * m * kdim * 2};
   cuuint32_t box[4] = {(cuuint32_t)oz::KS, (cuuint32_t)box_rows, (cuuint32_t)oz::S, 1u};
   cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   CUresult r = enc(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims,
@@ -510,8 +760,40 @@ void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, co
   oz::k_oz_slice_jobs<<<dim3(nparts * ((m + 31) / 32), njobs), 256, 0, st>>>(parts, step, m, jobs);
 }
 
+// The blocked Gauss-Jordan inversion of block row t of every active
+// subsystem (in place in G; t = 0 starts from B_0).
+void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
+                       void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
+                       cudaStream_t st) {
+  if (nparts <= 0) return;
+  if (t == 0) oz::k_gj_copy_b0<<<nparts, 256, 0, st>>>(parts, m, B, G);
+  OzOut out{nullptr, G, nullptr, nullptr, nullptr, nullptr};
+  unsigned char maps3[3 * 128];
+  std::memcpy(maps3, maps2, 2 * 128);
+  std::memcpy(maps3 + 2 * 128, static_cast<const unsigned char*>(maps2) + 128, 128);
+  const int npan = (m + 31) / 32;
+  for (int pnl = 0; pnl < npan; ++pnl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nparts * oz::kGjCS);
+    cfg.blockDim = dim3(oz::kGjThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = oz::kGjCS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, oz::k_gj_panel, parts, t, m, pnl, G, piv, static_cast<__nv_bfloat16*>(Us), Uexp,
+                       static_cast<__nv_bfloat16*>(Vs), Vexp, status);
+    if (m > 32) launch_oz_step(3, parts, nparts, pnl, m, out, Uexp, Vexp, Vexp, maps3, errflag, st, t);
+  }
+  oz::k_gj_unscramble<<<nparts, 256, 0, st>>>(parts, t, m, G, piv);
+}
+
 void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
-                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st) {
+                    const int* rexp0, const int* rexp1, const void* maps3, int* errflag, cudaStream_t st, int aux) {
   if (nparts <= 0) return;
   OzMaps mp;
   std::memcpy(&mp, maps3, sizeof mp);
@@ -524,12 +806,13 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
       cudaFuncSetAttribute(oz::k_oz_step<KIND_>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM);        \
       set = true;                                                                                                \
     }                                                                                                            \
-    oz::k_oz_step<KIND_><<<grid, oz::kThreads, oz::SMEM, st>>>(parts, step, m, ntn, out, lexp, rexp0, rexp1,     \
-                                                               errflag, mp);                                     \
+    oz::k_oz_step<KIND_><<<grid, oz::kThreads, oz::SMEM, st>>>(parts, step, aux, m, ntn, out, lexp, rexp0,      \
+                                                               rexp1, errflag, mp);                              \
   } while (0)
   if (kind == 0) DM_OZ(0);
   else if (kind == 1) DM_OZ(1);
-  else DM_OZ(2);
+  else if (kind == 2) DM_OZ(2);
+  else DM_OZ(3);
 #undef DM_OZ
 }
 

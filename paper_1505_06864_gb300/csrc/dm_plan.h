@@ -100,6 +100,12 @@ struct OzLevel {
   double* Y = nullptr;
   // tensor maps: left G, A, Acal; right CT, YT, AcalT, ZLT, ZRT
   alignas(64) unsigned char maps[8][128];
+  // blocked Gauss-Jordan inversion: panel slices U, V ([subsystem][9][m][32]),
+  // their exponents, the pivot rows, and the two panel maps
+  bool gj = false;
+  void *U = nullptr, *V = nullptr;
+  int *eU = nullptr, *eV = nullptr, *piv = nullptr;
+  alignas(64) unsigned char gj_maps[2][128];
 };
 
 // One level of the recursion: a set of independent systems, each split into

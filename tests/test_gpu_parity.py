@@ -563,3 +563,44 @@ def test_fp64_sliced_products_conditioned_blocks(dm):
     for P, lv in ((1, 1), (6, 1), (15, 2)):
         x, rel, _ = solve(dm, s, P, lv)
         check(x, xt, 1e-11)
+
+
+@pytest.mark.parametrize("N,m,r,P,levels", [(64, 16, 1, 4, 1), (40, 64, 2, 6, 2), (12, 256, 2, 3, 1),
+                                            (30, 40, 3, 5, 1), (20, 200, 1, 4, 1)])
+def test_fp64_blocked_inverse(dm, monkeypatch, N, m, r, P, levels):
+    """The float64 block inverse by panels of 32 columns whose rank-32 updates
+    run as digit-sliced tensor-core products (the default on sliced levels)
+    and the column-by-column cluster inverse (DM_FP64_INVERSE=cluster): both
+    against the oracle and against each other, on dominant and conditioned
+    blocks (partial pivoting exercised), m not a multiple of 32 included."""
+    for gen in ("dominant", "conditioned"):
+        s = (w.dominant_system(N, m, r, 900 + N) if gen == "dominant"
+             else w.conditioned_system(N, m, r, 901 + N, cond=1e3))
+        xs = {}
+        for mode in ("blocked", "cluster"):
+            monkeypatch.setenv("DM_FP64_INVERSE", mode)
+            x, rel, info = solve(dm, s, P, levels)
+            assert rel < 1e-13
+            xs[mode] = x
+        monkeypatch.delenv("DM_FP64_INVERSE")
+        xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
+        tol = TOL64 if gen == "dominant" else 1e-10
+        check(xs["blocked"], xo, tol)
+        check(xs["cluster"], xo, tol)
+
+
+def test_singular_block_reported_blocked_inverse(dm):
+    """A zero Schur complement on a sliced level (m = 16): the blocked
+    inversion reports DM_ESINGULAR with the block row, like the cluster one."""
+    s = w.dominant_system(6, 16, 1, 1)
+    s.B[3] = 0.0
+    s.A[3] = 0.0
+    s.C[2] = 0.0
+    plan = dm.dm_plan(6, 16, 1, 1, 1, "fp64")
+    try:
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_factor(plan, s.A, s.B, s.C)
+        assert e.value.code == dm.DM_ESINGULAR
+        assert "block row 3" in str(e.value)
+    finally:
+        dm.dm_destroy(plan)
