@@ -437,14 +437,15 @@ __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__
 // inverses), blocked by panels of 32 columns so that 15/16 of its float64
 // multiply-adds (the rank-32 trailing updates) run on the tensor cores as
 // digit-sliced products (KIND 3 above).  For panel K = [k0, k0 + 32):
-//   1. k_gj_panel (float64, one CTA per block, a thread per row holding the
-//      panel's 32 values): for each k in K, the pivot row r = argmax_{i >= k}
-//      |M[i][k]| (ties to the lowest row) is exchanged with row k (whole rows),
-//      then in-place Gauss-Jordan restricted to the panel's columns: row k
-//      scaled by 1/M[k][k] with 1/M[k][k] in column k, every other row i
-//      minus M[i][k] times row k with -M[i][k]/M[k][k] in column k.  The panel
-//      then holds U = [W; -M_RK W] (W = M_KK^{-1}); the kernel writes U's row
-//      slices and the column slices of V = M[K, J] (the pivot rows outside K).
+//   1. k_gj_panel (float64, a cluster of CTAs per block, a thread per row
+//      holding the panel's 32 values): for each k in K, the pivot row r =
+//      argmax_{i >= k} |M[i][k]| (ties to the lowest row) is exchanged with
+//      row k, then in-place Gauss-Jordan restricted to the panel's columns:
+//      row k scaled by 1/M[k][k] with 1/M[k][k] in column k, every other row
+//      i minus M[i][k] times row k with -M[i][k]/M[k][k] in column k.  The
+//      panel then holds U = [W; -M_RK W] (W = M_KK^{-1}); the kernel applies
+//      the row exchanges to the other columns and writes U's row slices and
+//      the column slices of V = M[K, J] (the pivot rows outside K).
 //   2. k_oz_step<3>: M[:, J] = (M[:, J], rows K zeroed) + U V.
 // After the last panel, k_gj_unscramble undoes the row exchanges on the
 // columns (column c of the working matrix is column inv_idx[c] of D^{-1}).
@@ -457,13 +458,29 @@ __global__ void __launch_bounds__(256) k_gj_copy_b0(const PartDesc* __restrict__
 
 // One panel, one cluster of kGjCS CTAs per block: CTA `rank` holds rows
 // [rank R, rank R + R) (R = ceil(m / kGjCS)), a thread per row with the
-// panel's 32 values in registers.  Per pivot: each CTA finds its best
-// candidate row and publishes it (and row k, by its owner) in shared memory;
-// one cluster barrier; every CTA reads the kGjCS candidates and the two rows
-// through distributed shared memory, and updates its own rows.  Rank 0
-// exchanges the rows outside the panel in global memory and records the pivot.
+// panel's 32 values in registers, rotated by one column per pivot (at pivot
+// kk, reg[c] is panel column (kk + c) mod 32, so the pivot column is always
+// reg[0] and the loop needs no unrolling; after 32 pivots the order is back).
+// Per pivot: each warp finds its best candidate row (a strict order: value,
+// then lowest row), its owner publishes the row in shared memory, and the
+// owner of row k publishes that row; one cluster barrier; every lane reads
+// the cluster's candidates and element `lane` of every candidate row and of
+// row k through distributed shared memory (one round of independent loads),
+// picks the winner, and the rows are updated.  The float64 multiply-adds of
+// the rank-1 updates (32 per row and pivot) bound the kernel; nothing else is
+// on the float64 pipe.  The exchanges of rows outside the panel are applied
+// after the last pivot as one permutation (pivot rows are always taken from
+// rows >= k, so every row outside K that moves receives a row of K).
 constexpr int kGjCS = 4;
 constexpr int kGjThreads = 64;
+constexpr int kGjWarps = kGjThreads / 32;
+constexpr int kGjSlots = kGjCS * kGjWarps;  // candidates per pivot
+static_assert(kGjSlots <= 32, "one candidate per lane");
+
+__device__ __forceinline__ bool gj_before(double ov, int oi, double v, int vi) {
+  return ov > v || (ov == v && oi < vi);
+}
+
 __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restrict__ parts, int t, int m, int panel,
                                                         double* __restrict__ G, int* __restrict__ piv,
                                                         __nv_bfloat16* __restrict__ Us, int* __restrict__ Uexp,
@@ -471,10 +488,14 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
                                                         int* __restrict__ status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ double cand_row[2][32], rowk_buf[2][32], cand_val[2];
-  __shared__ int cand_idx[2];
-  __shared__ double wv[2], prow[32], xrow[32], sprow[32], s_inv;
-  __shared__ int wi[2], s_r, s_bad;
+  // published per pivot (double-buffered: a buffer is rewritten two pivots
+  // later, after a cluster barrier that every reader of it has passed)
+  __shared__ __align__(16) double crow[2][kGjWarps][32], krow[2][32];
+  __shared__ double cval[2][kGjWarps];
+  __shared__ int cidx[2][kGjWarps];
+  // this CTA's own
+  __shared__ __align__(16) double sprow[kGjWarps][32], xrow[kGjWarps][32];
+  __shared__ int piv_s[32], perm[kMaxMTensor];
   const int rank = (int)cl.block_rank();
   const int q = blockIdx.x / kGjCS;
   const PartDesc p = parts[q];
@@ -484,99 +505,112 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int R = (m + kGjCS - 1) / kGjCS, i = rank * R + tid;
   const bool valid = tid < R && i < m;
-  const int k0 = 32 * panel, kw = min(32, m - k0);
+  const int k0 = 32 * panel, kw = min(32, m - k0);  // kw % 8 == 0
   double reg[32];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) reg[c] = (valid && c < kw) ? M[(long long)i * m + k0 + c] : 0.0;
-  if (tid == 0) s_bad = 0;
-#pragma unroll
+  for (int c = 0; c < 32; c += 2) {
+    double2 v2 = make_double2(0.0, 0.0);
+    if (valid && c < kw) v2 = *reinterpret_cast<const double2*>(M + (long long)i * m + k0 + c);
+    reg[c] = v2.x;
+    reg[c + 1] = v2.y;
+  }
+  bool bad = false;
+#pragma unroll 1
   for (int kk = 0; kk < 32; ++kk) {
-    if (kk >= kw) break;
+    if (kk >= kw) {  // padding columns of a narrow last panel: rotate only
+      const double t0 = reg[0];
+#pragma unroll
+      for (int c = 0; c < 31; ++c) reg[c] = reg[c + 1];
+      reg[31] = t0;
+      continue;
+    }
     const int k = k0 + kk, buf = kk & 1;
-    // this CTA's candidate: rows i >= k, largest modulus, ties to the lowest row
-    double v = (valid && i >= k) ? fabs(reg[kk]) : -1.0;
-    int vi = valid ? i : m;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, v, off);
-      const int oi = __shfl_down_sync(0xffffffffu, vi, off);
-      if (ov > v || (ov == v && oi < vi)) v = ov, vi = oi;
+    // this warp's candidate; rows < k rank below every row >= k (NaN just
+    // above them), threads without a row below everything, indexes unique
+    double v = -2.0;
+    int vi = m + rank * kGjThreads + tid;
+    if (valid) {
+      vi = i;
+      if (i >= k) {
+        const double a = fabs(reg[0]);
+        v = a == a ? a : -0.5;
+      } else {
+        v = -1.0;
+      }
     }
-    if (lane == 0) wv[warp] = v, wi[warp] = vi;
-    __syncthreads();
-    if (tid == 0) {
-      const bool second = wv[1] > wv[0] || (wv[1] == wv[0] && wi[1] < wi[0]);
-      cand_val[buf] = second ? wv[1] : wv[0];
-      cand_idx[buf] = second ? wi[1] : wi[0];
-    }
-    __syncthreads();
-    if (valid && i == cand_idx[buf])
 #pragma unroll
-      for (int c = 0; c < 32; ++c) cand_row[buf][c] = reg[c];
+    for (int off = 16; off; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, vi, off);
+      if (gj_before(ov, oi, v, vi)) v = ov, vi = oi;
+    }
+    if (valid && i == vi)
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) *reinterpret_cast<double2*>(&crow[buf][warp][c]) = make_double2(reg[c], reg[c + 1]);
     if (valid && i == k)
 #pragma unroll
-      for (int c = 0; c < 32; ++c) rowk_buf[buf][c] = reg[c];
-    cl.sync();  // every CTA's candidate and row k are published
-    if (tid == 0) {
-      double bv = -2.0;
-      int bi = m, bo = 0;
-      for (int rr = 0; rr < kGjCS; ++rr) {
-        const double cv = *cl.map_shared_rank(&cand_val[buf], rr);
-        const int ci = *cl.map_shared_rank(&cand_idx[buf], rr);
-        if (cv > bv || (cv == bv && ci < bi)) bv = cv, bi = ci, bo = rr;
-      }
-      s_r = bi;
-      (void)bo;
+      for (int c = 0; c < 32; c += 2) *reinterpret_cast<double2*>(&krow[buf][c]) = make_double2(reg[c], reg[c + 1]);
+    if (lane == 0) cval[buf][warp] = v, cidx[buf][warp] = vi;
+    cl.sync();
+    // one round of independent remote loads: the candidates, element `lane`
+    // of every candidate row, element `lane` of row k
+    double cv = -3.0;
+    int ci = 0x7fffffff, cs = lane;
+    if (lane < kGjSlots) {
+      cv = *cl.map_shared_rank(&cval[buf][lane % kGjWarps], lane / kGjWarps);
+      ci = *cl.map_shared_rank(&cidx[buf][lane % kGjWarps], lane / kGjWarps);
     }
-    __syncthreads();
-    const int r = s_r, owner_r = r / R, owner_k = k / R;
-    if (tid < 32) {
-      prow[tid] = cl.map_shared_rank(&cand_row[buf][0], owner_r)[tid];
-      xrow[tid] = cl.map_shared_rank(&rowk_buf[buf][0], owner_k)[tid];
+    double rowv[kGjSlots];
+#pragma unroll
+    for (int s = 0; s < kGjSlots; ++s) rowv[s] = cl.map_shared_rank(&crow[buf][s % kGjWarps][0], s / kGjWarps)[lane];
+    const double xk = cl.map_shared_rank(&krow[buf][0], k / R)[lane];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, cv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, ci, off);
+      const int os = __shfl_xor_sync(0xffffffffu, cs, off);
+      if (gj_before(ov, oi, cv, ci)) cv = ov, ci = oi, cs = os;
     }
-    __syncthreads();
-    if (tid == 0) {
-      double inv = 1.0 / prow[kk];
-      if (!(fabs(prow[kk]) > 0.0) || !isfinite(inv)) {
-        inv = 0.0;
-        if (rank == owner_k) s_bad = 1;
-      }
-      s_inv = inv;
+    const int r = ci;
+    double prow = rowv[0];
+#pragma unroll
+    for (int s = 1; s < kGjSlots; ++s)
+      if (cs == s) prow = rowv[s];
+    const double p0 = __shfl_sync(0xffffffffu, prow, 0);  // the pivot (column kk is reg[0])
+    double inv = 0.0;
+    if (lane == 0) inv = 1.0 / p0;
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    if (!(fabs(p0) > 0.0) || !isfinite(inv) || !isfinite(p0)) {
+      inv = 0.0;
+      bad = true;
     }
-    __syncthreads();
-    if (tid < 32) sprow[tid] = tid == kk ? s_inv : prow[tid] * s_inv;  // the scaled pivot row
-    if (rank == 0) {
-      if (r != k)
-        for (int c = tid; c < m; c += kGjThreads)
-          if (c < k0 || c >= k0 + kw) {
-            const double a = M[(long long)k * m + c];
-            M[(long long)k * m + c] = M[(long long)r * m + c];
-            M[(long long)r * m + c] = a;
-          }
-      if (tid == 0) piv[(long long)q * m + k] = r;
-    }
-    __syncthreads();
+    sprow[warp][lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
+    xrow[warp][lane] = xk;                             // the old row k
+    if (tid == 0) piv_s[kk] = r;
+    if (rank == 0 && tid == 0) piv[(long long)q * m + k] = r;
+    __syncwarp();
     if (valid) {
+      const double* sp = sprow[warp];
       if (i == k) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) reg[c] = sprow[c];
+        for (int c = 0; c < 31; ++c) reg[c] = sp[c + 1];
+        reg[31] = sp[0];
       } else {
-        if (i == r && r != k)
+        if (i == r)  // row r takes the old row k
 #pragma unroll
-          for (int c = 0; c < 32; ++c) reg[c] = xrow[c];  // row r takes the old row k
-        const double f = reg[kk];
-        reg[kk] = 0.0;
+          for (int c = 0; c < 32; ++c) reg[c] = xrow[warp][c];
+        const double f = reg[0];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) reg[c] = fma(-f, sprow[c], reg[c]);
+        for (int c = 0; c < 31; ++c) reg[c] = fma(-f, sp[c + 1], reg[c + 1]);
+        reg[31] = -f * sp[0];
       }
     }
   }
-  cl.sync();  // rank 0's exchanges outside the panel are visible to the cluster
+  // the eliminated panel and the row slices of U (scale per row over its 32 values)
   if (valid) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < kw) M[(long long)i * m + k0 + c] = reg[c];
-    // row slices of U (scale per row over the panel's 32 values)
+    for (int c = 0; c < 32; c += 2)
+      if (c < kw) *reinterpret_cast<double2*>(M + (long long)i * m + k0 + c) = make_double2(reg[c], reg[c + 1]);
     uint32_t hmax = 0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) hmax = max(hmax, (uint32_t)(__double_as_longlong(reg[c]) >> 32) & 0x7fffffffu);
@@ -599,18 +633,35 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       }
     }
   }
-  // column slices of V = the pivot rows K outside the panel (zero inside it),
-  // transposed: row j of the copy holds V[0..31][j]; a thread per column,
-  // the columns shared among the cluster's CTAs
+  // net row permutation of the pivots: position x ends up holding row perm[x]
+  for (int c = tid; c < m; c += kGjThreads) perm[c] = c;
+  __syncthreads();
+  if (tid == 0)
+    for (int kk = 0; kk < kw; ++kk) {
+      const int a = k0 + kk, b = piv_s[kk], tmp = perm[a];
+      perm[a] = perm[b];
+      perm[b] = tmp;
+    }
+  __syncthreads();
+  // a thread per column outside the panel (shared among the cluster's CTAs):
+  // the column slices of V = the pivot rows (transposed: row j of the copy
+  // holds V[0..31][j]; zero inside the panel), then the rows outside K that
+  // took part in an exchange receive their rows of K (read before written:
+  // the V loads come first, from this thread's own column)
   for (int jcol = rank * kGjThreads + tid; jcol < m; jcol += kGjCS * kGjThreads) {
     const bool inK = jcol >= k0 && jcol < k0 + kw;
     double vv[32];
     uint32_t hmax = 0;
 #pragma unroll
     for (int kk = 0; kk < 32; ++kk) {
-      vv[kk] = (!inK && kk < kw) ? M[(long long)(k0 + kk) * m + jcol] : 0.0;
+      vv[kk] = (!inK && kk < kw) ? M[(long long)perm[k0 + kk] * m + jcol] : 0.0;
       hmax = max(hmax, (uint32_t)(__double_as_longlong(vv[kk]) >> 32) & 0x7fffffffu);
     }
+    if (!inK)
+      for (int kk = 0; kk < kw; ++kk) {
+        const int x = piv_s[kk];
+        if (x >= k0 + kw) M[(long long)x * m + jcol] = M[(long long)perm[x] * m + jcol];
+      }
     const int e = scale_exponent(hmax);
     Vexp[(long long)q * m + jcol] = e;
     __nv_bfloat16* vdst = Vs + (long long)q * S * m * 32 + (long long)jcol * 32;
@@ -630,7 +681,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       }
     }
   }
-  if (tid == 0 && s_bad) atomicMin(status + p.sys, p.row0 + t + 1);
+  if (rank == 0 && tid == 0 && bad) atomicMin(status + p.sys, p.row0 + t + 1);
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
