@@ -49,7 +49,7 @@ namespace dm {
 namespace oz {
 using namespace ptx;
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // warps 0, 1: TMA producer and MMA issuer; all 8: epilogue
 constexpr int MT = 128;          // rows per tile
 constexpr int NT = 48;           // columns per tile
 constexpr int KS = 32;           // K elements per stage (64-byte rows, 64-byte swizzle)
@@ -78,6 +78,31 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm,
 
 // 2^k as a float64 for -1022 <= k <= 1023.
 __device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// The integer value of an integer-valued float32 |v| < 2^22: v + 1.5 2^23
+// lies in [2^23, 2^24), where the float's low mantissa bits are v's.
+__device__ __forceinline__ int acc_int_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+
+// The integer value of an integer-valued float32 |v| < 2^24 from its bits.
+__device__ __forceinline__ int acc_int(uint32_t b) {
+  const uint32_t u = b & 0x7fffffffu;
+  const uint32_t sh = min(150u - min(u >> 23, 150u), 31u);  // 23 - exponent; 31 for zero
+  const int mag = (int)(((u & 0x7fffffu) | 0x800000u) >> sh);
+  const int sg = (int)b >> 31;
+  return (mag ^ sg) - sg;
+}
+
+// x 2^s as a float64, built from the bits: exact for |x| < 2^53 when the
+// result is a normal number (the caller checks the exponent range).
+__device__ __forceinline__ double i2d_scaled(long long x, int s) {
+  const unsigned long long sg = (unsigned long long)x & 0x8000000000000000ull;
+  const unsigned long long a = (unsigned long long)(x < 0 ? -x : x);
+  const int lz = __clzll(a);                        // >= 11 for a < 2^53
+  const unsigned long long mant = a << ((lz - 11) & 63);  // leading bit at 52
+  // the leading bit adds one to the exponent field
+  const unsigned long long ex = (unsigned long long)(1022 + 63 - lz + s);
+  return a == 0 ? 0.0 : __longlong_as_double((long long)(sg | ((ex << 52) + mant)));
+}
 
 }  // namespace oz
 
@@ -223,72 +248,81 @@ __global__ void __launch_bounds__(kThreads, 1)
   ok = __syncthreads_and(ok) && !err;
 
   if (ok) {
-    // Accumulators of this thread's row (tensor-memory lane) for 16 columns
-    // at a time, combined exactly: ih = sum_{d=2..6} acc_d 2^(6(6-d)),
-    // il = sum_{d=7..11} acc_d 2^(6(11-d)); value = (ih 2^30 + il) 2^(e_r + f_n - 66).
-    // Results are staged through a per-warp 32 x 33 float64 tile so that row-
-    // major writes are coalesced.
-    double* stg = reinterpret_cast<double*>(base) + warp * (32 * 17);
-    const int rbase = tm * MT + warp * 32, row = rbase + lane;
+    // Accumulators of this thread's row (tensor-memory lane) for 8 columns
+    // at a time.  Each acc_d is an integer-valued float below 2^24: its
+    // integer comes from the float's bits (float32 and integer operations),
+    // pairs P_j = acc_{2j+2} 64 + acc_{2j+3} are exact in 32 bits, and
+    //   hi = P_0 2^12 + P_1 (< 2^39),  lo = (P_2 2^12 + P_3) 2^12 + P_4 (< 2^53)
+    // give the sum exactly as hi 2^36 + lo.  Both become float64 from their
+    // bits with the scale 2^(e_r + f_n - 66) in the exponent, and one float64
+    // add rounds their sum once (GB300's float64 pipe is narrow: one add per
+    // entry instead of conversions and products).  Warps 0-3 and 4-7 share
+    // the tile's columns (a warp reaches only its own 32 lanes).  Results
+    // are staged through a per-warp 32 x 9 float64 tile so that row-major
+    // writes are coalesced.
+    const int quarter = warp & 3, half = warp >> 2;
+    double* stg = reinterpret_cast<double*>(base) + warp * (32 * 9);
+    const int rbase = tm * MT + quarter * 32, row = rbase + lane;
     const int er = row < m ? lexp[(long long)zl * m + row] : 0;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
     const long long o = p.blk + (long long)t * mm;
-    for (int ch = 0; ch < NT; ch += 16) {
-      long long ih[16], il[16];
-      uint32_t nanc = 0;
+    // acc_d below 2^22 for every d (then the float32 magic-number
+    // conversion is exact): K = 32, or K = m <= 112 (acc_d <= 9 K 63^2)
+    const bool small = KIND == 3 || m <= 112;
+    for (int ch = half * (NT / 2); ch < (half + 1) * (NT / 2); ch += 8) {
+      uint32_t r[NACC][8];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) ih[c] = il[c] = 0;
+      for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
+      tmem_wait_ld();
 #pragma unroll
-      for (int dd = 0; dd < NACC; ++dd) {
-        float v[16];
-        tmem_ld16(tl + (uint32_t)(dd * NT + ch), v);
+      for (int dd = 0; dd < NACC; ++dd) tmem_regs_after_wait(r[dd]);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          if (v[c] != v[c]) nanc |= 1u << c;
-          const long long a = (long long)__float2int_rn(v[c]);
-          if (dd < 5)
-            ih[c] += a << (6 * (4 - dd));
-          else
-            il[c] += a << (6 * (9 - dd));
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
         const int n = tn * NT + ch + c;
+        int a[NACC];
+#pragma unroll
+        for (int dd = 0; dd < NACC; ++dd)
+          a[dd] = (dd < 4 || small) ? acc_int_small(__uint_as_float(r[dd][c])) : acc_int(r[dd][c]);
+        const long long hi = (long long)(a[0] * 64 + a[1]) * 4096 + (a[2] * 64 + a[3]);
+        const long long lo = ((long long)(a[4] * 64 + a[5]) * 4096 + (a[6] * 64 + a[7])) * 4096 + (a[8] * 64 + a[9]);
         double val = 0.0;
-        if (row < m && n < m) {
+        const bool kept = KIND != 3 || n < 32 * step || n >= 32 * step + 32;  // KIND 3: not the panel's columns
+        if (row < m && n < m && kept) {
+          const float a2 = __uint_as_float(r[0][c]);
           const int k = er + rexp[(long long)zr * m + n];
-          if ((nanc >> c) & 1u)
+          if (a2 != a2)  // NaN or infinite operand: every digit is NaN, acc_2 included
             val = __longlong_as_double(0x7ff8000000000000ll);
-          else if (k - 66 >= -1022 && k - 36 <= 1023)
-            val = fma((double)il[c], pow2(k - 66), (double)ih[c] * pow2(k - 36));
+          else if ((hi | lo) == 0)  // also the zero rows and columns, whose scale is the smallest
+            val = 0.0;
+          else if (k - 66 >= -1022 && k + 9 <= 1023)
+            val = i2d_scaled(hi, k - 30) + i2d_scaled(lo, k - 66);
           else
-            val = ldexp(fma((double)il[c], 0x1p-30, (double)ih[c]), k - 36);
+            val = ldexp(fma((double)lo, 0x1p-36, (double)hi), k - 30);
         }
-        stg[lane * 17 + c] = val;
+        stg[lane * 9 + c] = val;
       }
       __syncwarp();
-      // row-major float64 results: lane = (row parity, column), 16 row pairs;
-      // the loads an update needs are gathered before any store
-      const int cl = lane & 15, r0 = lane >> 4, n = tn * NT + ch + cl;
+      // row-major float64 results: lane = (row quarter, column), 8 row
+      // quads; the loads an update needs are gathered before any store
+      const int cl = lane & 7, r0 = lane >> 3, n = tn * NT + ch + cl;
       const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
       const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
       if (n < m && outside) {
         const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3;
-        double in[16];
+        double in[8];
         if (rmw || dnext || gj) {
           const double* src = rmw ? out.ZL + o : (gj ? out.G + o : out.B + o + mm);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int rr = rbase + r0 + 2 * i;
+          for (int i = 0; i < 8; ++i) {
+            const int rr = rbase + r0 + 4 * i;
             in[i] = (rr < m && !(gj && rr >= k0 && rr < k0 + 32)) ? src[(long long)rr * m + n] : 0.0;
           }
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int r = r0 + 2 * i, rr = rbase + r;
+        for (int i = 0; i < 8; ++i) {
+          const int rl = r0 + 4 * i, rr = rbase + rl;
           if (rr >= m) continue;
-          const double w = stg[r * 17 + cl];
+          const double w = stg[rl * 9 + cl];
           const long long e = (long long)rr * m + n;
           if (KIND == 0) {
             double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
@@ -457,28 +491,40 @@ __global__ void __launch_bounds__(256) k_gj_copy_b0(const PartDesc* __restrict__
 }
 
 // One panel, one cluster of kGjCS CTAs per block: CTA `rank` holds rows
-// [rank R, rank R + R) (R = ceil(m / kGjCS)), a thread per row with the
-// panel's 32 values in registers, rotated by one column per pivot (at pivot
-// kk, reg[c] is panel column (kk + c) mod 32, so the pivot column is always
-// reg[0] and the loop needs no unrolling; after 32 pivots the order is back).
-// Per pivot: each warp finds its best candidate row (a strict order: value,
-// then lowest row), its owner publishes the row in shared memory, and the
-// owner of row k publishes that row; one cluster barrier; every lane reads
-// the cluster's candidates and element `lane` of every candidate row and of
-// row k through distributed shared memory (one round of independent loads),
-// picks the winner, and the rows are updated.  The float64 multiply-adds of
-// the rank-1 updates (32 per row and pivot) bound the kernel; nothing else is
-// on the float64 pipe.  The exchanges of rows outside the panel are applied
-// after the last pivot as one permutation (pivot rows are always taken from
-// rows >= k, so every row outside K that moves receives a row of K).
+// [rank R, rank R + R) (R = ceil(m / kGjCS)); warp w of it rows R rank + 16 w
+// + (0..15), two lanes per row (lane = 16 h + row): lane half h holds panel
+// columns 16 h .. 16 h + 15 in registers, rotated by one column per pivot (at
+// pivot kk the row's register c of half h is panel column (kk + 16 h + c) mod
+// 32, so the pivot column is always register 0 of half 0 and the loop needs
+// no unrolling; after 32 pivots the order is back).  GB300's float64 unit
+// takes a warp instruction per about 68 cycles per SM sub-partition and
+// a dependent one 66 cycles later, so the per-pivot chain keeps float64
+// instructions to the arithmetic: the pivot search orders the float64 bits
+// of |M[i][k]| as integers, the checks read the bits, and the rank-1 update
+// (16 multiply-adds per lane) is spread over four warps per CTA, one per
+// sub-partition.  Per pivot: each warp finds its best row (a strict order:
+// magnitude, then lowest row), the CTA's best of four after a CTA barrier,
+// whose owner publishes the row in shared memory (the owner of row k
+// publishes row k); one cluster barrier; every lane reads the kGjCS
+// candidates, element `lane` of each candidate row and of row k through
+// distributed shared memory (one round of independent loads), picks the
+// winner, and the rows are updated.  The exchanges of rows outside the
+// panel are applied after the last pivot as one permutation (pivot rows are
+// always taken from rows >= k, so every row outside K that moves receives a
+// row of K).
 constexpr int kGjCS = 4;
-constexpr int kGjThreads = 64;
+constexpr int kGjThreads = 128;
 constexpr int kGjWarps = kGjThreads / 32;
-constexpr int kGjSlots = kGjCS * kGjWarps;  // candidates per pivot
-static_assert(kGjSlots <= 32, "one candidate per lane");
+static_assert(kGjWarps * 16 * kGjCS >= kMaxMTensor, "a lane pair per row");
 
-__device__ __forceinline__ bool gj_before(double ov, int oi, double v, int vi) {
-  return ov > v || (ov == v && oi < vi);
+struct __align__(16) GjCand {
+  unsigned long long key;  // 0: not eligible; 1: NaN; else |value| bits + 2
+  int idx;                 // row (unique per thread, so the order is strict)
+  int pad;
+};
+
+__device__ __forceinline__ bool gj_before(unsigned long long ok, int oi, unsigned long long k, int i) {
+  return ok > k || (ok == k && oi < i);
 }
 
 __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restrict__ parts, int t, int m, int panel,
@@ -490,10 +536,10 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   cg::cluster_group cl = cg::this_cluster();
   // published per pivot (double-buffered: a buffer is rewritten two pivots
   // later, after a cluster barrier that every reader of it has passed)
-  __shared__ __align__(16) double crow[2][kGjWarps][32], krow[2][32];
-  __shared__ double cval[2][kGjWarps];
-  __shared__ int cidx[2][kGjWarps];
+  __shared__ __align__(16) double crow[2][32], krow[2][32];
+  __shared__ GjCand cand[2];
   // this CTA's own
+  __shared__ GjCand wcand[kGjWarps];
   __shared__ __align__(16) double sprow[kGjWarps][32], xrow[kGjWarps][32];
   __shared__ int piv_s[32], perm[kMaxMTensor];
   const int rank = (int)cl.block_rank();
@@ -502,123 +548,127 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   if (t >= p.L) return;  // the same for every CTA of the cluster
   const long long mm = (long long)m * m;
   double* M = G + p.blk + (long long)t * mm;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = (m + kGjCS - 1) / kGjCS, i = rank * R + tid;
-  const bool valid = tid < R && i < m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, h = lane >> 4, rl = warp * 16 + (lane & 15);
+  const int R = (m + kGjCS - 1) / kGjCS, i = rank * R + rl;
+  const bool valid = rl < R && i < m;
   const int k0 = 32 * panel, kw = min(32, m - k0);  // kw % 8 == 0
-  double reg[32];
+  double reg[16];
 #pragma unroll
-  for (int c = 0; c < 32; c += 2) {
+  for (int c = 0; c < 16; c += 2) {
     double2 v2 = make_double2(0.0, 0.0);
-    if (valid && c < kw) v2 = *reinterpret_cast<const double2*>(M + (long long)i * m + k0 + c);
+    if (valid && 16 * h + c < kw) v2 = *reinterpret_cast<const double2*>(M + (long long)i * m + k0 + 16 * h + c);
     reg[c] = v2.x;
     reg[c + 1] = v2.y;
   }
   bool bad = false;
 #pragma unroll 1
   for (int kk = 0; kk < 32; ++kk) {
+    const double nxt = __shfl_xor_sync(0xffffffffu, reg[0], 16);  // the other half's first column
     if (kk >= kw) {  // padding columns of a narrow last panel: rotate only
-      const double t0 = reg[0];
 #pragma unroll
-      for (int c = 0; c < 31; ++c) reg[c] = reg[c + 1];
-      reg[31] = t0;
+      for (int c = 0; c < 15; ++c) reg[c] = reg[c + 1];
+      reg[15] = nxt;
       continue;
     }
     const int k = k0 + kk, buf = kk & 1;
-    // this warp's candidate; rows < k rank below every row >= k (NaN just
-    // above them), threads without a row below everything, indexes unique
-    double v = -2.0;
-    int vi = m + rank * kGjThreads + tid;
-    if (valid) {
-      vi = i;
-      if (i >= k) {
-        const double a = fabs(reg[0]);
-        v = a == a ? a : -0.5;
-      } else {
-        v = -1.0;
-      }
+    // this warp's candidate (column kk is register 0 of the half-0 lanes)
+    unsigned long long key = 0ull;
+    int idx = (h == 0 && valid) ? i : m + tid;
+    if (h == 0 && valid && i >= k) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(reg[0]) & 0x7fffffffffffffffull;
+      key = bits > 0x7ff0000000000000ull ? 1ull : bits + 2ull;
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, vi, off);
-      if (gj_before(ov, oi, v, vi)) v = ov, vi = oi;
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+      if (gj_before(ok, oi, key, idx)) key = ok, idx = oi;
     }
-    if (valid && i == vi)
+    if (lane == 0) wcand[warp] = GjCand{key, idx, 0};
+    __syncthreads();
+    GjCand best = wcand[0];
 #pragma unroll
-      for (int c = 0; c < 32; c += 2) *reinterpret_cast<double2*>(&crow[buf][warp][c]) = make_double2(reg[c], reg[c + 1]);
+    for (int w = 1; w < kGjWarps; ++w) {
+      const GjCand o = wcand[w];
+      if (gj_before(o.key, o.idx, best.key, best.idx)) best = o;
+    }
+    if (valid && i == best.idx)
+#pragma unroll
+      for (int c = 0; c < 16; c += 2)
+        *reinterpret_cast<double2*>(&crow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
     if (valid && i == k)
 #pragma unroll
-      for (int c = 0; c < 32; c += 2) *reinterpret_cast<double2*>(&krow[buf][c]) = make_double2(reg[c], reg[c + 1]);
-    if (lane == 0) cval[buf][warp] = v, cidx[buf][warp] = vi;
+      for (int c = 0; c < 16; c += 2)
+        *reinterpret_cast<double2*>(&krow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
+    if (tid == 0) cand[buf] = best;
     cl.sync();
-    // one round of independent remote loads: the candidates, element `lane`
-    // of every candidate row, element `lane` of row k
-    double cv = -3.0;
-    int ci = 0x7fffffff, cs = lane;
-    if (lane < kGjSlots) {
-      cv = *cl.map_shared_rank(&cval[buf][lane % kGjWarps], lane / kGjWarps);
-      ci = *cl.map_shared_rank(&cidx[buf][lane % kGjWarps], lane / kGjWarps);
-    }
-    double rowv[kGjSlots];
+    // one round of independent remote loads: the kGjCS candidates, element
+    // `lane` of every candidate row, element `lane` of row k
+    GjCand cs[kGjCS];
+    double rowv[kGjCS];
 #pragma unroll
-    for (int s = 0; s < kGjSlots; ++s) rowv[s] = cl.map_shared_rank(&crow[buf][s % kGjWarps][0], s / kGjWarps)[lane];
+    for (int s = 0; s < kGjCS; ++s) {
+      const uint4 raw = *reinterpret_cast<const uint4*>(cl.map_shared_rank(&cand[buf], s));
+      cs[s].key = ((unsigned long long)raw.y << 32) | raw.x;
+      cs[s].idx = (int)raw.z;
+      rowv[s] = cl.map_shared_rank(&crow[buf][0], s)[lane];
+    }
     const double xk = cl.map_shared_rank(&krow[buf][0], k / R)[lane];
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, cv, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, ci, off);
-      const int os = __shfl_xor_sync(0xffffffffu, cs, off);
-      if (gj_before(ov, oi, cv, ci)) cv = ov, ci = oi, cs = os;
-    }
-    const int r = ci;
+    unsigned long long bkey = cs[0].key;
+    int r = cs[0].idx;
     double prow = rowv[0];
 #pragma unroll
-    for (int s = 1; s < kGjSlots; ++s)
-      if (cs == s) prow = rowv[s];
-    const double p0 = __shfl_sync(0xffffffffu, prow, 0);  // the pivot (column kk is reg[0])
+    for (int s = 1; s < kGjCS; ++s)
+      if (gj_before(cs[s].key, cs[s].idx, bkey, r)) bkey = cs[s].key, r = cs[s].idx, prow = rowv[s];
+    const double p0 = __shfl_sync(0xffffffffu, prow, 0);  // the pivot (column kk)
+    const unsigned long long pb = (unsigned long long)__double_as_longlong(p0) & 0x7fffffffffffffffull;
+    // zero or not finite; a pivot below 2^-1022 (whose reciprocal overflows) too
+    const bool pbad = pb < 0x0010000000000000ull || pb >= 0x7ff0000000000000ull;
     double inv = 0.0;
-    if (lane == 0) inv = 1.0 / p0;
+    if (lane == 0 && !pbad) inv = 1.0 / p0;
     inv = __shfl_sync(0xffffffffu, inv, 0);
-    if (!(fabs(p0) > 0.0) || !isfinite(inv) || !isfinite(p0)) {
-      inv = 0.0;
-      bad = true;
-    }
+    if (pbad) bad = true;
     sprow[warp][lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
     xrow[warp][lane] = xk;                             // the old row k
     if (tid == 0) piv_s[kk] = r;
     if (rank == 0 && tid == 0) piv[(long long)q * m + k] = r;
     __syncwarp();
+    const double* sp = sprow[warp];
     if (valid) {
-      const double* sp = sprow[warp];
       if (i == k) {
 #pragma unroll
-        for (int c = 0; c < 31; ++c) reg[c] = sp[c + 1];
-        reg[31] = sp[0];
+        for (int c = 0; c < 15; ++c) reg[c] = sp[16 * h + c + 1];
+        reg[15] = h == 0 ? sp[16] : sp[0];
       } else {
-        if (i == r)  // row r takes the old row k
+        double other = nxt;
+        if (i == r) {  // row r takes the old row k
 #pragma unroll
-          for (int c = 0; c < 32; ++c) reg[c] = xrow[warp][c];
-        const double f = reg[0];
+          for (int c = 0; c < 16; ++c) reg[c] = xrow[warp][16 * h + c];
+          other = xrow[warp][16 * (1 - h)];
+        }
+        // the row's column kk (register 0 of its half-0 lane)
+        const double f = h == 0 ? reg[0] : other;
 #pragma unroll
-        for (int c = 0; c < 31; ++c) reg[c] = fma(-f, sp[c + 1], reg[c + 1]);
-        reg[31] = -f * sp[0];
+        for (int c = 0; c < 15; ++c) reg[c] = fma(-f, sp[16 * h + c + 1], reg[c + 1]);
+        reg[15] = h == 0 ? fma(-f, sp[16], other) : -f * sp[0];
       }
     }
   }
   // the eliminated panel and the row slices of U (scale per row over its 32 values)
+  uint32_t hmax = 0;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) hmax = max(hmax, (uint32_t)(__double_as_longlong(reg[c]) >> 32) & 0x7fffffffu);
+  hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 16));
   if (valid) {
 #pragma unroll
-    for (int c = 0; c < 32; c += 2)
-      if (c < kw) *reinterpret_cast<double2*>(M + (long long)i * m + k0 + c) = make_double2(reg[c], reg[c + 1]);
-    uint32_t hmax = 0;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) hmax = max(hmax, (uint32_t)(__double_as_longlong(reg[c]) >> 32) & 0x7fffffffu);
+    for (int c = 0; c < 16; c += 2)
+      if (16 * h + c < kw)
+        *reinterpret_cast<double2*>(M + (long long)i * m + k0 + 16 * h + c) = make_double2(reg[c], reg[c + 1]);
     const int e = scale_exponent(hmax);
-    Uexp[(long long)q * m + i] = e;
-    __nv_bfloat16* u = Us + (long long)q * S * m * 32 + (long long)i * 32;
+    if (h == 0) Uexp[(long long)q * m + i] = e;
+    __nv_bfloat16* u = Us + (long long)q * S * m * 32 + (long long)i * 32 + 16 * h;
 #pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += 8) {
+    for (int c0 = 0; c0 < 16; c0 += 8) {
       uint32_t d[8][S];
 #pragma unroll
       for (int uu = 0; uu < 8; ++uu) digits9((unsigned long long)__double_as_longlong(reg[c0 + uu]), e, d[uu]);
@@ -648,21 +698,21 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   // holds V[0..31][j]; zero inside the panel), then the rows outside K that
   // took part in an exchange receive their rows of K (read before written:
   // the V loads come first, from this thread's own column)
-  for (int jcol = rank * kGjThreads + tid; jcol < m; jcol += kGjCS * kGjThreads) {
+  for (int jcol = tid * kGjCS + rank; jcol < m; jcol += kGjCS * kGjThreads) {
     const bool inK = jcol >= k0 && jcol < k0 + kw;
     double vv[32];
-    uint32_t hmax = 0;
+    uint32_t vmax = 0;
 #pragma unroll
     for (int kk = 0; kk < 32; ++kk) {
       vv[kk] = (!inK && kk < kw) ? M[(long long)perm[k0 + kk] * m + jcol] : 0.0;
-      hmax = max(hmax, (uint32_t)(__double_as_longlong(vv[kk]) >> 32) & 0x7fffffffu);
+      vmax = max(vmax, (uint32_t)(__double_as_longlong(vv[kk]) >> 32) & 0x7fffffffu);
     }
     if (!inK)
       for (int kk = 0; kk < kw; ++kk) {
         const int x = piv_s[kk];
         if (x >= k0 + kw) M[(long long)x * m + jcol] = M[(long long)perm[x] * m + jcol];
       }
-    const int e = scale_exponent(hmax);
+    const int e = scale_exponent(vmax);
     Vexp[(long long)q * m + jcol] = e;
     __nv_bfloat16* vdst = Vs + (long long)q * S * m * 32 + (long long)jcol * 32;
 #pragma unroll
