@@ -496,36 +496,95 @@ __global__ void __launch_bounds__(256) k_gj_copy_b0(const PartDesc* __restrict__
 // columns 16 h .. 16 h + 15 in registers, rotated by one column per pivot (at
 // pivot kk the row's register c of half h is panel column (kk + 16 h + c) mod
 // 32, so the pivot column is always register 0 of half 0 and the loop needs
-// no unrolling; after 32 pivots the order is back).  GB300's float64 unit
-// takes a warp instruction per about 68 cycles per SM sub-partition and
-// a dependent one 66 cycles later, so the per-pivot chain keeps float64
-// instructions to the arithmetic: the pivot search orders the float64 bits
-// of |M[i][k]| as integers, the checks read the bits, and the rank-1 update
-// (16 multiply-adds per lane) is spread over four warps per CTA, one per
-// sub-partition.  Per pivot: each warp finds its best row (a strict order:
-// magnitude, then lowest row), the CTA's best of four after a CTA barrier,
-// whose owner publishes the row in shared memory (the owner of row k
-// publishes row k); one cluster barrier; every lane reads the kGjCS
-// candidates, element `lane` of each candidate row and of row k through
-// distributed shared memory (one round of independent loads), picks the
-// winner, and the rows are updated.  The exchanges of rows outside the
-// panel are applied after the last pivot as one permutation (pivot rows are
-// always taken from rows >= k, so every row outside K that moves receives a
-// row of K).
+// no unrolling; after 32 pivots the order is back).
+//
+// GB300's float64 unit takes a warp instruction per about 68 cycles per SM
+// sub-partition and a dependent one 66 cycles later (a division about 460),
+// so the per-pivot chain keeps float64 instructions to the arithmetic: the
+// pivot search orders the float64 bits of |M[i][k]| as integers, the checks
+// read the bits, the reciprocal is taken once per CTA, the rank-1 update (16
+// multiply-adds per lane) is spread over four warps per CTA, and it overlaps
+// the cluster barrier by one pivot of lookahead.  With pivot kk's scaled row
+// known, every row first updates only its next pivot column; the warps and
+// then the CTA choose their best row for pivot kk + 1 on it (a strict order:
+// magnitude, then lowest row), and that row is published as it is BEFORE
+// pivot kk's update, with its multiplier f and the reciprocal of its updated
+// pivot (row k + 1 likewise).  The CTA arrives at the cluster barrier, makes
+// the bulk update of its rows, then waits; each lane then reads the kGjCS
+// candidates and element `lane` (+ 1, the rotation) of each candidate row
+// and of row k + 1 through distributed shared memory (one round of
+// independent loads), picks the winner and applies pivot kk's update to that
+// one element (the multiply-add its owner made).  The exchanges of rows
+// outside the panel are applied after the last pivot as one permutation
+// (pivot rows are always taken from rows >= k, so every row outside K that
+// moves receives a row of K).
 constexpr int kGjCS = 4;
 constexpr int kGjThreads = 128;
 constexpr int kGjWarps = kGjThreads / 32;
 static_assert(kGjWarps * 16 * kGjCS >= kMaxMTensor, "a lane pair per row");
 
-struct __align__(16) GjCand {
+struct __align__(16) GjKey {
   unsigned long long key;  // 0: not eligible; 1: NaN; else |value| bits + 2
   int idx;                 // row (unique per thread, so the order is strict)
   int pad;
 };
 
+struct __align__(16) GjCand {
+  unsigned long long key;
+  int idx, pad;
+  double inv;  // 1 / the candidate's updated pivot (0 when unusable)
+  double f;    // the candidate's multiplier of the previous pivot
+};
+
 __device__ __forceinline__ bool gj_before(unsigned long long ok, int oi, unsigned long long k, int i) {
   return ok > k || (ok == k && oi < i);
 }
+
+__device__ __forceinline__ unsigned long long gj_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  return b > 0x7ff0000000000000ull ? 1ull : b + 2ull;
+}
+
+// zero, below 2^-1022 (whose reciprocal overflows) or not finite
+__device__ __forceinline__ bool gj_unusable(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  return b < 0x0010000000000000ull || b >= 0x7ff0000000000000ull;
+}
+
+// The CTA's best of every lane's (key, idx): a warp butterfly, then the best
+// of the warps' bests after a CTA barrier (the same result in every thread).
+__device__ __forceinline__ GjKey gj_cta_best(unsigned long long key, int idx, GjKey* wbest, int warp, int lane) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (gj_before(ok, oi, key, idx)) key = ok, idx = oi;
+  }
+  if (lane == 0) wbest[warp] = GjKey{key, idx, 0};
+  __syncthreads();
+  GjKey best = wbest[0];
+#pragma unroll
+  for (int w = 1; w < kGjWarps; ++w) {
+    const GjKey o = wbest[w];
+    if (gj_before(o.key, o.idx, best.key, best.idx)) best = o;
+  }
+  return best;
+}
+
+__device__ __forceinline__ GjCand gj_read_cand(const GjCand* c) {
+  const uint4* v = reinterpret_cast<const uint4*>(c);
+  const uint4 a = v[0], b = v[1];
+  GjCand r;
+  r.key = ((unsigned long long)a.y << 32) | a.x;
+  r.idx = (int)a.z;
+  r.pad = 0;
+  r.inv = __hiloint2double((int)b.y, (int)b.x);
+  r.f = __hiloint2double((int)b.w, (int)b.z);
+  return r;
+}
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restrict__ parts, int t, int m, int panel,
                                                         double* __restrict__ G, int* __restrict__ piv,
@@ -538,8 +597,9 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   // later, after a cluster barrier that every reader of it has passed)
   __shared__ __align__(16) double crow[2][32], krow[2][32];
   __shared__ GjCand cand[2];
+  __shared__ double kf[2];
   // this CTA's own
-  __shared__ GjCand wcand[kGjWarps];
+  __shared__ GjKey wbest[kGjWarps];
   __shared__ __align__(16) double sprow[kGjWarps][32], xrow[kGjWarps][32];
   __shared__ int piv_s[32], perm[kMaxMTensor];
   const int rank = (int)cl.block_rank();
@@ -552,6 +612,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   const int R = (m + kGjCS - 1) / kGjCS, i = rank * R + rl;
   const bool valid = rl < R && i < m;
   const int k0 = 32 * panel, kw = min(32, m - k0);  // kw % 8 == 0
+  const int noidx = m + rank * kGjThreads + tid;   // an index no row has
   double reg[16];
 #pragma unroll
   for (int c = 0; c < 16; c += 2) {
@@ -561,97 +622,128 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     reg[c + 1] = v2.y;
   }
   bool bad = false;
+  double* sp = sprow[warp];
+  double* xr = xrow[warp];
+  int r;  // the current pivot row
+  {
+    // pivot k0: candidates from the rows as they are
+    const bool elig = h == 0 && valid && i >= k0;
+    const GjKey best = gj_cta_best(elig ? gj_key(reg[0]) : 0ull, elig ? i : noidx, wbest, warp, lane);
+    if (valid && i == best.idx) {
+#pragma unroll
+      for (int c = 0; c < 16; c += 2)
+        *reinterpret_cast<double2*>(&crow[0][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
+      if (h == 0) {
+        cand[0].inv = gj_unusable(reg[0]) ? 0.0 : 1.0 / reg[0];
+        cand[0].f = 0.0;
+      }
+    }
+    if (valid && i == k0)
+#pragma unroll
+      for (int c = 0; c < 16; c += 2)
+        *reinterpret_cast<double2*>(&krow[0][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
+    if (tid == 0) cand[0].key = best.key, cand[0].idx = best.idx;
+    cl.sync();
+    GjCand w = gj_read_cand(cl.map_shared_rank(&cand[0], 0));
+    double prow = cl.map_shared_rank(&crow[0][0], 0)[lane];
+#pragma unroll
+    for (int s = 1; s < kGjCS; ++s) {
+      const GjCand o = gj_read_cand(cl.map_shared_rank(&cand[0], s));
+      const double v = cl.map_shared_rank(&crow[0][0], s)[lane];
+      if (gj_before(o.key, o.idx, w.key, w.idx)) w = o, prow = v;
+    }
+    const double xk = cl.map_shared_rank(&krow[0][0], k0 / R)[lane];
+    const double p0 = __shfl_sync(0xffffffffu, prow, 0);
+    double inv = w.inv;
+    if (gj_unusable(p0)) inv = 0.0, bad = true;
+    r = w.idx;
+    sp[lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
+    xr[lane] = xk;                            // the old row k
+    if (tid == 0) piv_s[0] = r;
+    if (rank == 0 && tid == 0) piv[(long long)q * m + k0] = r;
+    __syncwarp();
+  }
 #pragma unroll 1
   for (int kk = 0; kk < 32; ++kk) {
-    const double nxt = __shfl_xor_sync(0xffffffffu, reg[0], 16);  // the other half's first column
     if (kk >= kw) {  // padding columns of a narrow last panel: rotate only
+      const double nxt = __shfl_xor_sync(0xffffffffu, reg[0], 16);
 #pragma unroll
       for (int c = 0; c < 15; ++c) reg[c] = reg[c + 1];
       reg[15] = nxt;
       continue;
     }
-    const int k = k0 + kk, buf = kk & 1;
-    // this warp's candidate (column kk is register 0 of the half-0 lanes)
-    unsigned long long key = 0ull;
-    int idx = (h == 0 && valid) ? i : m + tid;
-    if (h == 0 && valid && i >= k) {
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(reg[0]) & 0x7fffffffffffffffull;
-      key = bits > 0x7ff0000000000000ull ? 1ull : bits + 2ull;
+    const int k = k0 + kk;
+    const bool la = kk + 1 < kw, swap = i == r && i != k;  // row r takes the old row k
+    if (swap)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) reg[c] = xr[16 * h + c];
+    const double other = __shfl_xor_sync(0xffffffffu, reg[0], 16);  // the other half's first column
+    const double f = h == 0 ? reg[0] : other;  // the row's multiplier (column kk)
+    if (la) {
+      // the next pivot column of every row first, its candidates, and the
+      // CTA's best row published before the update
+      const int buf = (kk + 1) & 1;
+      const double new1 = i == k ? sp[1] : fma(-f, sp[1], reg[1]);
+      const bool elig = h == 0 && valid && i > k;
+      const GjKey best = gj_cta_best(elig ? gj_key(new1) : 0ull, elig ? i : noidx, wbest, warp, lane);
+      if (valid && i == best.idx) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 2)
+          *reinterpret_cast<double2*>(&crow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
+        if (h == 0) {
+          cand[buf].inv = gj_unusable(new1) ? 0.0 : 1.0 / new1;
+          cand[buf].f = f;
+        }
+      }
+      if (valid && i == k + 1) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 2)
+          *reinterpret_cast<double2*>(&krow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
+        if (h == 0) kf[buf] = f;
+      }
+      if (tid == 0) cand[buf].key = best.key, cand[buf].idx = best.idx;
+      cluster_arrive();
     }
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-      if (gj_before(ok, oi, key, idx)) key = ok, idx = oi;
-    }
-    if (lane == 0) wcand[warp] = GjCand{key, idx, 0};
-    __syncthreads();
-    GjCand best = wcand[0];
-#pragma unroll
-    for (int w = 1; w < kGjWarps; ++w) {
-      const GjCand o = wcand[w];
-      if (gj_before(o.key, o.idx, best.key, best.idx)) best = o;
-    }
-    if (valid && i == best.idx)
-#pragma unroll
-      for (int c = 0; c < 16; c += 2)
-        *reinterpret_cast<double2*>(&crow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
-    if (valid && i == k)
-#pragma unroll
-      for (int c = 0; c < 16; c += 2)
-        *reinterpret_cast<double2*>(&krow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
-    if (tid == 0) cand[buf] = best;
-    cl.sync();
-    // one round of independent remote loads: the kGjCS candidates, element
-    // `lane` of every candidate row, element `lane` of row k
-    GjCand cs[kGjCS];
-    double rowv[kGjCS];
-#pragma unroll
-    for (int s = 0; s < kGjCS; ++s) {
-      const uint4 raw = *reinterpret_cast<const uint4*>(cl.map_shared_rank(&cand[buf], s));
-      cs[s].key = ((unsigned long long)raw.y << 32) | raw.x;
-      cs[s].idx = (int)raw.z;
-      rowv[s] = cl.map_shared_rank(&crow[buf][0], s)[lane];
-    }
-    const double xk = cl.map_shared_rank(&krow[buf][0], k / R)[lane];
-    unsigned long long bkey = cs[0].key;
-    int r = cs[0].idx;
-    double prow = rowv[0];
-#pragma unroll
-    for (int s = 1; s < kGjCS; ++s)
-      if (gj_before(cs[s].key, cs[s].idx, bkey, r)) bkey = cs[s].key, r = cs[s].idx, prow = rowv[s];
-    const double p0 = __shfl_sync(0xffffffffu, prow, 0);  // the pivot (column kk)
-    const unsigned long long pb = (unsigned long long)__double_as_longlong(p0) & 0x7fffffffffffffffull;
-    // zero or not finite; a pivot below 2^-1022 (whose reciprocal overflows) too
-    const bool pbad = pb < 0x0010000000000000ull || pb >= 0x7ff0000000000000ull;
-    double inv = 0.0;
-    if (lane == 0 && !pbad) inv = 1.0 / p0;
-    inv = __shfl_sync(0xffffffffu, inv, 0);
-    if (pbad) bad = true;
-    sprow[warp][lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
-    xrow[warp][lane] = xk;                             // the old row k
-    if (tid == 0) piv_s[kk] = r;
-    if (rank == 0 && tid == 0) piv[(long long)q * m + k] = r;
-    __syncwarp();
-    const double* sp = sprow[warp];
+    // pivot kk's update of this thread's row, rotated by one column
     if (valid) {
       if (i == k) {
 #pragma unroll
         for (int c = 0; c < 15; ++c) reg[c] = sp[16 * h + c + 1];
         reg[15] = h == 0 ? sp[16] : sp[0];
       } else {
-        double other = nxt;
-        if (i == r) {  // row r takes the old row k
-#pragma unroll
-          for (int c = 0; c < 16; ++c) reg[c] = xrow[warp][16 * h + c];
-          other = xrow[warp][16 * (1 - h)];
-        }
-        // the row's column kk (register 0 of its half-0 lane)
-        const double f = h == 0 ? reg[0] : other;
 #pragma unroll
         for (int c = 0; c < 15; ++c) reg[c] = fma(-f, sp[16 * h + c + 1], reg[c + 1]);
         reg[15] = h == 0 ? fma(-f, sp[16], other) : -f * sp[0];
       }
+    }
+    if (la) {
+      cluster_wait();
+      const int buf = (kk + 1) & 1, src = (lane + 1) & 31;
+      GjCand w = gj_read_cand(cl.map_shared_rank(&cand[buf], 0));
+      double pre = cl.map_shared_rank(&crow[buf][0], 0)[src];
+#pragma unroll
+      for (int s = 1; s < kGjCS; ++s) {
+        const GjCand o = gj_read_cand(cl.map_shared_rank(&cand[buf], s));
+        const double v = cl.map_shared_rank(&crow[buf][0], s)[src];
+        if (gj_before(o.key, o.idx, w.key, w.idx)) w = o, pre = v;
+      }
+      const int ko = (k + 1) / R;
+      const double kpre = cl.map_shared_rank(&krow[buf][0], ko)[src];
+      const double kfk = *cl.map_shared_rank(&kf[buf], ko);
+      // pivot kk's update of element `lane` of the winner and of row k + 1
+      const double spc = sp[src];
+      const double u = src == 0 ? -w.f * spc : fma(-w.f, spc, pre);
+      const double x = src == 0 ? -kfk * spc : fma(-kfk, spc, kpre);
+      const double p0 = __shfl_sync(0xffffffffu, u, 0);
+      double inv = w.inv;
+      if (gj_unusable(p0)) inv = 0.0, bad = true;
+      r = w.idx;
+      __syncwarp();
+      sp[lane] = lane == 0 ? inv : u * inv;
+      xr[lane] = x;
+      if (tid == 0) piv_s[kk + 1] = r;
+      if (rank == 0 && tid == 0) piv[(long long)q * m + k + 1] = r;
+      __syncwarp();
     }
   }
   // the eliminated panel and the row slices of U (scale per row over its 32 values)
