@@ -315,17 +315,13 @@ static size_t oz_bytes(long long nblk, int nparts, int m) {
 }
 
 // The float64 block inverse of a sliced level: blocked Gauss-Jordan with the
-// trailing updates on the tensor cores, unless DM_FP64_INVERSE=cluster.
-constexpr int kGjMinBlocks = 48;  // measured: 64 blocks of m = 256 93 vs 101 ms, 12 blocks 9.9 vs 5.4 ms per factor
+// trailing updates on the tensor cores, unless DM_FP64_INVERSE=cluster (the
+// column-by-column kernel).  Measured at m = 256 on GB300: faster for every
+// launch size, 64 blocks per launch (the top level) 1.45 vs 2.5 ms, and the
+// supplementary levels' 1-12 blocks per launch 9.2 vs 10.9 ms per factor.
 static bool gj_wanted() {
   const char* e = std::getenv("DM_FP64_INVERSE");
   return !(e && std::strcmp(e, "cluster") == 0);
-}
-
-// DM_FP64_INVERSE=blocked takes the blocked inversion for every launch (tests).
-static int gj_min_blocks() {
-  const char* e = std::getenv("DM_FP64_INVERSE");
-  return (e && std::strcmp(e, "blocked") == 0) ? 1 : kGjMinBlocks;
 }
 
 size_t Level::bytes_needed() const {
@@ -683,9 +679,7 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   cs.bytes = 26.0 * m * m;  // one block: float64 read, nine bf16 slices written
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t], nbk = L.active_back[t];
-    // the blocked inversion pays where a launch inverts many blocks (its
-    // panels run one CTA per block); fewer blocks: the cluster inverse
-    if (Z.gj && np >= gj_min_blocks())
+    if (Z.gj)
       DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np,
                 launch_gj_inverse(L.d_parts, np, t, m, L.B, G, Z.piv, Z.U, Z.eU, Z.V, Z.eV, Z.gj_maps, L.status,
                                   L.d_err, st));

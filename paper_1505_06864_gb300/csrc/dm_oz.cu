@@ -657,6 +657,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     double inv = w.inv;
     if (gj_unusable(p0)) inv = 0.0, bad = true;
     r = w.idx;
+    if (r < k0 || r >= m) r = k0, inv = 0.0, bad = true;  // never: the winner is an eligible row
     sp[lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
     xr[lane] = xk;                            // the old row k
     if (tid == 0) piv_s[0] = r;
@@ -738,6 +739,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       double inv = w.inv;
       if (gj_unusable(p0)) inv = 0.0, bad = true;
       r = w.idx;
+      if (r <= k || r >= m) r = k + 1, inv = 0.0, bad = true;  // never: the winner is an eligible row
       __syncwarp();
       sp[lane] = lane == 0 ? inv : u * inv;
       xr[lane] = x;
