@@ -308,10 +308,18 @@ static bool oz_wanted(const Level& L) {
          oz_eligible(L.max_m);
 }
 
-static size_t oz_bytes(long long nblk, int nparts, int m) {
+static size_t oz_bytes(long long nblk, int nparts, int nseps, int m) {
   const size_t mm = (size_t)m * m, sl = (size_t)oz_slice_blocks_bytes(m), nb = nblk / mm, np = std::max(1, nparts);
-  return (3 * nb + 7 * np) * (sl + m * sizeof(int)) + np * mm * sizeof(double) +
+  return (3 * nb + 7 * np + 5 * (size_t)nseps) * (sl + m * sizeof(int)) + np * mm * sizeof(double) +
          np * ((size_t)2 * 9 * m * 32 * 2 + 3 * m * sizeof(int));
+}
+
+// The supplementary blocks of a sliced level as digit-sliced tensor-core
+// products, unless DM_FP64_ASSEMBLY=fma (the float64 kernel).  Measured at
+// m = 256 on GB300: see the assembly kernel's figures in the design notes.
+static bool oz_asm_wanted() {
+  const char* e = std::getenv("DM_FP64_ASSEMBLY");
+  return !(e && std::strcmp(e, "fma") == 0);
 }
 
 // The float64 block inverse of a sliced level: blocked Gauss-Jordan with the
@@ -328,7 +336,7 @@ size_t Level::bytes_needed() const {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   size_t b = 3 * nblk * sizeof(double);     // A, B, C
   if (tc2_wanted(*this)) b += tc2_bytes(tc_mode, nblk, nparts, max_m);
-  else if (oz_wanted(*this)) b += oz_bytes(nblk, nparts, max_m);
+  else if (oz_wanted(*this)) b += oz_bytes(nblk, nparts, nseps, max_m);
   else if (tc_mode >= 0) b += 3 * nblk * sizeof(float);
   b += 4 * nblk * es;                       // G, Acal, ZL, ZR
   b += nvec * es;                           // z
@@ -452,6 +460,17 @@ int Level::allocate() {
            oz_make_map(Z.V, np, m, oz_box_rows_right(), Z.gj_maps[1], 32);
       if (!ok) return set_error(DM_ECUDA, "tensor map creation for the blocked inversion failed (m = %d)", m);
       Z.gj = true;
+    }
+    if (nseps > 0 && oz_asm_wanted()) {
+      OzAsm& a = Z.as;
+      DM_ALLOC(a.Cq, nseps * sl);
+      DM_ALLOC(a.S, 4LL * nseps * sl);
+      DM_ALLOC(a.eCq, nseps * ex);
+      DM_ALLOC(a.eS, 4LL * nseps * ex);
+      ok = oz_make_map(a.Cq, nseps, m, oz_box_rows_left(), a.maps[0]) &&
+           oz_make_map(a.S, 4LL * nseps, m, oz_box_rows_right(), a.maps[1]);
+      if (!ok) return set_error(DM_ECUDA, "tensor map creation for the sliced assembly failed (m = %d)", m);
+      Z.asm_on = true;
     }
   } else if (tc_mode >= 0) {
     DM_ALLOC(A32, nblk * sizeof(float));
@@ -651,7 +670,7 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   const int m = L.max_m;
   const long long nb = L.nblk / ((long long)m * m);
   double* G = static_cast<double*>(L.G);
-  OzOut out;
+  OzOut out{};
   out.B = L.B;
   out.G = G;
   out.Acal = static_cast<double*>(L.Acal);
@@ -734,7 +753,11 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   if constexpr (std::is_same<T, double>::value) {
     if (L.oz.on) {
       factor_level_oz(L, st, pf);
-      if (L.supp)
+      if (L.supp && L.oz.asm_on)
+        DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
+                  launch_oz_assemble(L.d_seps, L.nseps, L.max_m, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C,
+                                     L.oz.as, L.oz.eA, L.oz.maps[1], L.d_err, st));
+      else if (L.supp)
         DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
                   launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
                                        L.supp->C, st));

@@ -143,12 +143,26 @@ bool tc2_eligible(int m);
 struct OzOut {
   const double* B;
   double *G, *Acal, *ZL, *ZR, *Y;  // Y: Y_{t+1} per subsystem (rolling, float64)
+  // the supplementary blocks (Eq. e2311), one separator per CTA row
+  const SepDesc* seps;
+  double *HA, *HB, *HC;
 };
 bool oz_eligible(int m);
 int oz_slice_blocks_bytes(int m);
 bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out, int kdim = 0);
 int oz_box_rows_left();
 int oz_box_rows_right();
+// The supplementary blocks of a sliced level (Eq. e2311) as digit-sliced
+// products: C_q row slices and the four boundary spike blocks' column slices
+// per separator, then HB = B_q - A_q ZR - C_q ZL, HA = -A_q ZL, HC = -C_q ZR.
+struct OzAsm {
+  void *Cq, *S;   // [separator][9][m][m] C_q rows; [4 separator + b][9][m][m] spike columns
+  int *eCq, *eS;  // their scales
+  alignas(64) unsigned char maps[2][128];  // left Cq, right S
+};
+void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, const double* C, const double* ZL,
+                        const double* ZR, double* HA, double* HB, double* HC, const OzAsm& a, const int* eA,
+                        const void* mapA, int* errflag, cudaStream_t st);
 void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st);
 struct OzSliceJob {
   const double* src;

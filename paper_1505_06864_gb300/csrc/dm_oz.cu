@@ -115,6 +115,10 @@ namespace oz {
 // KIND 0: launch A, 1: launch B (forward step `step`), 2: backward step
 // `step`.  blockIdx.y = subsystem; blockIdx.x = ((2 * M-tile + product) *
 // ntn + N-tile).  Exponent arrays: [block][m] ints, indexed like the slices.
+// KIND 4, 5: the supplementary blocks of separator blockIdx.y (Eq. e2311),
+// left A_q / C_q: KIND 4 j = 0: HB = B_q - A_q ZR^j[q-1], j = 1: HA = -A_q
+// ZL^j[q-1]; KIND 5 j = 0: HB -= C_q ZL^{j+1}[q+1], j = 1: HC = -C_q
+// ZR^{j+1}[q+1] (parts unused).
 // KIND 3: the trailing update of panel `step` (columns K = [32 step, 32 step
 // + 32)) of the blocked Gauss-Jordan inversion of block row `aux`:
 // M[:, J] = (M[:, J] with the rows K zeroed) + U V, U the eliminated panel,
@@ -129,12 +133,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int err, nissued, ncons;
   const int pidx = blockIdx.y;
-  const PartDesc p = parts[pidx];
+  PartDesc p{};
+  SepDesc sd{};
+  if constexpr (KIND >= 4)
+    sd = out.seps[pidx];  // blockIdx.y = separator
+  else
+    p = parts[pidx];
   const int tn = blockIdx.x % ntn, rest = blockIdx.x / ntn, j = rest & 1, tm = rest >> 1;
   if (tm * MT >= m || tn * NT >= m) return;
-  int t;
+  int t = 0;
   bool act;
-  if (KIND == 0) {
+  if (KIND == 4) {
+    act = j == 0 || (sd.flags & HAS_HA) != 0;
+  } else if (KIND == 5) {
+    act = j == 0 || (sd.flags & HAS_HC) != 0;
+  } else if (KIND == 0) {
     t = step;
     act = t < p.L && (j == 0 ? (t < p.L - 1 || (p.flags & HAS_RIGHT) != 0) : (p.flags & HAS_LEFT) != 0);
   } else if (KIND == 1) {
@@ -151,7 +164,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long mm = (long long)m * m;
   const int b0 = (int)(p.blk / mm);
   int zl, zr;
-  if (KIND == 3) {
+  if (KIND == 4) {
+    zl = (int)(sd.blk_q / mm);  // A_q (all blocks)
+    zr = 4 * pidx + j;          // ZR^j[q-1]^T / ZL^j[q-1]^T
+  } else if (KIND == 5) {
+    zl = pidx;                  // C_q (per separator)
+    zr = 4 * pidx + 2 + j;      // ZL^{j+1}[q+1]^T / ZR^{j+1}[q+1]^T
+  } else if (KIND == 3) {
     zl = pidx;  // U slices (rolling)
     zr = pidx;  // V^T slices (rolling)
   } else if (KIND == 0) {
@@ -309,9 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
       if (n < m && outside) {
         const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3;
+        const bool hb = KIND >= 4 && j == 0;
         double in[8];
-        if (rmw || dnext || gj) {
-          const double* src = rmw ? out.ZL + o : (gj ? out.G + o : out.B + o + mm);
+        if (rmw || dnext || gj || hb) {
+          const double* src = rmw    ? out.ZL + o
+                              : gj   ? out.G + o
+                              : hb   ? (KIND == 4 ? out.B + sd.blk_q : out.HB + sd.hblk)
+                                     : out.B + o + mm;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int rr = rbase + r0 + 4 * i;
@@ -324,7 +347,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (rr >= m) continue;
           const double w = stg[rl * 9 + cl];
           const long long e = (long long)rr * m + n;
-          if (KIND == 0) {
+          if (KIND >= 4) {
+            if (j == 0)
+              out.HB[sd.hblk + e] = in[i] - w;               // HB = B_q - A_q ZR, then HB -= C_q ZL
+            else
+              (KIND == 4 ? out.HA : out.HC)[sd.hblk + e] = -w;  // HA = -A_q ZL, HC = -C_q ZR
+          } else if (KIND == 0) {
             double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
             d[o + e] = w;
           } else if (dnext) {
@@ -892,6 +920,31 @@ __global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restric
     slice_cols_group(jb.src + sblk * mm, dst, dq, jb.exps, m, g, red, s_e, tile);
 }
 
+// The assembly's operands per separator s (blockIdx.x = s * groups + group,
+// blockIdx.y = job): job 0 C_q rows -> Cq slot s; jobs 1-4 the boundary
+// spike blocks as columns -> S slot 4 s + job - 1: ZR^j[q-1], ZL^j[q-1] (only
+// with HA), ZL^{j+1}[q+1], ZR^{j+1}[q+1] (only with HC).
+__global__ void __launch_bounds__(256) k_oz_slice_seps(const SepDesc* __restrict__ seps, int m,
+                                                       const double* __restrict__ C, const double* __restrict__ ZL,
+                                                       const double* __restrict__ ZR, __nv_bfloat16* __restrict__ Cq,
+                                                       int* __restrict__ eCq, __nv_bfloat16* __restrict__ Sp,
+                                                       int* __restrict__ eS) {
+  __shared__ uint32_t red[8][32];
+  __shared__ int s_e[32];
+  __shared__ unsigned long long tile[32][33];
+  const int groups = (m + 31) / 32;
+  const int s = blockIdx.x / groups, g = blockIdx.x - s * groups, job = blockIdx.y;
+  const SepDesc sd = seps[s];
+  if (job == 0) {
+    slice_rows_group(C + sd.blk_q, Cq, s, eCq, m, g);
+    return;
+  }
+  if ((job == 2 && !(sd.flags & HAS_HA)) || (job == 4 && !(sd.flags & HAS_HC))) return;
+  const double* src = job == 1 ? ZR + sd.blk_prev : job == 2 ? ZL + sd.blk_prev : job == 3 ? ZL + sd.blk_next
+                                                                                         : ZR + sd.blk_next;
+  slice_cols_group(src, Sp, 4LL * s + job - 1, eS, m, g, red, s_e, tile);
+}
+
 }  // namespace oz
 
 // ---------------------------------------------------------------- host side
@@ -1007,8 +1060,26 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
   if (kind == 0) DM_OZ(0);
   else if (kind == 1) DM_OZ(1);
   else if (kind == 2) DM_OZ(2);
-  else DM_OZ(3);
+  else if (kind == 3) DM_OZ(3);
+  else if (kind == 4) DM_OZ(4);
+  else DM_OZ(5);
 #undef DM_OZ
+}
+
+void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, const double* C, const double* ZL,
+                        const double* ZR, double* HA, double* HB, double* HC, const OzAsm& a, const int* eA,
+                        const void* mapA, int* errflag, cudaStream_t st) {
+  if (nseps <= 0) return;
+  oz::k_oz_slice_seps<<<dim3(nseps * ((m + 31) / 32), 5), 256, 0, st>>>(
+      seps, m, C, ZL, ZR, static_cast<__nv_bfloat16*>(a.Cq), a.eCq, static_cast<__nv_bfloat16*>(a.S), a.eS);
+  OzOut out{B, nullptr, nullptr, nullptr, nullptr, nullptr, seps, HA, HB, HC};
+  unsigned char maps3[3 * 128];
+  std::memcpy(maps3, mapA, 128);
+  std::memcpy(maps3 + 128, a.maps[1], 128);
+  std::memcpy(maps3 + 256, a.maps[1], 128);
+  launch_oz_step(4, nullptr, nseps, 0, m, out, eA, a.eS, a.eS, maps3, errflag, st);
+  std::memcpy(maps3, a.maps[0], 128);
+  launch_oz_step(5, nullptr, nseps, 0, m, out, a.eCq, a.eS, a.eS, maps3, errflag, st);
 }
 
 }  // namespace dm

@@ -106,6 +106,9 @@ struct OzLevel {
   void *U = nullptr, *V = nullptr;
   int *eU = nullptr, *eV = nullptr, *piv = nullptr;
   alignas(64) unsigned char gj_maps[2][128];
+  // the supplementary blocks on the tensor cores (levels with a supplementary level)
+  bool asm_on = false;
+  OzAsm as;
 };
 
 // One level of the recursion: a set of independent systems, each split into

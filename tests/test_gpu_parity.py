@@ -589,6 +589,32 @@ def test_fp64_blocked_inverse(dm, monkeypatch, N, m, r, P, levels):
         check(xs["cluster"], xo, tol)
 
 
+@pytest.mark.parametrize("N,m,r,P,levels", [(64, 16, 1, 4, 1), (40, 64, 2, 6, 2), (30, 40, 3, 5, 1),
+                                            (24, 256, 1, 5, 1), (60, 32, 2, 12, 3)])
+def test_fp64_sliced_assembly(dm, monkeypatch, N, m, r, P, levels):
+    """The supplementary blocks (Eq. e2311) as digit-sliced tensor-core
+    products (the default on sliced levels) and by the float64 kernel
+    (DM_FP64_ASSEMBLY=fma): both against the oracle and against each other;
+    separators with and without both off-diagonal blocks, recursion levels
+    whose own supplementary blocks are sliced too, m not a multiple of 32."""
+    for gen in ("dominant", "conditioned"):
+        s = (w.dominant_system(N, m, r, 700 + N) if gen == "dominant"
+             else w.conditioned_system(N, m, r, 701 + N, cond=1e3))
+        xs = {}
+        for mode in ("sliced", "fma"):
+            if mode == "fma":
+                monkeypatch.setenv("DM_FP64_ASSEMBLY", "fma")
+            x, rel, info = solve(dm, s, P, levels)
+            assert rel < 1e-13
+            xs[mode] = x
+        monkeypatch.delenv("DM_FP64_ASSEMBLY")
+        xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
+        tol = TOL64 if gen == "dominant" else 1e-10
+        check(xs["sliced"], xo, tol)
+        check(xs["fma"], xo, tol)
+        check(xs["sliced"], xs["fma"], tol)
+
+
 def test_singular_block_reported_blocked_inverse(dm):
     """A zero Schur complement on a sliced level (m = 16): the blocked
     inversion reports DM_ESINGULAR with the block row, like the cluster one."""
