@@ -262,6 +262,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&accb);
   }
   if (warp < 2) __syncwarp();
+  // Before the accumulators are ready, every thread loads what its epilogue
+  // needs besides them: its row's scale, the column scales of its warp's 24
+  // columns (one per lane, passed by shuffle) and the values its stores
+  // update (they do not depend on the products), so that the epilogue waits
+  // on tensor memory only.  Warps 2-7 do it while the MMAs run.
+  const int quarter = warp & 3, half = warp >> 2;
+  const int rbase = tm * MT + quarter * 32, row = rbase + lane;
+  const int er = row < m ? lexp[(long long)zl * m + row] : 0;
+  int fexp = 0;
+  {
+    const int n = tn * NT + half * (NT / 2) + lane;
+    if (lane < NT / 2 && n < m) fexp = rexp[(long long)zr * m + n];
+  }
+  const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3, hb = KIND >= 4 && j == 0;
+  const long long o = p.blk + (long long)t * mm;
+  const int cl = lane & 7, r0 = lane >> 3;
+  const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
+  double inpre[NT / 16][8];
+  if (rmw || dnext || gj || hb) {
+    const double* src = rmw    ? out.ZL + o
+                        : gj   ? out.G + o
+                        : hb   ? (KIND == 4 ? out.B + sd.blk_q : out.HB + sd.hblk)
+                               : out.B + o + mm;
+#pragma unroll
+    for (int ci = 0; ci < NT / 16; ++ci) {
+      const int n = tn * NT + half * (NT / 2) + 8 * ci + cl;
+      const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rr = rbase + r0 + 4 * i;
+        inpre[ci][i] = (n < m && outside && rr < m && !(gj && rr >= k0 && rr < k0 + 32))
+                           ? src[(long long)rr * m + n]
+                           : 0.0;
+      }
+    }
+  }
   bool ok = mbar_wait(&accb, 0u);
   tc_fence_after();
   ok = __syncthreads_and(ok) && !err;
@@ -279,16 +315,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the tile's columns (a warp reaches only its own 32 lanes).  Results
     // are staged through a per-warp 32 x 9 float64 tile so that row-major
     // writes are coalesced.
-    const int quarter = warp & 3, half = warp >> 2;
     double* stg = reinterpret_cast<double*>(base) + warp * (32 * 9);
-    const int rbase = tm * MT + quarter * 32, row = rbase + lane;
-    const int er = row < m ? lexp[(long long)zl * m + row] : 0;
     const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-    const long long o = p.blk + (long long)t * mm;
     // acc_d below 2^22 for every d (then the float32 magic-number
     // conversion is exact): K = 32, or K = m <= 112 (acc_d <= 9 K 63^2)
     const bool small = KIND == 3 || m <= 112;
-    for (int ch = half * (NT / 2); ch < (half + 1) * (NT / 2); ch += 8) {
+#pragma unroll
+    for (int ci = 0; ci < NT / 16; ++ci) {
+      const int ch = half * (NT / 2) + 8 * ci;
       uint32_t r[NACC][8];
 #pragma unroll
       for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
@@ -298,6 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int n = tn * NT + ch + c;
+        const int k = er + __shfl_sync(0xffffffffu, fexp, 8 * ci + c);
         int a[NACC];
 #pragma unroll
         for (int dd = 0; dd < NACC; ++dd)
@@ -305,10 +340,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long hi = (long long)(a[0] * 64 + a[1]) * 4096 + (a[2] * 64 + a[3]);
         const long long lo = ((long long)(a[4] * 64 + a[5]) * 4096 + (a[6] * 64 + a[7])) * 4096 + (a[8] * 64 + a[9]);
         double val = 0.0;
-        const bool kept = KIND != 3 || n < 32 * step || n >= 32 * step + 32;  // KIND 3: not the panel's columns
+        const bool kept = KIND != 3 || n < k0 || n >= k0 + 32;  // KIND 3: not the panel's columns
         if (row < m && n < m && kept) {
           const float a2 = __uint_as_float(r[0][c]);
-          const int k = er + rexp[(long long)zr * m + n];
           if (a2 != a2)  // NaN or infinite operand: every digit is NaN, acc_2 included
             val = __longlong_as_double(0x7ff8000000000000ll);
           else if ((hi | lo) == 0)  // also the zero rows and columns, whose scale is the smallest
@@ -321,26 +355,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         stg[lane * 9 + c] = val;
       }
       __syncwarp();
-      // row-major float64 results: lane = (row quarter, column), 8 row
-      // quads; the loads an update needs are gathered before any store
-      const int cl = lane & 7, r0 = lane >> 3, n = tn * NT + ch + cl;
-      const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
+      // row-major float64 results: lane = (row quarter, column), 8 row quads
+      const int n = tn * NT + ch + cl;
       const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
       if (n < m && outside) {
-        const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3;
-        const bool hb = KIND >= 4 && j == 0;
-        double in[8];
-        if (rmw || dnext || gj || hb) {
-          const double* src = rmw    ? out.ZL + o
-                              : gj   ? out.G + o
-                              : hb   ? (KIND == 4 ? out.B + sd.blk_q : out.HB + sd.hblk)
-                                     : out.B + o + mm;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int rr = rbase + r0 + 4 * i;
-            in[i] = (rr < m && !(gj && rr >= k0 && rr < k0 + 32)) ? src[(long long)rr * m + n] : 0.0;
-          }
-        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int rl = r0 + 4 * i, rr = rbase + rl;
@@ -349,22 +367,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           const long long e = (long long)rr * m + n;
           if (KIND >= 4) {
             if (j == 0)
-              out.HB[sd.hblk + e] = in[i] - w;               // HB = B_q - A_q ZR, then HB -= C_q ZL
+              out.HB[sd.hblk + e] = inpre[ci][i] - w;           // HB = B_q - A_q ZR, then HB -= C_q ZL
             else
               (KIND == 4 ? out.HA : out.HC)[sd.hblk + e] = -w;  // HA = -A_q ZL, HC = -C_q ZR
           } else if (KIND == 0) {
             double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
             d[o + e] = w;
           } else if (dnext) {
-            out.G[o + mm + e] = in[i] - w;                // D_{t+1} = B_{t+1} - A_{t+1} Acal_t
+            out.G[o + mm + e] = inpre[ci][i] - w;                // D_{t+1} = B_{t+1} - A_{t+1} Acal_t
           } else if (KIND == 1) {
-            out.Y[(long long)pidx * mm + e] = -w;         // Y_{t+1} = -A_{t+1} Bcal_t
+            out.Y[(long long)pidx * mm + e] = -w;                // Y_{t+1} = -A_{t+1} Bcal_t
           } else if (rmw) {
-            out.ZL[o + e] = in[i] - w;                    // ZL_t -= Acal_t ZL_{t+1}
+            out.ZL[o + e] = inpre[ci][i] - w;                    // ZL_t -= Acal_t ZL_{t+1}
           } else if (gj) {
-            out.G[o + e] = in[i] + w;                     // Gauss-Jordan trailing update
+            out.G[o + e] = inpre[ci][i] + w;                     // Gauss-Jordan trailing update
           } else {
-            out.ZR[o + e] = -w;                           // ZR_t = -Acal_t ZR_{t+1}
+            out.ZR[o + e] = -w;                                  // ZR_t = -Acal_t ZR_{t+1}
           }
         }
       }
