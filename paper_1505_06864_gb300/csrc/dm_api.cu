@@ -698,17 +698,18 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   cs.bytes = 26.0 * m * m;  // one block: float64 read, nine bf16 slices written
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t], nbk = L.active_back[t];
-    if (Z.gj)
+    if (Z.gj) {  // the blocked inversion writes G_t's row slices itself
       DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np,
                 launch_gj_inverse(L.d_parts, np, t, m, L.B, G, Z.piv, Z.U, Z.eU, Z.V, Z.eV, Z.gj_maps, L.status,
-                                  L.d_err, st));
-    else
+                                  L.d_err, Z.G, Z.eG, st));
+    } else {
       DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<double>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
-    OzSliceJobs jg;
-    jg.job[0] = job(G, Z.G, Z.eG, 0);
-    Cost c0 = cs;
-    c0.bytes *= np;
-    DM_LAUNCH(pf, st, K_TC_CONVERT, c0, np, launch_oz_slice_jobs(L.d_parts, np, t, m, jg, 1, st));
+      OzSliceJobs jg;
+      jg.job[0] = job(G, Z.G, Z.eG, 0);
+      Cost c0 = cs;
+      c0.bytes *= np;
+      DM_LAUNCH(pf, st, K_TC_CONVERT, c0, np, launch_oz_slice_jobs(L.d_parts, np, t, m, jg, 1, st));
+    }
     DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdA[t], np,
               launch_oz_step(0, L.d_parts, np, t, m, out, lexp[0], r0exp[0], r1exp[0], maps[0], L.d_err, st));
     OzSliceJobs ja;

@@ -180,11 +180,12 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
                     int aux = 0);
 // Blocked Gauss-Jordan inversion with the rank-32 updates as digit-sliced
 // tensor-core products; maps2 = the panel-slice maps (U with 128-row boxes,
-// V with 48-row boxes), piv [nparts][m], Us / Vs [nparts][9][m][32] bf16,
-// Uexp / Vexp [nparts][m].
+// V with 48-row boxes), piv [nparts][m] (the column permutation), Us / Vs
+// [nparts][9][m][32] bf16, Uexp / Vexp [nparts][m]; Gs / eG receive the row
+// slices of the inverses ([nparts][9][m][m] bf16, [nparts][m]).
 void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
                        void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
-                       cudaStream_t st);
+                       void* Gs, int* eG, cudaStream_t st);
 int tc2_ntile(int m);
 bool tc2_make_map(int mode, const void* base, long long blocks, int m, int box_rows, void* out);
 int tc2_map_bytes();

@@ -527,8 +527,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__
 //      the row exchanges to the other columns and writes U's row slices and
 //      the column slices of V = M[K, J] (the pivot rows outside K).
 //   2. k_oz_step<3>: M[:, J] = (M[:, J], rows K zeroed) + U V.
-// After the last panel, k_gj_unscramble undoes the row exchanges on the
-// columns (column c of the working matrix is column inv_idx[c] of D^{-1}).
+// After the last panel, k_gj_finish undoes the row exchanges on the columns
+// (column c of the working matrix is column piv[c] of D^{-1}) and writes the
+// row slices of the inverse.
 __global__ void __launch_bounds__(256) k_gj_copy_b0(const PartDesc* __restrict__ parts, int m,
                                                     const double* __restrict__ B, double* __restrict__ G) {
   const PartDesc p = parts[blockIdx.x];
@@ -647,7 +648,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   // this CTA's own
   __shared__ GjKey wbest[kGjWarps];
   __shared__ __align__(16) double sprow[kGjWarps][32], xrow[kGjWarps][32];
-  __shared__ int piv_s[32], perm[kMaxMTensor];
+  __shared__ int piv_s[32], perm[kMaxMTensor], cperm[kMaxMTensor];
   const int rank = (int)cl.block_rank();
   const int q = blockIdx.x / kGjCS;
   const PartDesc p = parts[q];
@@ -707,7 +708,6 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     sp[lane] = lane == 0 ? inv : prow * inv;  // the scaled pivot row
     xr[lane] = xk;                            // the old row k
     if (tid == 0) piv_s[0] = r;
-    if (rank == 0 && tid == 0) piv[(long long)q * m + k0] = r;
     __syncwarp();
   }
 #pragma unroll 1
@@ -790,7 +790,6 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       sp[lane] = lane == 0 ? inv : u * inv;
       xr[lane] = x;
       if (tid == 0) piv_s[kk + 1] = r;
-      if (rank == 0 && tid == 0) piv[(long long)q * m + k + 1] = r;
       __syncwarp();
     }
   }
@@ -823,16 +822,31 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       }
     }
   }
-  // net row permutation of the pivots: position x ends up holding row perm[x]
-  for (int c = tid; c < m; c += kGjThreads) perm[c] = c;
+  // net row permutation of the pivots: position x ends up holding row perm[x];
+  // rank 0 also carries the inversion's column permutation (the exchanges of
+  // every panel so far applied in pivot order, from the identity at panel 0):
+  // column c of the final working matrix is column piv[c] of D^{-1}
+  int* colp = piv + (long long)q * m;
+  for (int c = tid; c < m; c += kGjThreads) {
+    perm[c] = c;
+    if (rank == 0) cperm[c] = panel == 0 ? c : colp[c];
+  }
   __syncthreads();
   if (tid == 0)
     for (int kk = 0; kk < kw; ++kk) {
-      const int a = k0 + kk, b = piv_s[kk], tmp = perm[a];
+      const int a = k0 + kk, b = piv_s[kk];
+      int tmp = perm[a];
       perm[a] = perm[b];
       perm[b] = tmp;
+      if (rank == 0) {
+        tmp = cperm[a];
+        cperm[a] = cperm[b];
+        cperm[b] = tmp;
+      }
     }
   __syncthreads();
+  if (rank == 0)
+    for (int c = tid; c < m; c += kGjThreads) colp[c] = cperm[c];
   // a thread per column outside the panel (shared among the cluster's CTAs):
   // the column slices of V = the pivot rows (transposed: row j of the copy
   // holds V[0..31][j]; zero inside the panel), then the rows outside K that
@@ -875,31 +889,62 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-__global__ void __launch_bounds__(256) k_gj_unscramble(const PartDesc* __restrict__ parts, int t, int m,
-                                                       double* __restrict__ G, const int* __restrict__ piv) {
-  __shared__ int idx[kMaxMTensor], inv_idx[kMaxMTensor];
-  __shared__ double rowbuf[8][kMaxMTensor];
-  const int q = blockIdx.x;
+// After the last panel: the column permutation undone and the row slices of
+// the block inverse G_t written (the left operand of the next products), one
+// pass: a CTA takes 32 rows of one block (blockIdx.x = block * groups +
+// group), a warp a row at a time: the row is read once, scattered to its
+// final column order in shared memory (its largest magnitude does not depend
+// on the order), then written back as float64 and as nine digit slices.
+__global__ void __launch_bounds__(256) k_gj_finish(const PartDesc* __restrict__ parts, int t, int m,
+                                                   double* __restrict__ G, const int* __restrict__ piv,
+                                                   __nv_bfloat16* __restrict__ Gs, int* __restrict__ eG) {
+  __shared__ int ip[kMaxMTensor];
+  __shared__ __align__(16) double rowb[8][kMaxMTensor];
+  const int groups = (m + 31) / 32;
+  const int q = blockIdx.x / groups, g = blockIdx.x - q * groups;
   const PartDesc p = parts[q];
   if (t >= p.L) return;
   const long long mm = (long long)m * m;
   double* M = G + p.blk + (long long)t * mm;
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < m; ++c) idx[c] = c;
-    for (int k = m - 1; k >= 0; --k) {
-      const int r = piv[(long long)q * m + k];
-      const int tmp = idx[k];
-      idx[k] = idx[r];
-      idx[r] = tmp;
-    }
-    for (int c = 0; c < m; ++c) inv_idx[idx[c]] = c;
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < m; r += 8) {
-    for (int c = lane; c < m; c += 32) rowbuf[warp][c] = M[(long long)r * m + c];
+  for (int c = threadIdx.x; c < m; c += blockDim.x) ip[c] = piv[(long long)q * m + c];
+  __syncthreads();
+  double* rb = rowb[warp];
+  const int rend = min(m, 32 * g + 32);
+  for (int r = 32 * g + warp; r < rend; r += 8) {
+    uint32_t hmax = 0;
+    for (int c = lane; c < m; c += 32) {
+      const double v = M[(long long)r * m + c];
+      rb[ip[c]] = v;
+      hmax = max(hmax, (uint32_t)(__double_as_longlong(v) >> 32) & 0x7fffffffu);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    const int e = scale_exponent(hmax);
+    if (lane == 0) eG[(long long)q * m + r] = e;
     __syncwarp();
-    for (int c = lane; c < m; c += 32) M[(long long)r * m + inv_idx[c]] = rowbuf[warp][c];
+    for (int c0 = lane * 8; c0 < m; c0 += 256) {  // m % 8 == 0
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double2 d2 = *reinterpret_cast<const double2*>(rb + c0 + u);
+        v[u] = d2.x;
+        v[u + 1] = d2.y;
+        *reinterpret_cast<double2*>(M + (long long)r * m + c0 + u) = d2;
+      }
+      uint32_t d[8][S];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) digits9((unsigned long long)__double_as_longlong(v[u]), e, d[u]);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        uint4 w;
+        w.x = (d[0][sl] >> 16) | (d[1][sl] & 0xffff0000u);
+        w.y = (d[2][sl] >> 16) | (d[3][sl] & 0xffff0000u);
+        w.z = (d[4][sl] >> 16) | (d[5][sl] & 0xffff0000u);
+        w.w = (d[6][sl] >> 16) | (d[7][sl] & 0xffff0000u);
+        *reinterpret_cast<uint4*>(Gs + ((long long)q * S + sl) * mm + (long long)r * m + c0) = w;
+      }
+    }
     __syncwarp();
   }
 }
@@ -1030,7 +1075,7 @@ void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, co
 // subsystem (in place in G; t = 0 starts from B_0).
 void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
                        void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
-                       cudaStream_t st) {
+                       void* Gs, int* eG, cudaStream_t st) {
   if (nparts <= 0) return;
   if (t == 0) oz::k_gj_copy_b0<<<nparts, 256, 0, st>>>(parts, m, B, G);
   OzOut out{nullptr, G, nullptr, nullptr, nullptr, nullptr};
@@ -1055,7 +1100,8 @@ void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const do
                        static_cast<__nv_bfloat16*>(Vs), Vexp, status);
     if (m > 32) launch_oz_step(3, parts, nparts, pnl, m, out, Uexp, Vexp, Vexp, maps3, errflag, st, t);
   }
-  oz::k_gj_unscramble<<<nparts, 256, 0, st>>>(parts, t, m, G, piv);
+  oz::k_gj_finish<<<nparts * ((m + 31) / 32), 256, 0, st>>>(parts, t, m, G, piv, static_cast<__nv_bfloat16*>(Gs),
+                                                             eG);
 }
 
 void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,
