@@ -49,7 +49,8 @@ namespace dm {
 namespace oz {
 using namespace ptx;
 
-constexpr int kThreads = 256;  // warps 0, 1: TMA producer and MMA issuer; all 8: epilogue
+constexpr int kEpiWarps = 8;                 // epilogue warps 2 .. 9
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0: TMA producer, warp 1: MMA issuer
 constexpr int MT = 128;          // rows per tile
 constexpr int NT = 48;           // columns per tile
 constexpr int KS = 32;           // K elements per stage (64-byte rows, 64-byte swizzle)
@@ -62,7 +63,8 @@ constexpr int RSL = NT * ROWB;   // one right slice: 3 KB
 constexpr int LBYTES = S * LSL;  // 72 KB
 constexpr int RBYTES = (S + 1) * RSL;  // 30 KB with the zero slice
 constexpr int STAGE = LBYTES + RBYTES;
-constexpr int SMEM = 1024 + kStages * STAGE;
+constexpr int STG = 32 * 9;                  // an epilogue warp's 32 x 9 float64 staging tile
+constexpr int SMEM = 1024 + kStages * STAGE + kEpiWarps * STG * 8;
 constexpr uint32_t kCols = 512;
 constexpr uint32_t kSbo = 8 * ROWB;  // 512-byte swizzle atoms
 constexpr uint64_t kLayout = 4;       // 64-byte swizzle
@@ -75,9 +77,6 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm,
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
-
-// 2^k as a float64 for -1022 <= k <= 1023.
-__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
 // The integer value of an integer-valued float32 |v| < 2^22: v + 1.5 2^23
 // lies in [2^23, 2^24), where the float's low mantissa bits are v's.
@@ -97,7 +96,7 @@ __device__ __forceinline__ int acc_int(uint32_t b) {
 __device__ __forceinline__ double i2d_scaled(long long x, int s) {
   const unsigned long long sg = (unsigned long long)x & 0x8000000000000000ull;
   const unsigned long long a = (unsigned long long)(x < 0 ? -x : x);
-  const int lz = __clzll(a);                        // >= 11 for a < 2^53
+  const int lz = __clzll(a);                              // >= 11 for a < 2^53
   const unsigned long long mant = a << ((lz - 11) & 63);  // leading bit at 52
   // the leading bit adds one to the exponent field
   const unsigned long long ex = (unsigned long long)(1022 + 63 - lz + s);
@@ -113,80 +112,109 @@ struct OzMaps {
 namespace oz {
 
 // KIND 0: launch A, 1: launch B (forward step `step`), 2: backward step
-// `step`.  blockIdx.y = subsystem; blockIdx.x = ((2 * M-tile + product) *
-// ntn + N-tile).  Exponent arrays: [block][m] ints, indexed like the slices.
-// KIND 4, 5: the supplementary blocks of separator blockIdx.y (Eq. e2311),
-// left A_q / C_q: KIND 4 j = 0: HB = B_q - A_q ZR^j[q-1], j = 1: HA = -A_q
-// ZL^j[q-1]; KIND 5 j = 0: HB -= C_q ZL^{j+1}[q+1], j = 1: HC = -C_q
-// ZR^{j+1}[q+1] (parts unused).
+// `step`, over the subsystems.  Exponent arrays: [block][m] ints, indexed
+// like the slices.
 // KIND 3: the trailing update of panel `step` (columns K = [32 step, 32 step
 // + 32)) of the blocked Gauss-Jordan inversion of block row `aux`:
 // M[:, J] = (M[:, J] with the rows K zeroed) + U V, U the eliminated panel,
 // V = M[K, J] before the update (both as slices, K = 32), J the other columns.
+// KIND 4, 5: the supplementary blocks of a separator (Eq. e2311), left A_q /
+// C_q: KIND 4 j = 0: HB = B_q - A_q ZR^j[q-1], j = 1: HA = -A_q ZL^j[q-1];
+// KIND 5 j = 0: HB -= C_q ZL^{j+1}[q+1], j = 1: HC = -C_q ZR^{j+1}[q+1]
+// (parts unused, out.seps instead).
+//
+// A tile = (subsystem or separator, product j, 128-row M-tile, 48-column
+// N-tile); tile = ((unit * 2 + j) * ntm + M-tile) * ntn + N-tile (KIND 3,
+// one product: (unit * ntm + M-tile) * ntn + N-tile).
+struct OzTile {
+  PartDesc p;
+  SepDesc sd;
+  int unit, j, tm, tn, t, zl, zr;
+  bool act;
+};
+
+template <int KIND>
+__device__ __forceinline__ OzTile oz_tile(int tile, const PartDesc* __restrict__ parts, const OzOut& out, int step,
+                                          int aux, int m, int ntm, int ntn) {
+  OzTile w{};
+  constexpr int nj = KIND == 3 ? 1 : 2;  // KIND 3 has one product
+  const int per = nj * ntm * ntn;
+  w.unit = tile / per;
+  const int rest = tile - w.unit * per;
+  w.tn = rest % ntn;
+  const int r2 = rest / ntn;
+  w.j = nj == 1 ? 0 : (r2 & 1);
+  w.tm = nj == 1 ? r2 : (r2 >> 1);
+  if constexpr (KIND >= 4)
+    w.sd = out.seps[w.unit];
+  else
+    w.p = parts[w.unit];
+  const PartDesc& p = w.p;
+  const int j = w.j, pidx = w.unit;
+  bool act;
+  if (KIND == 4) {
+    act = j == 0 || (w.sd.flags & HAS_HA) != 0;
+  } else if (KIND == 5) {
+    act = j == 0 || (w.sd.flags & HAS_HC) != 0;
+  } else if (KIND == 0) {
+    w.t = step;
+    act = w.t < p.L && (j == 0 ? (w.t < p.L - 1 || (p.flags & HAS_RIGHT) != 0) : (p.flags & HAS_LEFT) != 0);
+  } else if (KIND == 1) {
+    w.t = step;
+    act = w.t < p.L - 1 && (j == 0 || (p.flags & HAS_LEFT) != 0);
+  } else if (KIND == 2) {
+    w.t = p.L - 2 - step;
+    act = w.t >= 0 && (j == 0 ? (p.flags & HAS_LEFT) != 0 : (p.flags & HAS_RIGHT) != 0);
+  } else {
+    w.t = aux;
+    act = w.t < p.L && j == 0;
+  }
+  w.act = act && w.tm * MT < m && w.tn * NT < m;
+  const long long mm = (long long)m * m;
+  const int b0 = (int)(p.blk / mm), t = w.t;
+  if (KIND == 4) {
+    w.zl = (int)(w.sd.blk_q / mm);  // A_q (all blocks)
+    w.zr = 4 * pidx + j;            // ZR^j[q-1]^T / ZL^j[q-1]^T
+  } else if (KIND == 5) {
+    w.zl = pidx;                    // C_q (per separator)
+    w.zr = 4 * pidx + 2 + j;        // ZL^{j+1}[q+1]^T / ZR^{j+1}[q+1]^T
+  } else if (KIND == 3) {
+    w.zl = pidx;  // U slices (rolling)
+    w.zr = pidx;  // V^T slices (rolling)
+  } else if (KIND == 0) {
+    w.zl = pidx;                     // G_t slices (rolling)
+    w.zr = j == 0 ? b0 + t : pidx;   // C_t^T (all blocks) / Y_t^T (rolling)
+  } else if (KIND == 1) {
+    w.zl = b0 + t + 1;                          // A_{t+1}
+    w.zr = j == 0 ? pidx : 2 * pidx + (t & 1);  // Acal_t^T / Bcal_t^T
+  } else {
+    w.zl = b0 + t;                    // Acal_t
+    w.zr = 2 * pidx + ((t + 1) & 1);  // ZL_{t+1}^T / ZR_{t+1}^T
+  }
+  return w;
+}
+
+// Persistent: a CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...  Warp 0 (one lane) streams every tile's K slabs by TMA into a two-stage
+// ring and runs ahead into the next tile; warp 1 (one lane) issues the MMAs
+// of a tile once the epilogue has drained the accumulators of the previous
+// one (the ten accumulators take 480 of the 512 tensor-memory columns, so
+// there is one set); warps 2-9 run the epilogue, loading what it needs
+// besides the accumulators while the MMAs run.  Every wait is bounded; a
+// role that gives up sets `err`, which the others see at their next tile.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_oz_step(const PartDesc* __restrict__ parts, int step, int aux, int m, int ntn, OzOut out,
+    k_oz_step(const PartDesc* __restrict__ parts, int step, int aux, int m, int ntm, int ntn, int ntiles, OzOut out,
               const int* __restrict__ lexp, const int* __restrict__ rexp0, const int* __restrict__ rexp1,
               int* __restrict__ errflag, const __grid_constant__ OzMaps maps) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t full[kStages], empty[kStages], accb;
+  __shared__ uint64_t full[kStages], empty[kStages], tfull, tempty, mdone;
   __shared__ uint32_t tmem_slot;
   __shared__ int err, nissued, ncons;
-  const int pidx = blockIdx.y;
-  PartDesc p{};
-  SepDesc sd{};
-  if constexpr (KIND >= 4)
-    sd = out.seps[pidx];  // blockIdx.y = separator
-  else
-    p = parts[pidx];
-  const int tn = blockIdx.x % ntn, rest = blockIdx.x / ntn, j = rest & 1, tm = rest >> 1;
-  if (tm * MT >= m || tn * NT >= m) return;
-  int t = 0;
-  bool act;
-  if (KIND == 4) {
-    act = j == 0 || (sd.flags & HAS_HA) != 0;
-  } else if (KIND == 5) {
-    act = j == 0 || (sd.flags & HAS_HC) != 0;
-  } else if (KIND == 0) {
-    t = step;
-    act = t < p.L && (j == 0 ? (t < p.L - 1 || (p.flags & HAS_RIGHT) != 0) : (p.flags & HAS_LEFT) != 0);
-  } else if (KIND == 1) {
-    t = step;
-    act = t < p.L - 1 && (j == 0 || (p.flags & HAS_LEFT) != 0);
-  } else if (KIND == 2) {
-    t = p.L - 2 - step;
-    act = t >= 0 && (j == 0 ? (p.flags & HAS_LEFT) != 0 : (p.flags & HAS_RIGHT) != 0);
-  } else {
-    t = aux;
-    act = t < p.L && j == 0;
-  }
-  if (!act) return;
-  const long long mm = (long long)m * m;
-  const int b0 = (int)(p.blk / mm);
-  int zl, zr;
-  if (KIND == 4) {
-    zl = (int)(sd.blk_q / mm);  // A_q (all blocks)
-    zr = 4 * pidx + j;          // ZR^j[q-1]^T / ZL^j[q-1]^T
-  } else if (KIND == 5) {
-    zl = pidx;                  // C_q (per separator)
-    zr = 4 * pidx + 2 + j;      // ZL^{j+1}[q+1]^T / ZR^{j+1}[q+1]^T
-  } else if (KIND == 3) {
-    zl = pidx;  // U slices (rolling)
-    zr = pidx;  // V^T slices (rolling)
-  } else if (KIND == 0) {
-    zl = pidx;                   // G_t slices (rolling)
-    zr = j == 0 ? b0 + t : pidx;  // C_t^T (all blocks) / Y_t^T (rolling)
-  } else if (KIND == 1) {
-    zl = b0 + t + 1;                          // A_{t+1}
-    zr = j == 0 ? pidx : 2 * pidx + (t & 1);  // Acal_t^T / Bcal_t^T
-  } else {
-    zl = b0 + t;                    // Acal_t
-    zr = 2 * pidx + ((t + 1) & 1);  // ZL_{t+1}^T / ZR_{t+1}^T
-  }
-  const CUtensorMap* mr = j == 0 ? &maps.R0 : &maps.R1;
-  const int* rexp = j == 0 ? rexp0 : rexp1;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  double* stage_out = reinterpret_cast<double*>(base + kStages * STAGE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* verr = &err;
   // the zero right slice of both stages (never written by the copies)
   for (int st = 0; st < kStages; ++st)
     for (int i = threadIdx.x; i < RSL / 16; i += kThreads)
@@ -197,7 +225,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accb, 1);
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, kEpiWarps);
+    mbar_init(&mdone, 1);
     err = 0;
     nissued = 0;
     ncons = 0;
@@ -208,194 +238,244 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  const long long mm = (long long)m * m;
   const int nslab = KIND == 3 ? 1 : (m + KS - 1) / KS;
   constexpr uint32_t tx = (uint32_t)(S * (MT + NT) * ROWB);
 
-  if (warp == 0 && lane == 0) {
-    uint32_t ph[kStages] = {0u, 0u};
-    int s = 0;
-    for (; s < nslab; ++s) {
-      const int st = s & 1;
-      if (s >= kStages) {
-        if (!mbar_wait(&empty[st], ph[st])) {
-          err = 1;
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*verr; tile += gridDim.x) {
+        const OzTile w = oz_tile<KIND>(tile, parts, out, step, aux, m, ntm, ntn);
+        if (!w.act) continue;
+        const CUtensorMap* mr = w.j == 0 ? &maps.R0 : &maps.R1;
+        bool ok = true;
+        for (int s = 0; s < nslab; ++s, ++it) {
+          const int st = it & 1;
+          if (it >= kStages && !mbar_wait(&empty[st], (uint32_t)(((it >> 1) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          const uint32_t sb = smem_u32(base + st * STAGE);
+          mbar_expect_tx(&full[st], tx);
+          tma_load_4d(sb, &maps.L, s * KS, w.tm * MT, 0, w.zl, &full[st]);
+          tma_load_4d(sb + LBYTES, mr, s * KS, w.tn * NT, 0, w.zr, &full[st]);
+        }
+        if (!ok) {
+          *verr = 1;
           break;
         }
-        ph[st] ^= 1u;
       }
-      const uint32_t sb = smem_u32(base + st * STAGE);
-      mbar_expect_tx(&full[st], tx);
-      tma_load_4d(sb, &maps.L, s * KS, tm * MT, 0, zl, &full[st]);
-      tma_load_4d(sb + LBYTES, mr, s * KS, tn * NT, 0, zr, &full[st]);
+      nissued = it;
     }
-    nissued = s;
-  } else if (warp == 1 && lane == 0) {
-    int s = 0;
-    for (; s < nslab; ++s) {
-      const int st = s & 1;
-      if (!mbar_wait(&full[st], (uint32_t)((s >> 1) & 1))) {
-        err = 1;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*verr; tile += gridDim.x) {
+        const OzTile w = oz_tile<KIND>(tile, parts, out, step, aux, m, ntm, ntn);
+        if (!w.act) continue;
+        // the accumulators of the previous tile have been read
+        if (lt > 0 && !mbar_wait(&tempty, (uint32_t)((lt - 1) & 1))) {
+          *verr = 1;
+          break;
+        }
+        tc_fence_after();
+        bool ok = true;
+        for (int s = 0; s < nslab; ++s, ++it) {
+          const int st = it & 1;
+          if (!mbar_wait(&full[st], (uint32_t)((it >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t la = smem_u32(base + st * STAGE), ra = la + LBYTES;
+#pragma unroll
+          for (int k = 0; k < KS / 16; ++k) {
+            const uint32_t off = (uint32_t)(k * 32);
+#pragma unroll
+            for (int sl = 1; sl <= S; ++sl) {
+              const int T = sl == 1 ? S + 1 : min(S, 11 - sl);  // s = 1 runs into the zero slice
+              const uint64_t ad = kmajor_desc(la + (sl - 1) * LSL + off, kSbo, kLayout);
+#pragma unroll
+              for (int ta = 1; ta <= T; ta += 5) {
+                const int cnt = min(5, T - ta + 1);
+                const uint64_t bd = kmajor_desc(ra + (ta - 1) * RSL + off, kSbo, kLayout);
+                const uint32_t dcol = (uint32_t)((sl + ta - 2) * NT);
+                const uint32_t acc = (s == 0 && k == 0 && sl == 1) ? 0u : 1u;
+                mma<1>(tmem + dcol, ad, bd, make_idesc(1u, MT, NT * cnt), acc);
+              }
+            }
+          }
+          mma_commit(&empty[st]);
+        }
+        if (!ok) {
+          *verr = 1;
+          break;
+        }
+        mma_commit(&tfull);
+        ++lt;
+      }
+      ncons = it;
+      // every MMA issued here is complete before the accumulators are freed
+      mma_commit(&mdone);
+      mbar_wait(&mdone, 0u);
+    }
+    __syncwarp();
+  } else {
+    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;  // a warp reaches lanes 32 (warp % 4) ..
+    double* stg = stage_out + ew * STG;
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int cl = lane & 7, r0 = lane >> 3;
+    const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*verr; tile += gridDim.x) {
+      const OzTile w = oz_tile<KIND>(tile, parts, out, step, aux, m, ntm, ntn);
+      if (!w.act) continue;
+      const int j = w.j, t = w.t, pidx = w.unit;
+      const PartDesc& p = w.p;
+      const SepDesc& sd = w.sd;
+      const int* rexp = j == 0 ? rexp0 : rexp1;
+      // Before the accumulators are ready: the row's scale, the column scales
+      // of the warp's 24 columns (one per lane, passed by shuffle) and the
+      // values the stores update (they do not depend on the products)
+      const int rbase = w.tm * MT + quarter * 32, row = rbase + lane;
+      const int er = row < m ? lexp[(long long)w.zl * m + row] : 0;
+      int fexp = 0;
+      {
+        const int n = w.tn * NT + half * (NT / 2) + lane;
+        if (lane < NT / 2 && n < m) fexp = rexp[(long long)w.zr * m + n];
+      }
+      const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3, hb = KIND >= 4 && j == 0;
+      const bool upd = rmw || dnext || gj || hb;
+      const long long o = p.blk + (long long)t * mm;
+      const double* src = rmw    ? out.ZL + o
+                          : gj   ? out.G + o
+                          : hb   ? (KIND == 4 ? out.B + sd.blk_q : out.HB + sd.hblk)
+                                 : out.B + o + mm;
+      // the values chunk ci's stores update, loaded one chunk ahead
+      auto load_in = [&](int ci, double (&in)[8]) {
+        const int n = w.tn * NT + half * (NT / 2) + 8 * ci + cl;
+        const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = rbase + r0 + 4 * i;
+          in[i] = (upd && n < m && outside && rr < m && !(gj && rr >= k0 && rr < k0 + 32)) ? src[(long long)rr * m + n]
+                                                                                          : 0.0;
+        }
+      };
+      double incur[8], innext[8];
+      load_in(0, incur);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull, (uint32_t)(lt & 1)));
+      if (!ok) {
+        *verr = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t la = smem_u32(base + st * STAGE), ra = la + LBYTES;
+      // Accumulators of this thread's row (tensor-memory lane) for 8 columns
+      // at a time.  Each acc_d is an integer-valued float below 2^24: its
+      // integer comes from the float's bits (float32 and integer operations),
+      // pairs P_j = acc_{2j+2} 64 + acc_{2j+3} are exact in 32 bits, and
+      //   hi = P_0 2^12 + P_1 (< 2^39),  lo = (P_2 2^12 + P_3) 2^12 + P_4 (< 2^53)
+      // give the sum exactly as hi 2^36 + lo.  Both become float64 from their
+      // bits with the scale 2^(e_r + f_n - 66) in the exponent, and one
+      // float64 add rounds their sum once (one issue slot; rounding the
+      // 128-bit sum in integer arithmetic measured slower).  Warps of the
+      // same lane quarter share the tile's columns.  Results are staged
+      // through the warp's 32 x 9 float64 tile so that row-major writes are
+      // coalesced.
+      // acc_d below 2^22 for every d (then the float32 magic-number
+      // conversion is exact): K = 32, or K = m <= 112 (acc_d <= 9 K 63^2)
+      const bool small = KIND == 3 || m <= 112;
 #pragma unroll
-      for (int k = 0; k < KS / 16; ++k) {
-        const uint32_t off = (uint32_t)(k * 32);
+      for (int ci = 0; ci < NT / 16; ++ci) {
+        const int ch = half * (NT / 2) + 8 * ci;
+        uint32_t r[NACC][8];
 #pragma unroll
-        for (int sl = 1; sl <= S; ++sl) {
-          const int T = sl == 1 ? S + 1 : min(S, 11 - sl);  // s = 1 runs into the zero slice
-          const uint64_t ad = kmajor_desc(la + (sl - 1) * LSL + off, kSbo, kLayout);
+        for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
+        tmem_wait_ld();
 #pragma unroll
-          for (int ta = 1; ta <= T; ta += 5) {
-            const int cnt = min(5, T - ta + 1);
-            const uint64_t bd = kmajor_desc(ra + (ta - 1) * RSL + off, kSbo, kLayout);
-            const uint32_t dcol = (uint32_t)((sl + ta - 2) * NT);
-            const uint32_t acc = (s == 0 && k == 0 && sl == 1) ? 0u : 1u;
-            mma<1>(tmem + dcol, ad, bd, make_idesc(1u, MT, NT * cnt), acc);
-          }
+        for (int dd = 0; dd < NACC; ++dd) tmem_regs_after_wait(r[dd]);
+        if (ci == NT / 16 - 1) {  // the last accumulator read of this tile: the MMAs may go on
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty);
+        } else {
+          load_in(ci + 1, innext);
         }
-      }
-      mma_commit(&empty[st]);
-    }
-    ncons = s;
-    mma_commit(&accb);
-  }
-  if (warp < 2) __syncwarp();
-  // Before the accumulators are ready, every thread loads what its epilogue
-  // needs besides them: its row's scale, the column scales of its warp's 24
-  // columns (one per lane, passed by shuffle) and the values its stores
-  // update (they do not depend on the products), so that the epilogue waits
-  // on tensor memory only.  Warps 2-7 do it while the MMAs run.
-  const int quarter = warp & 3, half = warp >> 2;
-  const int rbase = tm * MT + quarter * 32, row = rbase + lane;
-  const int er = row < m ? lexp[(long long)zl * m + row] : 0;
-  int fexp = 0;
-  {
-    const int n = tn * NT + half * (NT / 2) + lane;
-    if (lane < NT / 2 && n < m) fexp = rexp[(long long)zr * m + n];
-  }
-  const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3, hb = KIND >= 4 && j == 0;
-  const long long o = p.blk + (long long)t * mm;
-  const int cl = lane & 7, r0 = lane >> 3;
-  const int k0 = 32 * step;  // KIND 3: the panel's columns and pivot rows
-  double inpre[NT / 16][8];
-  if (rmw || dnext || gj || hb) {
-    const double* src = rmw    ? out.ZL + o
-                        : gj   ? out.G + o
-                        : hb   ? (KIND == 4 ? out.B + sd.blk_q : out.HB + sd.hblk)
-                               : out.B + o + mm;
 #pragma unroll
-    for (int ci = 0; ci < NT / 16; ++ci) {
-      const int n = tn * NT + half * (NT / 2) + 8 * ci + cl;
-      const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
+        for (int c = 0; c < 8; ++c) {
+          const int n = w.tn * NT + ch + c;
+          const int k = er + __shfl_sync(0xffffffffu, fexp, 8 * ci + c);
+          int a[NACC];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int rr = rbase + r0 + 4 * i;
-        inpre[ci][i] = (n < m && outside && rr < m && !(gj && rr >= k0 && rr < k0 + 32))
-                           ? src[(long long)rr * m + n]
-                           : 0.0;
-      }
-    }
-  }
-  bool ok = mbar_wait(&accb, 0u);
-  tc_fence_after();
-  ok = __syncthreads_and(ok) && !err;
-
-  if (ok) {
-    // Accumulators of this thread's row (tensor-memory lane) for 8 columns
-    // at a time.  Each acc_d is an integer-valued float below 2^24: its
-    // integer comes from the float's bits (float32 and integer operations),
-    // pairs P_j = acc_{2j+2} 64 + acc_{2j+3} are exact in 32 bits, and
-    //   hi = P_0 2^12 + P_1 (< 2^39),  lo = (P_2 2^12 + P_3) 2^12 + P_4 (< 2^53)
-    // give the sum exactly as hi 2^36 + lo.  Both become float64 from their
-    // bits with the scale 2^(e_r + f_n - 66) in the exponent, and one float64
-    // add rounds their sum once (GB300's float64 pipe is narrow: one add per
-    // entry instead of conversions and products).  Warps 0-3 and 4-7 share
-    // the tile's columns (a warp reaches only its own 32 lanes).  Results
-    // are staged through a per-warp 32 x 9 float64 tile so that row-major
-    // writes are coalesced.
-    double* stg = reinterpret_cast<double*>(base) + warp * (32 * 9);
-    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-    // acc_d below 2^22 for every d (then the float32 magic-number
-    // conversion is exact): K = 32, or K = m <= 112 (acc_d <= 9 K 63^2)
-    const bool small = KIND == 3 || m <= 112;
-#pragma unroll
-    for (int ci = 0; ci < NT / 16; ++ci) {
-      const int ch = half * (NT / 2) + 8 * ci;
-      uint32_t r[NACC][8];
-#pragma unroll
-      for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
-      tmem_wait_ld();
-#pragma unroll
-      for (int dd = 0; dd < NACC; ++dd) tmem_regs_after_wait(r[dd]);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int n = tn * NT + ch + c;
-        const int k = er + __shfl_sync(0xffffffffu, fexp, 8 * ci + c);
-        int a[NACC];
-#pragma unroll
-        for (int dd = 0; dd < NACC; ++dd)
-          a[dd] = (dd < 4 || small) ? acc_int_small(__uint_as_float(r[dd][c])) : acc_int(r[dd][c]);
-        const long long hi = (long long)(a[0] * 64 + a[1]) * 4096 + (a[2] * 64 + a[3]);
-        const long long lo = ((long long)(a[4] * 64 + a[5]) * 4096 + (a[6] * 64 + a[7])) * 4096 + (a[8] * 64 + a[9]);
-        double val = 0.0;
-        const bool kept = KIND != 3 || n < k0 || n >= k0 + 32;  // KIND 3: not the panel's columns
-        if (row < m && n < m && kept) {
-          const float a2 = __uint_as_float(r[0][c]);
-          if (a2 != a2)  // NaN or infinite operand: every digit is NaN, acc_2 included
-            val = __longlong_as_double(0x7ff8000000000000ll);
-          else if ((hi | lo) == 0)  // also the zero rows and columns, whose scale is the smallest
-            val = 0.0;
-          else if (k - 66 >= -1022 && k + 9 <= 1023)
-            val = i2d_scaled(hi, k - 30) + i2d_scaled(lo, k - 66);
-          else
-            val = ldexp(fma((double)lo, 0x1p-36, (double)hi), k - 30);
-        }
-        stg[lane * 9 + c] = val;
-      }
-      __syncwarp();
-      // row-major float64 results: lane = (row quarter, column), 8 row quads
-      const int n = tn * NT + ch + cl;
-      const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
-      if (n < m && outside) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int rl = r0 + 4 * i, rr = rbase + rl;
-          if (rr >= m) continue;
-          const double w = stg[rl * 9 + cl];
-          const long long e = (long long)rr * m + n;
-          if (KIND >= 4) {
-            if (j == 0)
-              out.HB[sd.hblk + e] = inpre[ci][i] - w;           // HB = B_q - A_q ZR, then HB -= C_q ZL
+          for (int dd = 0; dd < NACC; ++dd)
+            a[dd] = (dd < 4 || small) ? acc_int_small(__uint_as_float(r[dd][c])) : acc_int(r[dd][c]);
+          const long long hi = (long long)(a[0] * 64 + a[1]) * 4096 + (a[2] * 64 + a[3]);
+          const long long lo =
+              ((long long)(a[4] * 64 + a[5]) * 4096 + (a[6] * 64 + a[7])) * 4096 + (a[8] * 64 + a[9]);
+          double val = 0.0;
+          const bool kept = KIND != 3 || n < k0 || n >= k0 + 32;  // KIND 3: not the panel's columns
+          if (row < m && n < m && kept) {
+            const float a2 = __uint_as_float(r[0][c]);
+            if (a2 != a2)  // NaN or infinite operand: every digit is NaN, acc_2 included
+              val = __longlong_as_double(0x7ff8000000000000ll);
+            else if ((hi | lo) == 0)  // also the zero rows and columns, whose scale is the smallest
+              val = 0.0;
+            else if (k - 66 >= -1022 && k + 9 <= 1023)
+              val = i2d_scaled(hi, k - 30) + i2d_scaled(lo, k - 66);
             else
-              (KIND == 4 ? out.HA : out.HC)[sd.hblk + e] = -w;  // HA = -A_q ZL, HC = -C_q ZR
-          } else if (KIND == 0) {
-            double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
-            d[o + e] = w;
-          } else if (dnext) {
-            out.G[o + mm + e] = inpre[ci][i] - w;                // D_{t+1} = B_{t+1} - A_{t+1} Acal_t
-          } else if (KIND == 1) {
-            out.Y[(long long)pidx * mm + e] = -w;                // Y_{t+1} = -A_{t+1} Bcal_t
-          } else if (rmw) {
-            out.ZL[o + e] = inpre[ci][i] - w;                    // ZL_t -= Acal_t ZL_{t+1}
-          } else if (gj) {
-            out.G[o + e] = inpre[ci][i] + w;                     // Gauss-Jordan trailing update
-          } else {
-            out.ZR[o + e] = -w;                                  // ZR_t = -Acal_t ZR_{t+1}
+              val = ldexp(fma((double)lo, 0x1p-36, (double)hi), k - 30);
+          }
+          stg[lane * 9 + c] = val;
+        }
+        __syncwarp();
+        // row-major float64 results: lane = (row quarter, column), 8 row quads
+        const int n = w.tn * NT + ch + cl;
+        const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
+        if (n < m && outside) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int rl = r0 + 4 * i, rr = rbase + rl;
+            if (rr >= m) continue;
+            const double v = stg[rl * 9 + cl];
+            const long long e = (long long)rr * m + n;
+            if (KIND >= 4) {
+              if (j == 0)
+                out.HB[sd.hblk + e] = incur[i] - v;               // HB = B_q - A_q ZR, then HB -= C_q ZL
+              else
+                (KIND == 4 ? out.HA : out.HC)[sd.hblk + e] = -v;  // HA = -A_q ZL, HC = -C_q ZR
+            } else if (KIND == 0) {
+              double* d = (j == 0) ? (t < p.L - 1 ? out.Acal : out.ZR) : out.ZL;
+              d[o + e] = v;
+            } else if (dnext) {
+              out.G[o + mm + e] = incur[i] - v;                    // D_{t+1} = B_{t+1} - A_{t+1} Acal_t
+            } else if (KIND == 1) {
+              out.Y[(long long)pidx * mm + e] = -v;                // Y_{t+1} = -A_{t+1} Bcal_t
+            } else if (rmw) {
+              out.ZL[o + e] = incur[i] - v;                        // ZL_t -= Acal_t ZL_{t+1}
+            } else if (gj) {
+              out.G[o + e] = incur[i] + v;                         // Gauss-Jordan trailing update
+            } else {
+              out.ZR[o + e] = -v;                                  // ZR_t = -Acal_t ZR_{t+1}
+            }
           }
         }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) incur[i] = innext[i];
       }
-      __syncwarp();
+      ++lt;
     }
   }
-  if (threadIdx.x == 0)
+  __syncthreads();
+  if (threadIdx.x == 0)  // copies still in flight after an error
     for (int s = ncons; s < nissued; ++s) mbar_wait(&full[s & 1], (uint32_t)((s >> 1) & 1));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, kCols);
-  if (threadIdx.x == 0 && !ok && errflag) atomicExch(errflag, 1);
+  if (threadIdx.x == 0 && err && errflag) atomicExch(errflag, 1);
 }
 
 // ---------------------------------------------------------------- slicing
@@ -1109,8 +1189,15 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
   if (nparts <= 0) return;
   OzMaps mp;
   std::memcpy(&mp, maps3, sizeof mp);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+  }
   const int ntm = (m + oz::MT - 1) / oz::MT, ntn = (m + oz::NT - 1) / oz::NT;
-  const dim3 grid(2 * ntm * ntn, nparts);
+  const int ntiles = nparts * (kind == 3 ? 1 : 2) * ntm * ntn;
+  const int grid = std::min(ntiles, nsm);
 #define DM_OZ(KIND_)                                                                                              \
   do {                                                                                                           \
     static bool set = false;                                                                                     \
@@ -1118,8 +1205,8 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
       cudaFuncSetAttribute(oz::k_oz_step<KIND_>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM);        \
       set = true;                                                                                                \
     }                                                                                                            \
-    oz::k_oz_step<KIND_><<<grid, oz::kThreads, oz::SMEM, st>>>(parts, step, aux, m, ntn, out, lexp, rexp0,      \
-                                                               rexp1, errflag, mp);                              \
+    oz::k_oz_step<KIND_><<<grid, oz::kThreads, oz::SMEM, st>>>(parts, step, aux, m, ntm, ntn, ntiles, out, lexp, \
+                                                               rexp0, rexp1, errflag, mp);                       \
   } while (0)
   if (kind == 0) DM_OZ(0);
   else if (kind == 1) DM_OZ(1);
