@@ -277,24 +277,13 @@ def main():
     # roofline of the dominant kernel class (largest summed event time)
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     kname, kd = top
-    achieved = kd["flops"] / (kd["ms"] / 1e3) / 1e12
-    # float64 is bound by the FP64 pipe (plain ALU arithmetic): peak = SMs x 2
-    # DFMA/clk (4 flop/clk) x the SM clock sampled during the timed region
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = clk.get("sm_mhz") or 2070.0
-    peak = sms * 4.0 * mhz * 1e6 / 1e12
-    src = (f"derived: {sms} SMs x 4 float64 flop/clk x {mhz:.0f} MHz (median SM clock sampled in the timed "
-           f"region); the dm_peak_probe register-tile FMA loop reaches "
-           f"{peaks.get('fp64', {}).get('tflops', float('nan')):.3f} TFLOP/s at "
-           f"{peaks.get('fp64', {}).get('sm_mhz') or float('nan'):.0f} MHz")
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": read_traffic(kname) if not mixed else None,
-            "peak_source": src, "nominal_peak": FP64_NOMINAL_TFLOPS,
-            "probe_peak": peaks.get("fp64", {}).get("tflops"),
-            "launches": kd["launches"], "avg_launch_ms": kd["ms"] / kd["launches"],
-            "share_of_step": kd["ms"] / sum(v["ms"] for v in prof.values()),
-            "timing": "CUDA events around each launch in a second run of the same steps "
-                      f"({prof_ms_step:.1f} ms/step instrumented vs {total_ms / args.steps:.1f} graph-replayed)"}
+    roof = class_roofline(kname, kd, prof, mixed, clk, peaks, dev)
+    roof["timing"] = ("CUDA events around each launch in a second run of the same steps "
+                      f"({prof_ms_step:.1f} ms/step instrumented vs {total_ms / args.steps:.1f} graph-replayed)")
+    others = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[1:4]
+    roof["next"] = {k: {key: val for key, val in class_roofline(k, v, prof, mixed, clk, peaks, dev).items()
+                        if key in ("bound", "achieved", "peak", "unit", "frac", "share_of_step")}
+                    for k, v in others}
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                    "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
                for k, v in prof.items()}
@@ -357,6 +346,54 @@ def rel_err(x, xref):
     x = x.reshape(-1, x.shape[-1])
     xref = xref.reshape(-1, xref.shape[-1])
     return float(np.max(np.linalg.norm(x - xref, axis=0) / np.maximum(np.linalg.norm(xref, axis=0), 1e-300)))
+
+
+# float64 classes whose products run as digit-sliced bf16 tensor-core MMAs: per
+# float64 multiply-add, 54 slice-pair products (the 53 pairs with s + t <= 11
+# and one against the zero slice that initialises the accumulators)
+SLICED_CLASSES = ("fwd_factor", "back_factor", "inv_update", "assemble_h")
+SLICE_PRODUCTS = 54
+HBM_CLASSES = ("inv", "tc_convert", "sweep_solve", "backsub", "sep_copy", "assemble_f", "axpy_norms")
+
+
+def class_roofline(kname, kd, prof, mixed, clk, peaks, dev):
+    """Roofline of one kernel class: algorithmic flops (or bytes) of its
+    launches over their summed CUDA-event time, against the peak of what
+    bounds it: the derived float64 ALU peak for float64 CUDA-core kernels, the
+    measured bf16 tensor peak (in MMA flops) for the digit-sliced products,
+    the measured copy bandwidth for the passes that only move data."""
+    import torch
+    base = kname.split("@")[0]
+    secs = kd["ms"] / 1e3
+    share = kd["ms"] / sum(v["ms"] for v in prof.values())
+    common = {"kernel": kname, "launches": kd["launches"], "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
+              "share_of_step": share, "traffic": read_traffic(kname) if not mixed else None}
+    mp = measured_peaks()
+    if not mixed and base in SLICED_CLASSES:
+        alg = kd["flops"] / secs / 1e12
+        peak = mp.get("bf16_tflops") or 1900.0
+        return {**common, "bound": "tensor", "achieved": alg * SLICE_PRODUCTS, "peak": peak, "unit": "TFLOP/s",
+                "frac": alg * SLICE_PRODUCTS / peak, "achieved_algorithmic": alg,
+                "mma_flops_per_algorithmic": SLICE_PRODUCTS,
+                "peak_source": "bf16 dense, measured cuBLAS burst (MEASURED_PEAKS.json), of measured"}
+    if base in HBM_CLASSES:
+        ach = kd["bytes"] / secs / 1e9
+        peak = mp.get("hbm_gbs") or 6800.0
+        return {**common, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json), of measured"}
+    # float64 is bound by the FP64 pipe (plain ALU arithmetic): peak = SMs x 2
+    # DFMA/clk (4 flop/clk) x the SM clock sampled during the timed region
+    achieved = kd["flops"] / secs / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = sms * 4.0 * mhz * 1e6 / 1e12
+    src = (f"derived: {sms} SMs x 4 float64 flop/clk x {mhz:.0f} MHz (median SM clock sampled in the timed "
+           f"region); the dm_peak_probe register-tile FMA loop reaches "
+           f"{peaks.get('fp64', {}).get('tflops', float('nan')):.3f} TFLOP/s at "
+           f"{peaks.get('fp64', {}).get('sm_mhz') or float('nan'):.0f} MHz")
+    return {**common, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src, "nominal_peak": FP64_NOMINAL_TFLOPS,
+            "probe_peak": peaks.get("fp64", {}).get("tflops")}
 
 
 def read_traffic(kernel):

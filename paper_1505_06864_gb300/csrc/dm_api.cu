@@ -530,7 +530,7 @@ Level::~Level() {
 // Profiler
 const char* const kClassNames[K_NCLASS] = {
     "inv", "fwd_factor", "back_factor", "assemble_h", "fwd_solve", "back_solve", "assemble_f",
-    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve", "tc_convert"};
+    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve", "tc_convert", "inv_panel", "inv_update"};
 
 cudaEvent_t Prof::take() {
   if (!pool.empty()) {
@@ -550,8 +550,9 @@ void Prof::begin(cudaStream_t st, cudaEvent_t* e0) {
   cudaEventRecord(*e0, st);
 }
 
-void Prof::end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, bool launched) {
-  if (launched) ++launches;
+void Prof::end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, int kernels) {
+  const bool launched = kernels > 0;
+  launches += kernels;
   if (!on || !e0) return;
   if (!launched) {
     pool.push_back(e0);
@@ -590,13 +591,15 @@ Prof::~Prof() {
   for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
-#define DM_LAUNCH(pf, st, cls, cost, active, call)             \
-  do {                                                         \
-    cudaEvent_t e0_;                                           \
-    (pf).begin((st), &e0_);                                    \
-    call;                                                      \
-    (pf).end((st), e0_, (cls), (cost).flops, (cost).bytes, (active) > 0); \
+// One profiled call that launches `nk` kernels (when active > 0).
+#define DM_LAUNCH_K(pf, st, cls, cost, active, nk, call)                         \
+  do {                                                                           \
+    cudaEvent_t e0_;                                                             \
+    (pf).begin((st), &e0_);                                                      \
+    call;                                                                        \
+    (pf).end((st), e0_, (cls), (cost).flops, (cost).bytes, (active) > 0 ? (nk) : 0); \
   } while (0)
+#define DM_LAUNCH(pf, st, cls, cost, active, call) DM_LAUNCH_K(pf, st, cls, cost, active, 1, call)
 
 // Forward and backward sweeps of a float32 level on the tensor-core step
 // kernels (dm_tc2.cu): operand copies of A, B, C^T and Y_0 = A_first^T, then
@@ -637,7 +640,7 @@ static void factor_level_tc2(Level& L, cudaStream_t st, Prof& pf) {
     launch_tc2_convert(mode, L.C, nullptr, nullptr, (int)nb, 0, m, true, T.CT, T.capCT, st);
     launch_tc2_convert(mode, L.A, nullptr, L.d_parts, L.nparts, 0, m, true, T.YT, T.capYT, st);
   };
-  DM_LAUNCH(pf, st, K_TC_CONVERT, L.c_cvt, 1, convert_inputs());
+  DM_LAUNCH_K(pf, st, K_TC_CONVERT, L.c_cvt, 1, 4, convert_inputs());
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t];
     DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<float>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
@@ -693,15 +696,34 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
     launch_oz_slice_jobs(L.d_parts, L.nparts, 0, m, j0, 1, st);
   };
   Cost cslice = L.c_cvt;
-  DM_LAUNCH(pf, st, K_TC_CONVERT, cslice, 1, slice_inputs());
+  DM_LAUNCH_K(pf, st, K_TC_CONVERT, cslice, 1, 3, slice_inputs());
   Cost cs;
   cs.bytes = 26.0 * m * m;  // one block: float64 read, nine bf16 slices written
   for (int t = 0; t < L.Lmax; ++t) {
     const int np = L.active_fwd[t], nbk = L.active_back[t];
-    if (Z.gj) {  // the blocked inversion writes G_t's row slices itself
-      DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np,
-                launch_gj_inverse(L.d_parts, np, t, m, L.B, G, Z.piv, Z.U, Z.eU, Z.V, Z.eV, Z.gj_maps, L.status,
-                                  L.d_err, Z.G, Z.eG, st));
+    if (Z.gj) {
+      // the blocked inversion, its phases profiled apart: the float64 panels
+      // (2 m kw^2 flops per block), the tensor-core trailing updates (2 m (m -
+      // kw) kw), the copy of B_0 and the finishing pass, which also writes
+      // G_t's row slices
+      Cost cb, cf;
+      cb.bytes = np * 16.0 * m * m;           // B_0 read, written to G
+      cf.bytes = np * (16.0 + 18.0) * m * m;  // G_t read and written, nine bf16 slices written
+      if (t == 0) DM_LAUNCH(pf, st, K_INV, cb, np, launch_gj_begin(L.d_parts, np, t, m, L.B, G, st));
+      for (int k0 = 0; k0 < m; k0 += 32) {
+        const double kw = std::min(32, m - k0);
+        Cost cp, cu;
+        cp.flops = np * 2.0 * m * kw * kw;
+        cp.bytes = np * (16.0 * m * kw + 18.0 * 32.0 * 2 * m + 8.0 * kw * m);
+        cu.flops = np * 2.0 * m * (m - kw) * kw;
+        cu.bytes = np * (16.0 * m * (m - kw) + 18.0 * 32.0 * 2 * m);
+        DM_LAUNCH(pf, st, K_INV_PANEL, cp, np,
+                  launch_gj_panel(L.d_parts, np, t, m, k0 / 32, G, Z.piv, Z.U, Z.eU, Z.V, Z.eV, L.status, st));
+        if (m > 32)
+          DM_LAUNCH(pf, st, K_INV_UPDATE, cu, np,
+                    launch_gj_update(L.d_parts, np, t, m, k0 / 32, G, Z.eU, Z.eV, Z.gj_maps, L.d_err, st));
+      }
+      DM_LAUNCH(pf, st, K_INV, cf, np, launch_gj_finish(L.d_parts, np, t, m, G, Z.piv, Z.G, Z.eG, st));
     } else {
       DM_LAUNCH(pf, st, K_INV, L.c_inv[t], np, launch_inv<double>(L.d_parts, np, t, L.B, G, L.status, L.max_m, st));
       OzSliceJobs jg;
@@ -755,8 +777,8 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
     if (L.oz.on) {
       factor_level_oz(L, st, pf);
       if (L.supp && L.oz.asm_on)
-        DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
-                  launch_oz_assemble(L.d_seps, L.nseps, L.max_m, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C,
+        DM_LAUNCH_K(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps, 3,
+                    launch_oz_assemble(L.d_seps, L.nseps, L.max_m, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C,
                                      L.oz.as, L.oz.eA, L.oz.maps[1], L.d_err, st));
       else if (L.supp)
         DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
@@ -777,11 +799,10 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   }
   const bool split = aux && aux->st;
   cudaStream_t sb = split ? aux->st : st;
-  if (L.tc_mode >= 0) {
-    launch_to_f32(L.A, L.A32, L.nblk, st);
-    launch_to_f32(L.B, L.B32, L.nblk, st);
-    launch_to_f32(L.C, L.C32, L.nblk, st);
-  }
+  if (L.tc_mode >= 0)
+    DM_LAUNCH_K(pf, st, K_TC_CONVERT, L.c_cvt, 1, 3,
+                (launch_to_f32(L.A, L.A32, L.nblk, st), launch_to_f32(L.B, L.B32, L.nblk, st),
+                 launch_to_f32(L.C, L.C32, L.nblk, st)));
   // block products on the tensor cores (float32 levels with a tensor mode) or CUDA cores
   auto fwd = [&](int np, int t, cudaStream_t s, int lo, int hi) {
     if constexpr (std::is_same<T, float>::value) {
@@ -1028,6 +1049,23 @@ int Plan::run(GraphCache& g, F&& body) {
     cudaGraph_t gr = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &gr);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, gr, 0);
+    if (e == cudaSuccess) {
+      // a replay launches exactly the graph's kernel nodes (a call that
+      // issues several kernels counted as one in the eager run)
+      size_t nn = 0;
+      if (cudaGraphGetNodes(gr, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(gr, nodes.data(), &nn) == cudaSuccess) {
+          long long k = 0;
+          for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+          }
+          g.launches = k;
+        }
+      }
+      cudaGetLastError();
+    }
     if (gr) cudaGraphDestroy(gr);
     if (e != cudaSuccess) {
       cudaGetLastError();

@@ -186,6 +186,14 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
 void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
                        void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
                        void* Gs, int* eG, cudaStream_t st);
+// its phases (launch_gj_inverse runs them in order)
+void launch_gj_begin(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, cudaStream_t st);
+void launch_gj_panel(const PartDesc* parts, int nparts, int t, int m, int pnl, double* G, int* piv, void* Us,
+                     int* Uexp, void* Vs, int* Vexp, int* status, cudaStream_t st);
+void launch_gj_update(const PartDesc* parts, int nparts, int t, int m, int pnl, double* G, const int* Uexp,
+                      const int* Vexp, const void* maps2, int* errflag, cudaStream_t st);
+void launch_gj_finish(const PartDesc* parts, int nparts, int t, int m, double* G, const int* piv, void* Gs, int* eG,
+                      cudaStream_t st);
 int tc2_ntile(int m);
 bool tc2_make_map(int mode, const void* base, long long blocks, int m, int box_rows, void* out);
 int tc2_map_bytes();

@@ -1152,36 +1152,59 @@ void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, co
 }
 
 // The blocked Gauss-Jordan inversion of block row t of every active
-// subsystem (in place in G; t = 0 starts from B_0).
-void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
-                       void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
-                       void* Gs, int* eG, cudaStream_t st) {
+// subsystem (in place in G; t = 0 starts from B_0), as four phases: the copy
+// of B_0, per panel of 32 columns the panel and its trailing update, and the
+// finishing pass (the column permutation undone, the row slices written).
+void launch_gj_begin(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, cudaStream_t st) {
+  if (nparts > 0 && t == 0) oz::k_gj_copy_b0<<<nparts, 256, 0, st>>>(parts, m, B, G);
+}
+
+void launch_gj_panel(const PartDesc* parts, int nparts, int t, int m, int pnl, double* G, int* piv, void* Us,
+                     int* Uexp, void* Vs, int* Vexp, int* status, cudaStream_t st) {
   if (nparts <= 0) return;
-  if (t == 0) oz::k_gj_copy_b0<<<nparts, 256, 0, st>>>(parts, m, B, G);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nparts * oz::kGjCS);
+  cfg.blockDim = dim3(oz::kGjThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = oz::kGjCS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, oz::k_gj_panel, parts, t, m, pnl, G, piv, static_cast<__nv_bfloat16*>(Us), Uexp,
+                     static_cast<__nv_bfloat16*>(Vs), Vexp, status);
+}
+
+void launch_gj_update(const PartDesc* parts, int nparts, int t, int m, int pnl, double* G, const int* Uexp,
+                      const int* Vexp, const void* maps2, int* errflag, cudaStream_t st) {
+  if (nparts <= 0) return;
   OzOut out{nullptr, G, nullptr, nullptr, nullptr, nullptr};
   unsigned char maps3[3 * 128];
   std::memcpy(maps3, maps2, 2 * 128);
   std::memcpy(maps3 + 2 * 128, static_cast<const unsigned char*>(maps2) + 128, 128);
-  const int npan = (m + 31) / 32;
-  for (int pnl = 0; pnl < npan; ++pnl) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nparts * oz::kGjCS);
-    cfg.blockDim = dim3(oz::kGjThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = oz::kGjCS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, oz::k_gj_panel, parts, t, m, pnl, G, piv, static_cast<__nv_bfloat16*>(Us), Uexp,
-                       static_cast<__nv_bfloat16*>(Vs), Vexp, status);
-    if (m > 32) launch_oz_step(3, parts, nparts, pnl, m, out, Uexp, Vexp, Vexp, maps3, errflag, st, t);
-  }
+  launch_oz_step(3, parts, nparts, pnl, m, out, Uexp, Vexp, Vexp, maps3, errflag, st, t);
+}
+
+void launch_gj_finish(const PartDesc* parts, int nparts, int t, int m, double* G, const int* piv, void* Gs, int* eG,
+                      cudaStream_t st) {
+  if (nparts <= 0) return;
   oz::k_gj_finish<<<nparts * ((m + 31) / 32), 256, 0, st>>>(parts, t, m, G, piv, static_cast<__nv_bfloat16*>(Gs),
                                                              eG);
+}
+
+void launch_gj_inverse(const PartDesc* parts, int nparts, int t, int m, const double* B, double* G, int* piv,
+                       void* Us, int* Uexp, void* Vs, int* Vexp, const void* maps2, int* status, int* errflag,
+                       void* Gs, int* eG, cudaStream_t st) {
+  if (nparts <= 0) return;
+  launch_gj_begin(parts, nparts, t, m, B, G, st);
+  for (int pnl = 0; pnl < (m + 31) / 32; ++pnl) {
+    launch_gj_panel(parts, nparts, t, m, pnl, G, piv, Us, Uexp, Vs, Vexp, status, st);
+    if (m > 32) launch_gj_update(parts, nparts, t, m, pnl, G, Uexp, Vexp, maps2, errflag, st);
+  }
+  launch_gj_finish(parts, nparts, t, m, G, piv, Gs, eG, st);
 }
 
 void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m, const OzOut& out, const int* lexp,

@@ -15,7 +15,7 @@ namespace dm {
 // Kernel classes of the profiler (one per launcher).
 enum KClass {
   K_INV, K_FWD_FACTOR, K_BACK_FACTOR, K_ASSEMBLE_H, K_FWD_SOLVE, K_BACK_SOLVE, K_ASSEMBLE_F,
-  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_TC_CONVERT, K_NCLASS
+  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_TC_CONVERT, K_INV_PANEL, K_INV_UPDATE, K_NCLASS
 };
 extern const char* const kClassNames[K_NCLASS];
 
@@ -38,7 +38,7 @@ struct Prof {
   double ms[K_NCLASS * kDepths] = {}, flops[K_NCLASS * kDepths] = {}, bytes[K_NCLASS * kDepths] = {};
   cudaEvent_t take();
   void begin(cudaStream_t st, cudaEvent_t* e0);
-  void end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, bool launched);
+  void end(cudaStream_t st, cudaEvent_t e0, int cls, double fl, double by, int kernels);
   int collect();  // fold finished records into the per-class sums
   void reset();
   ~Prof();
