@@ -210,6 +210,7 @@ void Level::compute_costs() {
   c_fwds.assign(std::max(Lmax, 1), Cost());
   c_backs.assign(std::max(Lmax, 1), Cost());
   c_fwdA.assign(std::max(Lmax, 1), Cost());
+  c_fwdA0.assign(std::max(Lmax, 1), Cost());
   c_fwdB.assign(std::max(Lmax, 1), Cost());
   c_cvt = Cost();
   c_asm_h = c_asm_f = c_backsub = c_resid = c_axpy = c_sepcopy = Cost();
@@ -231,7 +232,12 @@ void Level::compute_costs() {
         // the same products split as the tensor-core step kernels launch them:
         // A = G_t [C_t | Y_t], B = A_{t+1} [Acal_t | Bcal_t]
         Cost& ca = c_fwdA[t];
-        if (t < p.L - 1 || hr) { ca.flops += m3; ca.bytes += es * m2 * 2 + 3 * es * m2; }
+        if (t < p.L - 1 || hr) {
+          ca.flops += m3;
+          ca.bytes += es * m2 * 2 + 3 * es * m2;
+          c_fwdA0[t].flops += m3;
+          c_fwdA0[t].bytes += es * m2 * 2 + 3 * es * m2;
+        }
         if (hl) { ca.flops += m3; ca.bytes += es * m2 * 2 + 2 * es * m2; }
         if (t < p.L - 1) {
           Cost& cb = c_fwdB[t];
@@ -461,6 +467,15 @@ int Level::allocate() {
       if (!ok) return set_error(DM_ECUDA, "tensor map creation for the blocked inversion failed (m = %d)", m);
       Z.gj = true;
     }
+    const char* eb = std::getenv("DM_BANDED");
+    if (!(eb && std::strcmp(eb, "0") == 0)) {
+      DM_ALLOC(Z.band, sizeof(int));
+      if (cudaHostAlloc(reinterpret_cast<void**>(&Z.band_host), sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DM_ENOMEM, "cudaHostAlloc of 4 bytes failed");
+      }
+      *Z.band_host = kBandMax + 1;
+    }
     if (nseps > 0 && oz_asm_wanted()) {
       OzAsm& a = Z.as;
       DM_ALLOC(a.Cq, nseps * sl);
@@ -524,13 +539,15 @@ void Level::release(void* p) {
 
 Level::~Level() {
   for (void* p : owned) cudaFree(p);
+  if (oz.band_host) cudaFreeHost(oz.band_host);
 }
 
 // ---------------------------------------------------------------------------
 // Profiler
 const char* const kClassNames[K_NCLASS] = {
     "inv", "fwd_factor", "back_factor", "assemble_h", "fwd_solve", "back_solve", "assemble_f",
-    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve", "tc_convert", "inv_panel", "inv_update"};
+    "backsub", "sep_copy", "residual", "axpy_norms", "sweep_solve", "tc_convert", "inv_panel", "inv_update",
+    "banded"};
 
 cudaEvent_t Prof::take() {
   if (!pool.empty()) {
@@ -680,6 +697,19 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   out.ZL = static_cast<double*>(L.ZL);
   out.ZR = static_cast<double*>(L.ZR);
   out.Y = Z.Y;
+  out.band = Z.band;
+  // banded A and C as the previous factorisation found them (profiling costs
+  // only: the kernels read the flag this factorisation's slicing sets)
+  const int wb = Z.band ? *Z.band_host : kBandMax + 1;
+  const bool banded_h = wb <= kBandMax;
+  auto band_cost = [&](int units, int products) {
+    Cost c;
+    if (banded_h) {
+      c.flops = (double)units * products * 2.0 * m * m * (2 * wb + 1);
+      c.bytes = (double)units * products * (16.0 + 8.0) * m * m;
+    }
+    return c;
+  };
   alignas(64) unsigned char maps[3][3][128];
   const int sel[3][3] = {{0, 3, 4}, {1, 5, 6}, {2, 6, 7}};
   for (int k = 0; k < 3; ++k)
@@ -689,8 +719,10 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   const int* r1exp[3] = {Z.eYT, Z.eZLT, Z.eZRT};
   auto job = [](const double* src, void* dst, int* e, int kind) { return OzSliceJob{src, dst, e, kind}; };
   auto slice_inputs = [&] {
-    launch_oz_slice_all(false, L.A, (int)nb, m, Z.A, Z.eA, st);
-    launch_oz_slice_all(true, L.C, (int)nb, m, Z.CT, Z.eCT, st);
+    if (Z.band) cudaMemsetAsync(Z.band, 0, sizeof(int), st);
+    launch_oz_slice_all(false, L.A, (int)nb, m, Z.A, Z.eA, Z.band, st);
+    launch_oz_slice_all(true, L.C, (int)nb, m, Z.CT, Z.eCT, Z.band, st);
+    if (Z.band) cudaMemcpyAsync(Z.band_host, Z.band, sizeof(int), cudaMemcpyDeviceToHost, st);
     OzSliceJobs j0;
     j0.job[0] = job(L.A, Z.YT, Z.eYT, 8);
     launch_oz_slice_jobs(L.d_parts, L.nparts, 0, m, j0, 1, st);
@@ -732,9 +764,15 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
       c0.bytes *= np;
       DM_LAUNCH(pf, st, K_TC_CONVERT, c0, np, launch_oz_slice_jobs(L.d_parts, np, t, m, jg, 1, st));
     }
-    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdA[t], np,
+    Cost ca = L.c_fwdA[t];
+    if (banded_h) ca.flops -= L.c_fwdA0[t].flops, ca.bytes -= L.c_fwdA0[t].bytes;
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, ca, np,
               launch_oz_step(0, L.d_parts, np, t, m, out, lexp[0], r0exp[0], r1exp[0], maps[0], L.d_err, st));
+    if (Z.band)  // G_t C_t when C is banded (the tiles above skip it then)
+      DM_LAUNCH(pf, st, K_BANDED, band_cost(np, 1), np,
+                launch_band_gc(L.d_parts, np, t, m, G, L.C, out.Acal, out.ZR, Z.band, st));
     OzSliceJobs ja;
+    ja.band = Z.band;
     ja.job[0] = job(out.Acal, Z.Acal, Z.eAcal, 1);
     ja.job[1] = job(out.Acal, Z.AcalT, Z.eAcalT, 2);
     ja.job[2] = job(out.ZL, Z.ZLT, Z.eZLT, 3);
@@ -742,8 +780,11 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
     Cost c1 = cs;
     c1.bytes *= 4.0 * np;
     DM_LAUNCH(pf, st, K_TC_CONVERT, c1, np, launch_oz_slice_jobs(L.d_parts, np, t, m, ja, 4, st));
-    DM_LAUNCH(pf, st, K_FWD_FACTOR, L.c_fwdB[t], nbk,
+    DM_LAUNCH(pf, st, K_FWD_FACTOR, banded_h ? Cost() : L.c_fwdB[t], nbk,
               launch_oz_step(1, L.d_parts, nbk, t, m, out, lexp[1], r0exp[1], r1exp[1], maps[1], L.d_err, st));
+    if (Z.band)  // both products of launch B when A is banded
+      DM_LAUNCH(pf, st, K_BANDED, band_cost(nbk, 2), nbk,
+                launch_band_b(L.d_parts, nbk, t, m, L.A, L.B, out.Acal, out.ZL, G, Z.Y, Z.band, st));
     OzSliceJobs jy;
     jy.job[0] = job(Z.Y, Z.YT, Z.eYT, 5);
     Cost c2 = cs;
@@ -776,10 +817,22 @@ static void factor_level_t(Level& L, cudaStream_t st, Prof& pf, Aux* aux) {
   if constexpr (std::is_same<T, double>::value) {
     if (L.oz.on) {
       factor_level_oz(L, st, pf);
-      if (L.supp && L.oz.asm_on)
-        DM_LAUNCH_K(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps, 3,
+      if (L.supp && L.oz.asm_on) {
+        const bool bh = L.oz.band && *L.oz.band_host <= kBandMax;
+        DM_LAUNCH_K(pf, st, K_ASSEMBLE_H, bh ? Cost() : L.c_asm_h, L.nseps, 3,
                     launch_oz_assemble(L.d_seps, L.nseps, L.max_m, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B, L.supp->C,
-                                     L.oz.as, L.oz.eA, L.oz.maps[1], L.d_err, st));
+                                       L.oz.as, L.oz.eA, L.oz.maps[1], L.d_err, L.oz.band, st));
+        if (L.oz.band) {  // the supplementary blocks when A and C are banded
+          Cost cb;
+          if (bh) {
+            cb.flops = (double)L.nseps * 4 * 2.0 * L.max_m * L.max_m * (2 * *L.oz.band_host + 1);
+            cb.bytes = (double)L.nseps * 4 * 24.0 * L.max_m * L.max_m;
+          }
+          DM_LAUNCH(pf, st, K_BANDED, cb, L.nseps,
+                    launch_band_h(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,
+                                  L.supp->C, L.oz.band, st));
+        }
+      }
       else if (L.supp)
         DM_LAUNCH(pf, st, K_ASSEMBLE_H, L.c_asm_h, L.nseps,
                   launch_assemble_h<T>(L.d_seps, L.nseps, L.max_m, L.A, L.B, L.C, ZL, ZR, L.supp->A, L.supp->B,

@@ -146,7 +146,12 @@ struct OzOut {
   // the supplementary blocks (Eq. e2311), one separator per CTA row
   const SepDesc* seps;
   double *HA, *HB, *HC;
+  // the level's largest |row - column| of a nonzero entry of A and C (null:
+  // not detected); at most kBandMax: the products with a banded operand run
+  // in the banded kernels and the tensor-core tiles for them are skipped
+  const int* band;
 };
+constexpr int kBandMax = 6;
 bool oz_eligible(int m);
 int oz_slice_blocks_bytes(int m);
 bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out, int kdim = 0);
@@ -162,8 +167,19 @@ struct OzAsm {
 };
 void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, const double* C, const double* ZL,
                         const double* ZR, double* HA, double* HB, double* HC, const OzAsm& a, const int* eA,
-                        const void* mapA, int* errflag, cudaStream_t st);
-void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st);
+                        const void* mapA, int* errflag, const int* band, cudaStream_t st);
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, int* band,
+                         cudaStream_t st);
+// Products with a banded operand (half-bandwidth w = *band <= kBandMax, else
+// nothing is done): G_t C_t of launch A, both products of launch B, and the
+// supplementary blocks; float64 multiply-adds over the band only.
+void launch_band_gc(const PartDesc* parts, int nparts, int t, int m, const double* G, const double* C, double* Acal,
+                    double* ZR, const int* band, cudaStream_t st);
+void launch_band_b(const PartDesc* parts, int nparts, int t, int m, const double* A, const double* B,
+                   const double* Acal, const double* ZL, double* G, double* Y, const int* band, cudaStream_t st);
+void launch_band_h(const SepDesc* seps, int nseps, int m, const double* A, const double* B, const double* C,
+                   const double* ZL, const double* ZR, double* HA, double* HB, double* HC, const int* band,
+                   cudaStream_t st);
 struct OzSliceJob {
   const double* src;
   void* dst;
@@ -172,6 +188,7 @@ struct OzSliceJob {
 };
 struct OzSliceJobs {
   OzSliceJob job[4];
+  const int* band = nullptr;  // kinds 2 and 3 (launch B's operands) are skipped when banded
 };
 void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
                           cudaStream_t st);

@@ -169,6 +169,9 @@ __device__ __forceinline__ OzTile oz_tile(int tile, const PartDesc* __restrict__
     w.t = aux;
     act = w.t < p.L && j == 0;
   }
+  // products with a banded operand run in the banded kernels instead
+  const bool banded = out.band && *out.band <= kBandMax;
+  if (banded && ((KIND == 0 && j == 0) || KIND == 1 || KIND >= 4)) act = false;
   w.act = act && w.tm * MT < m && w.tn * NT < m;
   const long long mm = (long long)m * m;
   const int b0 = (int)(p.blk / mm), t = w.t;
@@ -485,15 +488,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Row slices (left operands): exps[r] = e with |v| < 2^e for the row's
 // largest |v|; slice s element (r, k) at (q * 9 + s) m^2 + r m + k.  One
 // warp per row, eight consecutive columns per lane (m % 8 == 0).
+// With `band` set, the largest |row - column| of a nonzero entry seen is
+// folded into *band (atomicMax), for the banded-product path.
 __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                                 long long qdst, int* __restrict__ exps, int m, int g) {
+                                                 long long qdst, int* __restrict__ exps, int m, int g,
+                                                 int* __restrict__ band = nullptr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
   const int rend = min(m, 32 * g + 32);
+  int wmax = 0;
   for (int r = 32 * g + warp; r < rend; r += nw) {
     uint32_t hmax = 0;
-    for (int c = lane; c < m; c += 32) hmax = max(hmax, (uint32_t)(bits[(long long)r * m + c] >> 32) & 0x7fffffffu);
+    for (int c = lane; c < m; c += 32) {
+      const unsigned long long b = bits[(long long)r * m + c];
+      hmax = max(hmax, (uint32_t)(b >> 32) & 0x7fffffffu);
+      if (band && (b << 1)) wmax = max(wmax, abs(r - c));
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
     const int e = scale_exponent(hmax);
@@ -513,6 +524,11 @@ __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src,
       }
     }
   }
+  if (band) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0 && wmax > 0) atomicMax(band, wmax);
+  }
 }
 
 // Column slices, transposed (right operands): exps[n] for column n, slice s
@@ -522,14 +538,25 @@ __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src,
 // per slice (8-byte stores).  256 threads.
 __device__ __forceinline__ void slice_cols_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
                                                  long long qdst, int* __restrict__ exps, int m, int g,
-                                                 uint32_t (*red)[32], int* s_e, unsigned long long (*tile)[33]) {
+                                                 uint32_t (*red)[32], int* s_e, unsigned long long (*tile)[33],
+                                                 int* __restrict__ band = nullptr) {
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = 32 * g + lane;
   uint32_t hmax = 0;
+  int wmax = 0;
   if (n < m)
-    for (int k = warp; k < m; k += 8) hmax = max(hmax, (uint32_t)(bits[(long long)k * m + n] >> 32) & 0x7fffffffu);
+    for (int k = warp; k < m; k += 8) {
+      const unsigned long long b = bits[(long long)k * m + n];
+      hmax = max(hmax, (uint32_t)(b >> 32) & 0x7fffffffu);
+      if (band && (b << 1)) wmax = max(wmax, abs(k - n));
+    }
+  if (band) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0 && wmax > 0) atomicMax(band, wmax);
+  }
   red[warp][lane] = hmax;
   __syncthreads();
   if (warp == 0) {
@@ -569,7 +596,8 @@ __device__ __forceinline__ void slice_cols_group(const double* __restrict__ src,
 // columns): blockIdx.x = block * groups + group, looping past the grid.
 template <bool COLS>
 __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__ src, int nblocks, int m,
-                                                      __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
+                                                      __nv_bfloat16* __restrict__ dst, int* __restrict__ exps,
+                                                      int* __restrict__ band) {
   __shared__ uint32_t red[8][32];
   __shared__ int s_e[32];
   __shared__ unsigned long long tile[32][33];
@@ -578,9 +606,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__
   for (long long i = blockIdx.x; i < (long long)nblocks * groups; i += gridDim.x) {
     const int q = (int)(i / groups), g = (int)(i - (long long)q * groups);
     if (COLS)
-      slice_cols_group(src + q * mm, dst, q, exps, m, g, red, s_e, tile);
+      slice_cols_group(src + q * mm, dst, q, exps, m, g, red, s_e, tile, band);
     else
-      slice_rows_group(src + q * mm, dst, q, exps, m, g);
+      slice_rows_group(src + q * mm, dst, q, exps, m, g, band);
     __syncthreads();
   }
 }
@@ -1055,6 +1083,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_jobs(const PartDesc* __restric
     case 7: t = p.L - 2 - step; act = t >= 0 && hr; sblk = p.blk / mm + t; dq = 2 * q + (t & 1); break;
     default: act = hl; sblk = p.blk / mm; dq = q; break;
   }
+  // launch B's right operands (Acal_t^T, ZL_t^T before the last row) are
+  // not needed when its products run in the banded kernel
+  if (jobs.band && *jobs.band <= kBandMax && (jb.kind == 2 || (jb.kind == 3 && t < p.L - 1))) act = false;
   if (!act) return;
   __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(jb.dst);
   if (jb.kind == 0 || jb.kind == 1)
@@ -1071,10 +1102,11 @@ __global__ void __launch_bounds__(256) k_oz_slice_seps(const SepDesc* __restrict
                                                        const double* __restrict__ C, const double* __restrict__ ZL,
                                                        const double* __restrict__ ZR, __nv_bfloat16* __restrict__ Cq,
                                                        int* __restrict__ eCq, __nv_bfloat16* __restrict__ Sp,
-                                                       int* __restrict__ eS) {
+                                                       int* __restrict__ eS, const int* __restrict__ band) {
   __shared__ uint32_t red[8][32];
   __shared__ int s_e[32];
   __shared__ unsigned long long tile[32][33];
+  if (band && *band <= kBandMax) return;  // the banded assembly needs no slices
   const int groups = (m + 31) / 32;
   const int s = blockIdx.x / groups, g = blockIdx.x - s * groups, job = blockIdx.y;
   const SepDesc sd = seps[s];
@@ -1086,6 +1118,131 @@ __global__ void __launch_bounds__(256) k_oz_slice_seps(const SepDesc* __restrict
   const double* src = job == 1 ? ZR + sd.blk_prev : job == 2 ? ZL + sd.blk_prev : job == 3 ? ZL + sd.blk_next
                                                                                          : ZR + sd.blk_next;
   slice_cols_group(src, Sp, 4LL * s + job - 1, eS, m, g, red, s_e, tile);
+}
+
+// ---------------------------------------------------------------- banded operands
+// When every A and C block of the level has its nonzeros within w <= kBandMax
+// of the diagonal (detected by the input slicing), the products with A or C
+// as an operand cost (2w + 1) multiply-adds per entry instead of m: these
+// float64 kernels compute them over the band (the other terms are exact
+// zeros), and the tensor-core tiles and slices for them are skipped.  A CTA
+// takes 32 rows of one block (blockIdx.x = unit * groups + group); a warp a
+// row at a time, a lane every 32nd column; the band of the banded operand in
+// shared memory, the dense operand read along rows (coalesced).
+
+// launch A's first product: X = G_t C_t (Acal_t, or the right spike ZR_{L-1})
+__global__ void __launch_bounds__(256) k_band_gc(const PartDesc* __restrict__ parts, int t, int m,
+                                                 const double* __restrict__ G, const double* __restrict__ C,
+                                                 double* __restrict__ Acal, double* __restrict__ ZR,
+                                                 const int* __restrict__ band) {
+  __shared__ double bd[2 * kBandMax + 1][kMaxMTensor];  // bd[d + w][n] = C[n + d][n]
+  const int w = *band;
+  if (w > kBandMax) return;
+  const int groups = (m + 31) / 32;
+  const int q = blockIdx.x / groups, g = blockIdx.x - q * groups;
+  const PartDesc p = parts[q];
+  if (t >= p.L || (t == p.L - 1 && !(p.flags & HAS_RIGHT))) return;
+  const long long mm = (long long)m * m, o = p.blk + (long long)t * mm;
+  const double* Gt = G + o;
+  const double* Ct = C + o;
+  double* X = (t < p.L - 1 ? Acal : ZR) + o;
+  for (int i = threadIdx.x; i < (2 * w + 1) * m; i += blockDim.x) {
+    const int dd = i / m, n = i - dd * m, k = n + dd - w;
+    bd[dd][n] = (k >= 0 && k < m) ? Ct[(long long)k * m + n] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 32 * g + warp; r < min(m, 32 * g + 32); r += 8)
+    for (int n = lane; n < m; n += 32) {
+      double acc = 0.0;
+      for (int d = -w; d <= w; ++d) {
+        const int k = n + d;
+        if (k >= 0 && k < m) acc = fma(Gt[(long long)r * m + k], bd[d + w][n], acc);
+      }
+      X[(long long)r * m + n] = acc;
+    }
+}
+
+// Row r of the banded left operand L times the dense X: sum_{k=r-w..r+w} L[r][k] X[k][n].
+__device__ __forceinline__ double band_row(const double* lb, const double* __restrict__ X, int r, int n, int m,
+                                           int w) {
+  double acc = 0.0;
+  for (int d = -w; d <= w; ++d) {
+    const int k = r + d;
+    if (k >= 0 && k < m) acc = fma(lb[d + w], X[(long long)k * m + n], acc);
+  }
+  return acc;
+}
+
+// The 32 rows' bands of L into lb[row][d + w] = L[r][r + d].
+__device__ __forceinline__ void load_row_band(double (*lb)[2 * kBandMax + 1], const double* __restrict__ L, int g, int m,
+                                              int w) {
+  for (int i = threadIdx.x; i < 32 * (2 * w + 1); i += blockDim.x) {
+    const int rl = i / (2 * w + 1), dd = i - rl * (2 * w + 1), r = 32 * g + rl, k = r + dd - w;
+    lb[rl][dd] = (r < m && k >= 0 && k < m) ? L[(long long)r * m + k] : 0.0;
+  }
+}
+
+// launch B: D_{t+1} = B_{t+1} - A_{t+1} Acal_t (blockIdx.y = 0) and
+// Y_{t+1} = -A_{t+1} Bcal_t (= ZL_t, blockIdx.y = 1, with a left spike)
+__global__ void __launch_bounds__(256) k_band_b(const PartDesc* __restrict__ parts, int t, int m,
+                                                const double* __restrict__ A, const double* __restrict__ B,
+                                                const double* __restrict__ Acal, const double* __restrict__ ZL,
+                                                double* __restrict__ G, double* __restrict__ Y,
+                                                const int* __restrict__ band) {
+  __shared__ double lb[32][2 * kBandMax + 1];
+  const int w = *band;
+  if (w > kBandMax) return;
+  const int groups = (m + 31) / 32;
+  const int q = blockIdx.x / groups, g = blockIdx.x - q * groups, j = blockIdx.y;
+  const PartDesc p = parts[q];
+  if (t >= p.L - 1 || (j == 1 && !(p.flags & HAS_LEFT))) return;
+  const long long mm = (long long)m * m, o = p.blk + (long long)t * mm;
+  load_row_band(lb, A + o + mm, g, m, w);
+  __syncthreads();
+  const double* X = (j == 0 ? Acal : ZL) + o;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 32 * g + warp; r < min(m, 32 * g + 32); r += 8)
+    for (int n = lane; n < m; n += 32) {
+      const double v = band_row(lb[r - 32 * g], X, r, n, m, w);
+      const long long e = (long long)r * m + n;
+      if (j == 0)
+        G[o + mm + e] = B[o + mm + e] - v;  // D_{t+1}
+      else
+        Y[(long long)q * mm + e] = -v;      // Y_{t+1}
+    }
+}
+
+// the supplementary blocks (Eq. e2311): blockIdx.y = 0: HB = B_q - A_q ZR^j[q-1]
+// - C_q ZL^{j+1}[q+1]; 1: HA = -A_q ZL^j[q-1]; 2: HC = -C_q ZR^{j+1}[q+1]
+__global__ void __launch_bounds__(256) k_band_h(const SepDesc* __restrict__ seps, int m, const double* __restrict__ A,
+                                                const double* __restrict__ B, const double* __restrict__ C,
+                                                const double* __restrict__ ZL, const double* __restrict__ ZR,
+                                                double* __restrict__ HA, double* __restrict__ HB,
+                                                double* __restrict__ HC, const int* __restrict__ band) {
+  __shared__ double ab[32][2 * kBandMax + 1], cb[32][2 * kBandMax + 1];
+  const int w = *band;
+  if (w > kBandMax) return;
+  const int groups = (m + 31) / 32;
+  const int s = blockIdx.x / groups, g = blockIdx.x - s * groups, j = blockIdx.y;
+  const SepDesc sd = seps[s];
+  if ((j == 1 && !(sd.flags & HAS_HA)) || (j == 2 && !(sd.flags & HAS_HC))) return;
+  if (j != 2) load_row_band(ab, A + sd.blk_q, g, m, w);
+  if (j != 1) load_row_band(cb, C + sd.blk_q, g, m, w);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 32 * g + warp; r < min(m, 32 * g + 32); r += 8)
+    for (int n = lane; n < m; n += 32) {
+      const int rl = r - 32 * g;
+      const long long e = (long long)r * m + n;
+      if (j == 0)
+        HB[sd.hblk + e] = B[sd.blk_q + e] - (band_row(ab[rl], ZR + sd.blk_prev, r, n, m, w) +
+                                             band_row(cb[rl], ZL + sd.blk_next, r, n, m, w));
+      else if (j == 1)
+        HA[sd.hblk + e] = -band_row(ab[rl], ZL + sd.blk_prev, r, n, m, w);
+      else
+        HC[sd.hblk + e] = -band_row(cb[rl], ZR + sd.blk_next, r, n, m, w);
+    }
 }
 
 }  // namespace oz
@@ -1135,14 +1292,15 @@ bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* 
 int oz_box_rows_left() { return oz::MT; }
 int oz_box_rows_right() { return oz::NT; }
 
-void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, cudaStream_t st) {
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, int* band,
+                         cudaStream_t st) {
   if (nblocks <= 0) return;
   const long long work = (long long)nblocks * ((m + 31) / 32);
   const int grid = (int)std::min<long long>(work, 152LL * 16);
   if (cols)
-    oz::k_oz_slice_all<true><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps);
+    oz::k_oz_slice_all<true><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps, band);
   else
-    oz::k_oz_slice_all<false><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps);
+    oz::k_oz_slice_all<false><<<grid, 256, 0, st>>>(src, nblocks, m, static_cast<__nv_bfloat16*>(dst), exps, band);
 }
 
 void launch_oz_slice_jobs(const PartDesc* parts, int nparts, int step, int m, const OzSliceJobs& jobs, int njobs,
@@ -1242,11 +1400,11 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
 
 void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, const double* C, const double* ZL,
                         const double* ZR, double* HA, double* HB, double* HC, const OzAsm& a, const int* eA,
-                        const void* mapA, int* errflag, cudaStream_t st) {
+                        const void* mapA, int* errflag, const int* band, cudaStream_t st) {
   if (nseps <= 0) return;
   oz::k_oz_slice_seps<<<dim3(nseps * ((m + 31) / 32), 5), 256, 0, st>>>(
-      seps, m, C, ZL, ZR, static_cast<__nv_bfloat16*>(a.Cq), a.eCq, static_cast<__nv_bfloat16*>(a.S), a.eS);
-  OzOut out{B, nullptr, nullptr, nullptr, nullptr, nullptr, seps, HA, HB, HC};
+      seps, m, C, ZL, ZR, static_cast<__nv_bfloat16*>(a.Cq), a.eCq, static_cast<__nv_bfloat16*>(a.S), a.eS, band);
+  OzOut out{B, nullptr, nullptr, nullptr, nullptr, nullptr, seps, HA, HB, HC, band};
   unsigned char maps3[3 * 128];
   std::memcpy(maps3, mapA, 128);
   std::memcpy(maps3 + 128, a.maps[1], 128);
@@ -1254,6 +1412,25 @@ void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, 
   launch_oz_step(4, nullptr, nseps, 0, m, out, eA, a.eS, a.eS, maps3, errflag, st);
   std::memcpy(maps3, a.maps[0], 128);
   launch_oz_step(5, nullptr, nseps, 0, m, out, a.eCq, a.eS, a.eS, maps3, errflag, st);
+}
+
+void launch_band_gc(const PartDesc* parts, int nparts, int t, int m, const double* G, const double* C, double* Acal,
+                    double* ZR, const int* band, cudaStream_t st) {
+  if (nparts <= 0 || !band) return;
+  oz::k_band_gc<<<nparts * ((m + 31) / 32), 256, 0, st>>>(parts, t, m, G, C, Acal, ZR, band);
+}
+
+void launch_band_b(const PartDesc* parts, int nparts, int t, int m, const double* A, const double* B,
+                   const double* Acal, const double* ZL, double* G, double* Y, const int* band, cudaStream_t st) {
+  if (nparts <= 0 || !band) return;
+  oz::k_band_b<<<dim3(nparts * ((m + 31) / 32), 2), 256, 0, st>>>(parts, t, m, A, B, Acal, ZL, G, Y, band);
+}
+
+void launch_band_h(const SepDesc* seps, int nseps, int m, const double* A, const double* B, const double* C,
+                   const double* ZL, const double* ZR, double* HA, double* HB, double* HC, const int* band,
+                   cudaStream_t st) {
+  if (nseps <= 0 || !band) return;
+  oz::k_band_h<<<dim3(nseps * ((m + 31) / 32), 3), 256, 0, st>>>(seps, m, A, B, C, ZL, ZR, HA, HB, HC, band);
 }
 
 }  // namespace dm

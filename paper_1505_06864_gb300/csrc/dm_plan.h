@@ -15,7 +15,8 @@ namespace dm {
 // Kernel classes of the profiler (one per launcher).
 enum KClass {
   K_INV, K_FWD_FACTOR, K_BACK_FACTOR, K_ASSEMBLE_H, K_FWD_SOLVE, K_BACK_SOLVE, K_ASSEMBLE_F,
-  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_TC_CONVERT, K_INV_PANEL, K_INV_UPDATE, K_NCLASS
+  K_BACKSUB, K_SEP_COPY, K_RESIDUAL, K_AXPY, K_SWEEP_SOLVE, K_TC_CONVERT, K_INV_PANEL, K_INV_UPDATE, K_BANDED,
+  K_NCLASS
 };
 extern const char* const kClassNames[K_NCLASS];
 
@@ -109,6 +110,12 @@ struct OzLevel {
   // the supplementary blocks on the tensor cores (levels with a supplementary level)
   bool asm_on = false;
   OzAsm as;
+  // banded A and C: the largest |row - column| of a nonzero entry, found by
+  // the input slicing on the device (null: detection off, DM_BANDED=0), and
+  // its copy in page-locked host memory after each factorisation (for the
+  // profiling costs of the next one; the device decides the path)
+  int* band = nullptr;
+  int* band_host = nullptr;
 };
 
 // One level of the recursion: a set of independent systems, each split into
@@ -136,6 +143,7 @@ struct Level {
   // per-step launch costs
   std::vector<Cost> c_inv, c_fwd, c_back, c_fwds, c_backs;
   std::vector<Cost> c_fwdA, c_fwdB;  // the two launches of a forward step of the tensor-core step kernels
+  std::vector<Cost> c_fwdA0;         // launch A's first product (G_t C_t) alone
   Cost c_cvt;                         // one operand conversion of the level's blocks
   std::vector<double> fwd_chain_frac;  // share of c_fwd[t] in the type-0 (chain) tiles
   std::vector<int> last_part;           // per system: index in parts of its last subsystem

@@ -615,6 +615,41 @@ def test_fp64_sliced_assembly(dm, monkeypatch, N, m, r, P, levels):
         check(xs["sliced"], xs["fma"], tol)
 
 
+@pytest.mark.parametrize("N,m,r,P,levels,hb", [(48, 64, 1, 6, 2, 3), (40, 40, 2, 5, 1, 6), (40, 40, 2, 5, 1, 7),
+                                               (30, 256, 1, 4, 1, 3), (64, 16, 2, 8, 2, 2)])
+def test_banded_products(dm, monkeypatch, N, m, r, P, levels, hb):
+    """Banded off-diagonal blocks (half-bandwidth hb): with hb <= 6 the
+    products with A or C as an operand run over the band in float64 (found by
+    the input slicing on the device), with hb = 7 the tensor-core products
+    run; both against the oracle and against the path with the detection off
+    (DM_BANDED=0), also on recursion levels whose own blocks are dense."""
+    s = w.pde_banded_system(N, m, r, 500 + N + hb, hb=hb)
+    xs = {}
+    for mode in ("auto", "off"):
+        if mode == "off":
+            monkeypatch.setenv("DM_BANDED", "0")
+        x, rel, info = solve(dm, s, P, levels)
+        assert rel < 1e-13
+        xs[mode] = x
+    monkeypatch.delenv("DM_BANDED")
+    # the path taken: a second factorisation's profile counts banded flops
+    # exactly when the first one found a band of at most 6
+    plan = dm.dm_plan(N, m, r, P, levels, "fp64")
+    try:
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        dm.dm_profile(plan, True)
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        prof = dm.dm_profile(plan, False)
+    finally:
+        dm.dm_destroy(plan)
+    banded_flops = prof.get("banded", {}).get("flops", 0.0)
+    assert (banded_flops > 0) == (hb <= 6)
+    xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
+    check(xs["auto"], xo, TOL64)
+    check(xs["off"], xo, TOL64)
+    check(xs["auto"], xs["off"], TOL64)
+
+
 def test_singular_block_reported_blocked_inverse(dm):
     """A zero Schur complement on a sliced level (m = 16): the blocked
     inversion reports DM_ESINGULAR with the block row, like the cluster one."""
