@@ -719,7 +719,10 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
   const int* r1exp[3] = {Z.eYT, Z.eZLT, Z.eZRT};
   auto job = [](const double* src, void* dst, int* e, int kind) { return OzSliceJob{src, dst, e, kind}; };
   auto slice_inputs = [&] {
-    if (Z.band) cudaMemsetAsync(Z.band, 0, sizeof(int), st);
+    if (Z.band) {
+      cudaMemsetAsync(Z.band, 0, sizeof(int), st);
+      launch_band_detect(L.A, L.C, L.nblk, m, Z.band, st);
+    }
     launch_oz_slice_all(false, L.A, (int)nb, m, Z.A, Z.eA, Z.band, st);
     launch_oz_slice_all(true, L.C, (int)nb, m, Z.CT, Z.eCT, Z.band, st);
     if (Z.band) cudaMemcpyAsync(Z.band_host, Z.band, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -728,7 +731,7 @@ static void factor_level_oz(Level& L, cudaStream_t st, Prof& pf) {
     launch_oz_slice_jobs(L.d_parts, L.nparts, 0, m, j0, 1, st);
   };
   Cost cslice = L.c_cvt;
-  DM_LAUNCH_K(pf, st, K_TC_CONVERT, cslice, 1, 3, slice_inputs());
+  DM_LAUNCH_K(pf, st, K_TC_CONVERT, cslice, 1, Z.band ? 4 : 3, slice_inputs());
   Cost cs;
   cs.bytes = 26.0 * m * m;  // one block: float64 read, nine bf16 slices written
   for (int t = 0; t < L.Lmax; ++t) {

@@ -168,8 +168,11 @@ struct OzAsm {
 void launch_oz_assemble(const SepDesc* seps, int nseps, int m, const double* B, const double* C, const double* ZL,
                         const double* ZR, double* HA, double* HB, double* HC, const OzAsm& a, const int* eA,
                         const void* mapA, int* errflag, const int* band, cudaStream_t st);
-void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, int* band,
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, const int* band,
                          cudaStream_t st);
+// The level's band into *band (atomicMax; the caller zeroes it first): the
+// largest |row - column| of a nonzero entry of the n entries of A and of C.
+void launch_band_detect(const double* A, const double* C, long long n, int m, int* band, cudaStream_t st);
 // Products with a banded operand (half-bandwidth w = *band <= kBandMax, else
 // nothing is done): G_t C_t of launch A, both products of launch B, and the
 // supplementary blocks; float64 multiply-adds over the band only.

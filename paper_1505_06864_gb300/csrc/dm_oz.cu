@@ -393,6 +393,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int ci = 0; ci < NT / 16; ++ci) {
         const int ch = half * (NT / 2) + 8 * ci;
+        // chunks past the block's last column, and (KIND 3) inside the
+        // panel's columns, produce nothing: only the release of the
+        // accumulators after the last chunk remains
+        const int c0n = w.tn * NT + ch;
+        const bool dead = c0n >= m || (KIND == 3 && c0n >= k0 && c0n < k0 + 32);
+        if (dead) {
+          if (ci == NT / 16 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty);
+          } else {
+            load_in(ci + 1, innext);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) incur[i] = innext[i];
+          }
+          continue;
+        }
         uint32_t r[NACC][8];
 #pragma unroll
         for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
@@ -488,23 +505,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Row slices (left operands): exps[r] = e with |v| < 2^e for the row's
 // largest |v|; slice s element (r, k) at (q * 9 + s) m^2 + r m + k.  One
 // warp per row, eight consecutive columns per lane (m % 8 == 0).
-// With `band` set, the largest |row - column| of a nonzero entry seen is
-// folded into *band (atomicMax), for the banded-product path.
 __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                                 long long qdst, int* __restrict__ exps, int m, int g,
-                                                 int* __restrict__ band = nullptr) {
+                                                 long long qdst, int* __restrict__ exps, int m, int g) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
   const int rend = min(m, 32 * g + 32);
-  int wmax = 0;
   for (int r = 32 * g + warp; r < rend; r += nw) {
     uint32_t hmax = 0;
-    for (int c = lane; c < m; c += 32) {
-      const unsigned long long b = bits[(long long)r * m + c];
-      hmax = max(hmax, (uint32_t)(b >> 32) & 0x7fffffffu);
-      if (band && (b << 1)) wmax = max(wmax, abs(r - c));
-    }
+    for (int c = lane; c < m; c += 32) hmax = max(hmax, (uint32_t)(bits[(long long)r * m + c] >> 32) & 0x7fffffffu);
 #pragma unroll
     for (int o = 16; o; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
     const int e = scale_exponent(hmax);
@@ -524,11 +533,6 @@ __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src,
       }
     }
   }
-  if (band) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    if (lane == 0 && wmax > 0) atomicMax(band, wmax);
-  }
 }
 
 // Column slices, transposed (right operands): exps[n] for column n, slice s
@@ -538,25 +542,14 @@ __device__ __forceinline__ void slice_rows_group(const double* __restrict__ src,
 // per slice (8-byte stores).  256 threads.
 __device__ __forceinline__ void slice_cols_group(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
                                                  long long qdst, int* __restrict__ exps, int m, int g,
-                                                 uint32_t (*red)[32], int* s_e, unsigned long long (*tile)[33],
-                                                 int* __restrict__ band = nullptr) {
+                                                 uint32_t (*red)[32], int* s_e, unsigned long long (*tile)[33]) {
   const long long mm = (long long)m * m;
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(src);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = 32 * g + lane;
   uint32_t hmax = 0;
-  int wmax = 0;
   if (n < m)
-    for (int k = warp; k < m; k += 8) {
-      const unsigned long long b = bits[(long long)k * m + n];
-      hmax = max(hmax, (uint32_t)(b >> 32) & 0x7fffffffu);
-      if (band && (b << 1)) wmax = max(wmax, abs(k - n));
-    }
-  if (band) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    if (lane == 0 && wmax > 0) atomicMax(band, wmax);
-  }
+    for (int k = warp; k < m; k += 8) hmax = max(hmax, (uint32_t)(bits[(long long)k * m + n] >> 32) & 0x7fffffffu);
   red[warp][lane] = hmax;
   __syncthreads();
   if (warp == 0) {
@@ -594,21 +587,24 @@ __device__ __forceinline__ void slice_cols_group(const double* __restrict__ src,
 
 // Slices of every block of a level's array (A as rows, C as transposed
 // columns): blockIdx.x = block * groups + group, looping past the grid.
+// With `band` set and the level's A and C banded (*band <= kBandMax), nothing
+// is done: only the tensor-core tiles the banded kernels replace read these.
 template <bool COLS>
 __global__ void __launch_bounds__(256) k_oz_slice_all(const double* __restrict__ src, int nblocks, int m,
                                                       __nv_bfloat16* __restrict__ dst, int* __restrict__ exps,
-                                                      int* __restrict__ band) {
+                                                      const int* __restrict__ band) {
   __shared__ uint32_t red[8][32];
   __shared__ int s_e[32];
   __shared__ unsigned long long tile[32][33];
+  if (band && *band <= kBandMax) return;
   const long long mm = (long long)m * m;
   const int groups = (m + 31) / 32;
   for (long long i = blockIdx.x; i < (long long)nblocks * groups; i += gridDim.x) {
     const int q = (int)(i / groups), g = (int)(i - (long long)q * groups);
     if (COLS)
-      slice_cols_group(src + q * mm, dst, q, exps, m, g, red, s_e, tile, band);
+      slice_cols_group(src + q * mm, dst, q, exps, m, g, red, s_e, tile);
     else
-      slice_rows_group(src + q * mm, dst, q, exps, m, g, band);
+      slice_rows_group(src + q * mm, dst, q, exps, m, g);
     __syncthreads();
   }
 }
@@ -1245,6 +1241,24 @@ __global__ void __launch_bounds__(256) k_band_h(const SepDesc* __restrict__ seps
     }
 }
 
+// The level's band: the largest |row - column| of a nonzero entry (any bit
+// but the sign set) of the A and C blocks, folded into *band.  Read only.
+__global__ void __launch_bounds__(256) k_band_detect(const double* __restrict__ A, const double* __restrict__ C,
+                                                     long long n, int m, int* __restrict__ band) {
+  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(A);
+  const unsigned long long* c = reinterpret_cast<const unsigned long long*>(C);
+  int wmax = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    if (((a[e] | c[e]) << 1) != 0) {
+      const int col = (int)(e % m), row = (int)((e / m) % m);
+      wmax = max(wmax, abs(row - col));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(band, wmax);
+}
+
 }  // namespace oz
 
 // ---------------------------------------------------------------- host side
@@ -1292,7 +1306,12 @@ bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* 
 int oz_box_rows_left() { return oz::MT; }
 int oz_box_rows_right() { return oz::NT; }
 
-void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, int* band,
+void launch_band_detect(const double* A, const double* C, long long n, int m, int* band, cudaStream_t st) {
+  if (n <= 0 || !band) return;
+  oz::k_band_detect<<<152 * 8, 256, 0, st>>>(A, C, n, m, band);
+}
+
+void launch_oz_slice_all(bool cols, const double* src, int nblocks, int m, void* dst, int* exps, const int* band,
                          cudaStream_t st) {
   if (nblocks <= 0) return;
   const long long work = (long long)nblocks * ((m + 31) / 32);
