@@ -470,6 +470,7 @@ int Level::allocate() {
     const char* eb = std::getenv("DM_BANDED");
     if (!(eb && std::strcmp(eb, "0") == 0)) {
       DM_ALLOC(Z.band, sizeof(int));
+      cudaMemset(Z.band, 0x7f, sizeof(int));  // "not banded" until a factorisation finds out
       if (cudaHostAlloc(reinterpret_cast<void**>(&Z.band_host), sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return set_error(DM_ENOMEM, "cudaHostAlloc of 4 bytes failed");
@@ -1291,10 +1292,16 @@ void Plan::residual(const double* x_dev, const double* b_dev, double* r_dev) {
   Cost c64 = top.c_resid;
   c64.flops -= top.c_resid_tc.flops;
   c64.bytes -= top.c_resid_tc.bytes;
+  if (top.oz.band && *top.oz.band_host <= kBandMax) {
+    // banded A, C: 2 m^2 r (B) + 4 (2w + 1) m r flops and B plus the bands read per row
+    const double m = top.max_m, w = *top.oz.band_host, f = (2.0 * m * m + 4.0 * (2 * w + 1) * m) / (6.0 * m * m);
+    c64.flops *= f;
+    c64.bytes *= (m * m + 2 * (2 * w + 1) * m + 3 * m) / (3.0 * m * m + 3 * m);
+  }
   if (top.nsys > top.nres_tc)
     DM_LAUNCH(prof, stream, K_RESIDUAL, c64, top.nsys - top.nres_tc,
               launch_residual(top.d_sys, top.nsys, top.nrows, top.max_m, top.max_r, top.A, top.B, top.C, x_dev,
-                              b_dev, r_dev, nrm, stream));
+                              b_dev, r_dev, nrm, stream, top.oz.band));
   if (top.nres_tc > 0) {
     DM_LAUNCH(prof, stream, K_RESIDUAL, Cost(), top.nres_tc,
               launch_col_scales(top.d_sys, top.nsys, top.nrows, x_dev, colhi, stream));

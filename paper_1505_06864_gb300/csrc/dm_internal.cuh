@@ -87,9 +87,11 @@ void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const
                      double* x, cudaStream_t st);
 // r = b - T x (float64), per-system column norms: nrm[s*4*64 + 0*64 + c] = ||r_c||^2,
 // [1] = ||b_c||^2 (both accumulated by atomics; zeroed by the caller).
+// With `band` (a level's band flag, see OzOut::band) at most kBandMax, the A
+// and C products run over the band only.
 void launch_residual(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* A,
                      const double* B, const double* C, const double* x, const double* b, double* r,
-                     double* nrm, cudaStream_t st);
+                     double* nrm, cudaStream_t st, const int* band = nullptr);
 // x += d, nrm[2] += ||d_c||^2, nrm[3] += ||x_c||^2 (after the update)
 // Residual b - T x of the systems with SysDesc::sliced set, float64-accurate
 // from exact bf16 slice products on the tensor cores (m <= 128, r <= 16).

@@ -1518,9 +1518,13 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
                                                   const double* __restrict__ x,
                                                   const double* __restrict__ b,
                                                   double* __restrict__ rout,
-                                                  double* __restrict__ nrm) {
+                                                  double* __restrict__ nrm,
+                                                  const int* __restrict__ band) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2 * kMaxR];
+  // A and C banded (half-bandwidth w <= kBandMax, found by the factorisation
+  // of these blocks): their products run over the band only
+  const int wb = band ? *band : kBandMax + 1;
   const int si = find_sys(sys, nsys, blockIdx.x);
   const SysDesc sd = sys[si];
   if (sd.sliced) return;  // residual on the tensor cores (k_residual_sliced)
@@ -1550,14 +1554,31 @@ __global__ void __launch_bounds__(256) k_residual(const SysDesc* __restrict__ sy
         const double* ar = A + o + (long long)row * m;
         const double* br = B + o + (long long)row * m;
         const double* cr = C + o + (long long)row * m;
+        if (wb <= kBandMax) {
 #pragma unroll 2
-        for (int k = 0; k < m; ++k) {
-          const double av = hasA ? ar[k] : 0.0, bv = br[k], cv = hasC ? cr[k] : 0.0;
-          const double* xm = xs + k * RB;
-          const double* x0 = xm + m * RB;
-          const double* xp = x0 + m * RB;
+          for (int k = 0; k < m; ++k) {
+            const double bv = br[k];
+            const double* x0 = xs + (m + k) * RB;
 #pragma unroll
-          for (int c = 0; c < RB; ++c) acc[c] = fma(av, xm[c], fma(bv, x0[c], fma(cv, xp[c], acc[c])));
+            for (int c = 0; c < RB; ++c) acc[c] = fma(bv, x0[c], acc[c]);
+          }
+          for (int k = max(0, row - wb); k <= min(m - 1, row + wb); ++k) {
+            const double av = hasA ? ar[k] : 0.0, cv = hasC ? cr[k] : 0.0;
+            const double* xm = xs + k * RB;
+            const double* xp = xm + 2 * m * RB;
+#pragma unroll
+            for (int c = 0; c < RB; ++c) acc[c] = fma(av, xm[c], fma(cv, xp[c], acc[c]));
+          }
+        } else {
+#pragma unroll 2
+          for (int k = 0; k < m; ++k) {
+            const double av = hasA ? ar[k] : 0.0, bv = br[k], cv = hasC ? cr[k] : 0.0;
+            const double* xm = xs + k * RB;
+            const double* x0 = xm + m * RB;
+            const double* xp = x0 + m * RB;
+#pragma unroll
+            for (int c = 0; c < RB; ++c) acc[c] = fma(av, xm[c], fma(bv, x0[c], fma(cv, xp[c], acc[c])));
+          }
         }
 #pragma unroll
         for (int c = 0; c < RB; ++c) {
@@ -2063,13 +2084,13 @@ void launch_sep_copy(const SepDesc* seps, int nseps, int max_m, int max_r, const
 
 void launch_residual(const SysDesc* sys, int nsys, int nrows, int max_m, int max_r, const double* A,
                      const double* B, const double* C, const double* x, const double* b, double* r,
-                     double* nrm, cudaStream_t st) {
+                     double* nrm, cudaStream_t st, const int* band) {
   if (nsys <= 0 || nrows <= 0) return;
   auto go = [&](auto rm) {
     constexpr int RM = decltype(rm)::value;
     const size_t bytes = sizeof(double) * 3 * (size_t)max_m * RM;
     allow_smem(k_residual<RM>, bytes);
-    k_residual<RM><<<nrows, 256, bytes, st>>>(sys, nsys, A, B, C, x, b, r, nrm);
+    k_residual<RM><<<nrows, 256, bytes, st>>>(sys, nsys, A, B, C, x, b, r, nrm, band);
   };
   if (!narrow_dispatch(max_r, go)) go(std::integral_constant<int, 16>());
 }
