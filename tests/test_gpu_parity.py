@@ -615,15 +615,20 @@ def test_fp64_sliced_assembly(dm, monkeypatch, N, m, r, P, levels):
         check(xs["sliced"], xs["fma"], tol)
 
 
-@pytest.mark.parametrize("N,m,r,P,levels,hb", [(48, 64, 1, 6, 2, 3), (40, 40, 2, 5, 1, 6), (40, 40, 2, 5, 1, 7),
-                                               (30, 256, 1, 4, 1, 3), (64, 16, 2, 8, 2, 2)])
-def test_banded_products(dm, monkeypatch, N, m, r, P, levels, hb):
+@pytest.mark.parametrize("N,m,r,P,levels,hb,spike", [(48, 64, 1, 6, 2, 3, False), (40, 40, 2, 5, 1, 6, False),
+                                                     (40, 40, 2, 5, 1, 7, False), (30, 256, 1, 4, 1, 3, False),
+                                                     (64, 16, 2, 8, 2, 2, False), (40, 40, 2, 5, 1, 3, True)])
+def test_banded_products(dm, monkeypatch, N, m, r, P, levels, hb, spike):
     """Banded off-diagonal blocks (half-bandwidth hb): with hb <= 6 the
-    products with A or C as an operand run over the band in float64 (found by
-    the input slicing on the device), with hb = 7 the tensor-core products
-    run; both against the oracle and against the path with the detection off
+    products with A or C as an operand run over the band in float64 (found on
+    the device before each factorisation), with hb = 7 -- or one entry far from
+    the diagonal in a single C block (spike) -- the tensor-core products run;
+    both against the oracle and against the path with the detection off
     (DM_BANDED=0), also on recursion levels whose own blocks are dense."""
     s = w.pde_banded_system(N, m, r, 500 + N + hb, hb=hb)
+    if spike:  # one off-band entry in one block; b re-manufactured for x_true
+        s.C[N // 2][0][m - 1] = 0.25
+        s.b[:] = w.manufacture_rhs(s.A, s.B, s.C, s.x_true)
     xs = {}
     for mode in ("auto", "off"):
         if mode == "off":
@@ -643,7 +648,7 @@ def test_banded_products(dm, monkeypatch, N, m, r, P, levels, hb):
     finally:
         dm.dm_destroy(plan)
     banded_flops = prof.get("banded", {}).get("flops", 0.0)
-    assert (banded_flops > 0) == (hb <= 6)
+    assert (banded_flops > 0) == (hb <= 6 and not spike)
     xo = o.dm(s.A, s.B, s.C, s.b, P, levels=levels, P2=info["P2"] if info["P2"] > 1 else None)
     check(xs["auto"], xo, TOL64)
     check(xs["off"], xo, TOL64)
