@@ -119,6 +119,11 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
  * the sums are combined in float64 -- an error bound of the size of the
  * float64 dot product's.  DM_PLAN_FP64_FMA keeps them on the float64 pipe. */
 #define DM_PLAN_FP64_FMA 2
+/* The float64 block inverse of those levels is by default blocked
+ * Gauss-Jordan (panels of 32 columns in float64, their rank-32 trailing
+ * updates as digit-sliced tensor-core products); DM_PLAN_FP64_INV_COLUMN
+ * takes the column-by-column Gauss-Jordan kernel instead (same pivoting). */
+#define DM_PLAN_FP64_INV_COLUMN 4
 int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags);
 
 /* DM inside the subsystems (Section 4.2.2; counts Eqs. DMrec121, DMrec1212,
@@ -201,6 +206,14 @@ int dm_solve(dm_plan_t plan, const double* b, double* x, double* relres_out);
  * for the synthetic system and one plan at a time; a call for a remembered
  * shape returns at once. */
 int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* levels, double* ms_out);
+
+/* dm_autotune that also times the kernel variants at the chosen (P, levels):
+ * for float64 plans whose levels can use the digit-sliced products, the
+ * products on the float64 pipe (DM_PLAN_FP64_FMA) and the column-by-column
+ * inverse (DM_PLAN_FP64_INV_COLUMN); *flags receives the fastest variant's
+ * plan flags (0: the defaults), which dm_plan with P = 0 and levels = 0 then
+ * applies.  flags may be NULL. */
+int dm_autotune_ex(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags, double* ms_out);
 
 /* Continuous batching.  dm_submit queues a solve of b on the plan's resident
  * factors; dm_submit_system queues a factor (of A, B, C) followed by a solve.

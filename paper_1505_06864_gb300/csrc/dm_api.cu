@@ -93,6 +93,7 @@ int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tenso
     supp.reset(new Level());
     supp->depth = depth + 1;
     supp->fp64_fma = fp64_fma;
+    supp->inv_column = inv_column;
     int rc = supp->build(sub, false);
     if (rc) return rc;
   }
@@ -333,9 +334,9 @@ static bool oz_asm_wanted() {
 // column-by-column kernel).  Measured at m = 256 on GB300: faster for every
 // launch size, 64 blocks per launch (the top level) 1.45 vs 2.5 ms, and the
 // supplementary levels' 1-12 blocks per launch 9.2 vs 10.9 ms per factor.
-static bool gj_wanted() {
+static bool gj_wanted(const Level& L) {
   const char* e = std::getenv("DM_FP64_INVERSE");
-  return !(e && std::strcmp(e, "cluster") == 0);
+  return !L.inv_column && !(e && std::strcmp(e, "cluster") == 0);
 }
 
 size_t Level::bytes_needed() const {
@@ -455,7 +456,7 @@ int Level::allocate() {
     for (int i = 0; ok && i < 5; ++i) ok = oz_make_map(rbase[i], rblk[i], m, oz_box_rows_right(), Z.maps[3 + i]);
     if (!ok) return set_error(DM_ECUDA, "tensor map creation for the float64 slice products failed (m = %d)", m);
     Z.on = true;
-    if (gj_wanted()) {
+    if (gj_wanted(*this)) {
       const size_t pb = (size_t)9 * m * 32 * 2;
       DM_ALLOC(Z.U, np * pb);
       DM_ALLOC(Z.V, np * pb);
@@ -1142,6 +1143,7 @@ int Plan::init(const std::vector<SysSpec>& specs, int prec) {
   DM_CUDA(cudaGetDevice(&device));
   top.lazy_inputs = true;
   top.fp64_fma = !specs.empty() && (specs[0].flags & DM_PLAN_FP64_FMA) != 0;
+  top.inv_column = !specs.empty() && (specs[0].flags & DM_PLAN_FP64_INV_COLUMN) != 0;
   int rc = top.build(specs, prec != DM_FP64, prec == DM_TF32 ? 0 : (prec == DM_BF16X3 ? 1 : -1));
   if (rc) return rc;
   {
@@ -1575,7 +1577,8 @@ int dm_plan(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int preci
 
 int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths) {
   if (!lengths) return set_error(DM_EINVAL, "NULL lengths");
-  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA)) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
+  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA | DM_PLAN_FP64_INV_COLUMN))
+    return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, 1, &s);
   if (rc) return rc;
@@ -1587,12 +1590,17 @@ int dm_partition_sizes(int N, int m, int nrhs, int P, int flags, int* lengths) {
 
 int dm_plan_ex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision, int flags) {
   if (!out) return set_error(DM_EINVAL, "out is NULL");
-  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA)) return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
+  if (flags & ~(DM_PLAN_EQUAL_TIME | DM_PLAN_FP64_FMA | DM_PLAN_FP64_INV_COLUMN))
+    return set_error(DM_EINVAL, "unknown plan flags 0x%x", flags);
   if (precision != DM_FP64 && precision != DM_FP32 && precision != DM_TF32 && precision != DM_BF16X3)
     return set_error(DM_EINVAL, "unknown precision %d", precision);
   if ((precision == DM_TF32 || precision == DM_BF16X3) && m > kMaxMTensor)
     return set_error(DM_EINVAL, "tensor-core precisions support m <= %d", kMaxMTensor);
-  if (P == 0 && levels == 0) tuned_lookup(N, m, nrhs, precision, &P, &levels);  // measured choice, if any
+  if (P == 0 && levels == 0) {  // the measured choice, if any, with its kernel variant
+    int tf = 0;
+    if (tuned_lookup(N, m, nrhs, precision, &P, &levels, &tf) && !(flags & (DM_PLAN_FP64_FMA | DM_PLAN_FP64_INV_COLUMN)))
+      flags |= tf;
+  }
   SysSpec s;
   int rc = make_spec(N, m, nrhs, P, levels, &s);
   if (rc) return rc;

@@ -130,6 +130,7 @@ struct Level {
   Tc2Level tc2;
   OzLevel oz;
   bool fp64_fma = false;  // float64 products on the FP64 pipe even where digit slicing applies
+  bool inv_column = false;  // the column-by-column float64 inverse even where the blocked one applies
   int nsys = 0;
   std::vector<SysSpec> spec;
   std::vector<long long> blk0, vec0;  // per-system offsets of row 0
@@ -249,7 +250,8 @@ int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
 bool is_device_ptr(const void* p);
 
 void serve_drain(struct dm_plan_s* plan);
-bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels);
+bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels, int* flags = nullptr);
+int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_out, int* flags_out, bool variants);
 
 }  // namespace dm
 

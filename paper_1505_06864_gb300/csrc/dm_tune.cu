@@ -8,9 +8,12 @@
 // subsystems), each with recursion depth 1, 2 and 3 (Section 4.2.1).  The
 // synthetic system has uniform [-1, 1] blocks made diagonally dominant, drawn
 // on the device by a counter-based hash; the timing covers dm_factor +
-// dm_solve as a user would call them.  Results are kept per (N, m, nrhs,
-// precision) in memory and, when the environment variable DM_TUNE_CACHE names
-// a file, in that file (one line per shape).
+// dm_solve as a user would call them.  With variants (dm_autotune_ex), the
+// kernel variants of float64 sliced levels (products on the FP64 pipe, the
+// column-by-column inverse) are then timed at the chosen (P, levels) and the
+// fastest plan flags kept.  Results are kept per (N, m, nrhs, precision) in
+// memory and, when the environment variable DM_TUNE_CACHE names a file, in
+// that file (one line per shape: N m nrhs precision P levels ms flags).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +28,7 @@
 #include <vector>
 
 #include "../../include/dm.h"
+#include "dm_internal.cuh"
 #include "dm_plan.h"
 
 namespace dm {
@@ -70,6 +74,8 @@ __global__ void k_fill_vec(double* b, long long n, uint64_t seed) {
 struct Choice {
   int P, levels;
   double ms;
+  int flags;      // plan flags of the fastest kernel variant
+  bool variants;  // the variants were timed
 };
 using Key = std::tuple<int, int, int, int>;
 std::mutex g_mu;
@@ -83,10 +89,13 @@ void load_cache_locked() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int N, m, r, prec, P, lv;
-  double ms;
-  while (std::fscanf(f, "%d %d %d %d %d %d %lf", &N, &m, &r, &prec, &P, &lv, &ms) == 7)
-    g_cache[Key(N, m, r, prec)] = Choice{P, lv, ms};
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    int N, m, r, prec, P, lv, fl = 0;
+    double ms;
+    const int k = std::sscanf(line, "%d %d %d %d %d %d %lf %d", &N, &m, &r, &prec, &P, &lv, &ms, &fl);
+    if (k >= 7) g_cache[Key(N, m, r, prec)] = Choice{P, lv, ms, k == 8 ? fl : 0, k == 8};
+  }
   std::fclose(f);
 }
 
@@ -96,8 +105,9 @@ void save_cache_locked() {
   FILE* f = std::fopen(path, "w");
   if (!f) return;
   for (auto& kv : g_cache)
-    std::fprintf(f, "%d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                 std::get<3>(kv.first), kv.second.P, kv.second.levels, kv.second.ms);
+    std::fprintf(f, "%d %d %d %d %d %d %.6f %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), kv.second.P, kv.second.levels, kv.second.ms,
+                 kv.second.flags);
   std::fclose(f);
 }
 
@@ -118,25 +128,29 @@ struct DevBuf {
 
 }  // namespace
 
-bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels) {
+bool tuned_lookup(int N, int m, int r, int prec, int* P, int* levels, int* flags) {
   std::lock_guard<std::mutex> lk(g_mu);
   load_cache_locked();
   auto it = g_cache.find(Key(N, m, r, prec));
   if (it == g_cache.end()) return false;
   *P = it->second.P;
   *levels = it->second.levels;
+  if (flags) *flags = it->second.flags;
   return true;
 }
 
-int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_out) {
+int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_out, int* flags_out, bool variants) {
+  // kernel variants worth timing: float64 levels that can use the digit-sliced products
+  const bool try_variants = variants && prec == DM_FP64 && oz_eligible(m);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache_locked();
     auto it = g_cache.find(Key(N, m, r, prec));
-    if (it != g_cache.end()) {
+    if (it != g_cache.end() && (it->second.variants || !try_variants)) {
       *P_out = it->second.P;
       *lv_out = it->second.levels;
       if (ms_out) *ms_out = it->second.ms;
+      if (flags_out) *flags_out = it->second.flags;
       return DM_OK;
     }
   }
@@ -164,12 +178,13 @@ int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_
   k_shift<<<1024, 256>>>(A.p, B.p, C.p, N, m);
   k_fill_vec<<<256, 256>>>(b.p, nv, 777u);
   if (cudaDeviceSynchronize() != cudaSuccess) return set_error(DM_ECUDA, "autotune: input generation failed");
-  Choice best{0, 0, 1e300};
-  for (auto& c : cand) {
+  // one factor + solve (the second of two) of a candidate plan; 1e300 when it cannot run
+  auto time_plan = [&](int P, int lv, int flags, SysSpec* used) {
     SysSpec s;
-    if (make_spec(N, m, r, std::get<0>(c), std::get<1>(c), &s) != DM_OK) continue;
+    if (make_spec(N, m, r, P, lv, &s) != DM_OK) return 1e300;
+    s.flags = flags;
     Plan plan;
-    if (plan.init(std::vector<SysSpec>{s}, prec) != DM_OK) continue;  // e.g. does not fit: skip
+    if (plan.init(std::vector<SysSpec>{s}, prec) != DM_OK) return 1e300;  // e.g. does not fit: skip
     double ms = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       const auto t0 = std::chrono::steady_clock::now();
@@ -177,15 +192,24 @@ int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_
       std::vector<double> rel(1);
       if (e == DM_OK) e = plan.solve(b.p, x.p, rel.data());
       const auto t1 = std::chrono::steady_clock::now();
-      if (e != DM_OK && e != DM_ENOTCONV) {
-        ms = 1e300;
-        break;
-      }
+      if (e != DM_OK && e != DM_ENOTCONV) return 1e300;
       if (rep == 1) ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     }
-    if (ms < best.ms) best = Choice{s.P, s.levels, ms};
+    if (used) *used = s;
+    return ms;
+  };
+  Choice best{0, 0, 1e300, 0, try_variants};
+  for (auto& c : cand) {
+    SysSpec s;
+    const double ms = time_plan(std::get<0>(c), std::get<1>(c), 0, &s);
+    if (ms < best.ms) best = Choice{s.P, s.levels, ms, 0, try_variants};
   }
   if (best.P == 0) return set_error(DM_ENOMEM, "autotune: no candidate could be timed");
+  if (try_variants)
+    for (int fl : {DM_PLAN_FP64_FMA, DM_PLAN_FP64_INV_COLUMN}) {
+      const double ms = time_plan(best.P, best.levels, fl, nullptr);
+      if (ms < best.ms) best.ms = ms, best.flags = fl;
+    }
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_cache[Key(N, m, r, prec)] = best;
@@ -194,6 +218,7 @@ int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_
   *P_out = best.P;
   *lv_out = best.levels;
   if (ms_out) *ms_out = best.ms;
+  if (flags_out) *flags_out = best.flags;
   return DM_OK;
 }
 
@@ -202,5 +227,11 @@ int autotune(int N, int m, int r, int prec, int* P_out, int* lv_out, double* ms_
 extern "C" int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* levels, double* ms_out) {
   if (!P || !levels) return dm::set_error(DM_EINVAL, "NULL argument to dm_autotune");
   if (precision < DM_FP64 || precision > DM_BF16X3) return dm::set_error(DM_EINVAL, "unknown precision");
-  return dm::autotune(N, m, nrhs, precision, P, levels, ms_out);
+  return dm::autotune(N, m, nrhs, precision, P, levels, ms_out, nullptr, false);
+}
+
+extern "C" int dm_autotune_ex(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags, double* ms_out) {
+  if (!P || !levels) return dm::set_error(DM_EINVAL, "NULL argument to dm_autotune_ex");
+  if (precision < DM_FP64 || precision > DM_BF16X3) return dm::set_error(DM_EINVAL, "unknown precision");
+  return dm::autotune(N, m, nrhs, precision, P, levels, ms_out, flags, true);
 }

@@ -72,6 +72,8 @@ def lib():
             "dm_solve_complex": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_partition_sizes": (I, [I, I, I, I, I, ctypes.POINTER(I)]),
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "dm_autotune_ex": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(D)]),
             "dm_factor": (I, [P, P, P, P]),
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_solve_last": (I, [P, P, P]),
@@ -175,6 +177,7 @@ def dm_plan(N, m, nrhs, P=0, levels=0, precision=DM_FP64):
 
 DM_PLAN_EQUAL_TIME = 1
 DM_PLAN_FP64_FMA = 2
+DM_PLAN_FP64_INV_COLUMN = 4
 
 
 def dm_plan_ex(N, m, nrhs, P=0, levels=0, precision=DM_FP64, flags=0):
@@ -229,6 +232,17 @@ def dm_autotune(N, m, nrhs, precision=DM_FP64):
     _check(lib().dm_autotune(int(N), int(m), int(nrhs), int(precision), ctypes.byref(p), ctypes.byref(lv),
                              ctypes.byref(ms)))
     return p.value, lv.value, ms.value
+
+
+def dm_autotune_ex(N, m, nrhs, precision=DM_FP64):
+    """(P, levels, flags, ms): dm_autotune, then the kernel variants timed at
+    that choice; flags are the fastest variant's plan flags."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p, lv, fl, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().dm_autotune_ex(int(N), int(m), int(nrhs), int(precision), ctypes.byref(p), ctypes.byref(lv),
+                                ctypes.byref(fl), ctypes.byref(ms)))
+    return p.value, lv.value, fl.value, ms.value
 
 
 def dm_factor(plan, A, B, C):

@@ -83,6 +83,25 @@ def test_partition_sizes_match_oracle(dm):
             o.partition_lengths_equal_time(N, P, m, r)
 
 
+def test_plan_flags_checked_without_gpu(dm):
+    """The kernel-variant flags are accepted by the host-side partitioner (they
+    do not change the partition); an unknown bit is refused before any device
+    call, by dm_plan_ex and by dm_partition_sizes."""
+    base = dm.dm_partition_sizes(100, 8, 1, 5)
+    for fl in (dm.DM_PLAN_FP64_FMA, dm.DM_PLAN_FP64_INV_COLUMN, dm.DM_PLAN_FP64_FMA | dm.DM_PLAN_FP64_INV_COLUMN):
+        assert dm.dm_partition_sizes(100, 8, 1, 5, fl) == base
+    for fl in (8, 16, 1 << 30):
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_partition_sizes(100, 8, 1, 5, fl)
+        assert e.value.code == dm.DM_EINVAL
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_plan_ex(100, 8, 1, 5, 1, dm.DM_FP64, fl)
+        assert e.value.code == dm.DM_EINVAL and "flags" in dm.dm_last_error()
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_autotune_ex(100, 8, 1, 9)
+    assert e.value.code == dm.DM_EINVAL
+
+
 def test_noalloc_refuses_host_arrays_before_the_call(dm):
     """dm_solve_noalloc takes device memory only: numpy arrays are refused by
     the binding with DM_EINVAL and nothing reaches the library."""

@@ -554,6 +554,50 @@ def test_fp64_products_sliced_and_fma(dm, N, m, r, P, levels):
     check(out[0], out[dm.DM_PLAN_FP64_FMA], TOL64)
 
 
+def test_autotune_variants_and_column_inverse(dm):
+    """dm_autotune_ex picks (P, levels) and then the fastest kernel variant of
+    the float64 sliced levels; dm_plan with P = levels = 0 applies all three.
+    The column-by-column inverse (DM_PLAN_FP64_INV_COLUMN) launches no panel
+    kernel and agrees with the oracle and with the blocked inverse."""
+    N, m, r = 260, 64, 2
+    P, lv, fl, ms = dm.dm_autotune_ex(N, m, r, "fp64")
+    assert P >= 1 and lv >= 1 and ms > 0
+    assert fl in (0, dm.DM_PLAN_FP64_FMA, dm.DM_PLAN_FP64_INV_COLUMN)
+    assert dm.dm_autotune_ex(N, m, r, "fp64")[:3] == (P, lv, fl)   # remembered
+    assert dm.dm_autotune(N, m, r, "fp64")[:2] == (P, lv)
+    s = w.dominant_system(N, m, r, 67)
+    plan = dm.dm_plan(N, m, r, 0, 0, "fp64")
+    try:
+        q = dm.dm_plan_query(plan)
+        assert (q["P"], q["levels"]) == (P, lv)
+        dm.dm_factor(plan, s.A, s.B, s.C)
+        x = np.zeros_like(s.b)
+        dm.dm_solve(plan, s.b, x)
+        check(x, o.dm(s.A, s.B, s.C, s.b, P, levels=lv, P2=q["P2"] if q["P2"] > 1 else None), TOL64)
+    finally:
+        dm.dm_destroy(plan)
+    out = {}
+    for flags in (0, dm.DM_PLAN_FP64_INV_COLUMN):
+        plan = dm.dm_plan_ex(N, m, r, 8, 2, "fp64", flags)
+        try:
+            dm.dm_factor(plan, s.A, s.B, s.C)
+            dm.dm_profile(plan, True)
+            dm.dm_factor(plan, s.A, s.B, s.C)
+            prof = dm.dm_profile(plan, False)
+            x = np.zeros_like(s.b)
+            assert dm.dm_solve(plan, s.b, x) < 1e-14
+            P2 = dm.dm_plan_query(plan)["P2"]
+        finally:
+            dm.dm_destroy(plan)
+        panel = sum(v["launches"] for k, v in prof.items() if k.split("@")[0] == "inv_panel")
+        assert (panel > 0) == (flags == 0), (flags, panel)
+        out[flags] = x
+    xo = o.dm(s.A, s.B, s.C, s.b, 8, levels=2, P2=P2 if P2 > 1 else None)
+    check(out[0], xo, TOL64)
+    check(out[dm.DM_PLAN_FP64_INV_COLUMN], xo, TOL64)
+    check(out[0], out[dm.DM_PLAN_FP64_INV_COLUMN], TOL64)
+
+
 def test_fp64_sliced_products_conditioned_blocks(dm):
     """Dense nonsymmetric blocks with cond(B_i) = 1e4 (pivoting inside the
     blocks, entries of widely different size in G_i): the digit-sliced
