@@ -86,6 +86,8 @@ def parse():
                     help="pde: the benchmark line (default); precision / batch / serve: the "
                          "conditioned-block, batched and served workloads, one JSON line each")
     ap.add_argument("--seconds", type=float, default=2.0, help="serve: length of the arrival stream")
+    ap.add_argument("--budget", type=float, default=0.25,
+                    help="serve: latency budget for admission in seconds (0: admit everything)")
     return ap.parse_args()
 
 
@@ -701,9 +703,11 @@ def run_batch(args):
 def run_serve(args):
     """Poisson arrivals (mean 2000 requests/s) of solves on a pool of resident
     systems (the batching workload's size mix plus 5 % large N=8192, m=256);
-    30 % repeat right-hand sides on resident factors, the rest factor + solve;
-    split-bf16 factors refined in float64.  Latency = done - submit on the
-    library's clock."""
+    30 % repeat right-hand sides on resident factors (one column each,
+    dm_submit_cols: queued ones on a plan share a solve), the rest factor +
+    solve of the plan's nrhs columns; split-bf16 factors refined in float64.
+    Admission by a latency budget (--budget).  Latency = done - submit on the
+    library's clock, over admitted requests."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -719,9 +723,21 @@ def run_serve(args):
         plan = dm.dm_plan(n, m, r, P, lv, "bf16x3")
         dm.dm_set_borrow_inputs(plan)
         dm.dm_factor(plan, a_, b_, c_)
-        rhs2 = [torch.randn_like(rhs) for _ in range(3)]
+        rhs2 = [torch.randn(n, m, 1, dtype=torch.float64, device=dev) for _ in range(3)]
         pool.append(dict(plan=plan, A=a_, B=b_, C=c_, b=rhs, rhs=rhs2, large=i >= len(small)))
     torch.cuda.synchronize()
+    # seed the admission estimates: one factor + solve and one narrow solve per plan
+    seed = []
+    for p in pool:
+        x = torch.empty_like(p["b"])
+        seed.append(dm.dm_submit_system(p["plan"], p["A"], p["B"], p["C"], p["b"], x))
+        seed.append(dm.dm_submit_cols(p["plan"], p["rhs"][0], torch.empty_like(p["rhs"][0]), 1))
+        p["keep"] = x
+    for t in seed:
+        while dm.dm_poll(t)[0] == dm.DM_PENDING:
+            time.sleep(0.0005)
+    dm.dm_serve_budget(args.budget)
+    stats0 = dm.dm_serve_stats()
     gaps = rng.exponential(1.0 / 2000.0, size=int(args.seconds * 2000 * 1.2))
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < args.seconds]
@@ -737,7 +753,9 @@ def run_serve(args):
         x = torch.empty_like(p["b"])
         try:
             if rng.random() < 0.3:
-                t = dm.dm_submit(p["plan"], p["rhs"][rng.integers(3)], x)
+                rhs = p["rhs"][rng.integers(3)]
+                x = torch.empty_like(rhs)
+                t = dm.dm_submit_cols(p["plan"], rhs, x, 1)
             else:
                 t = dm.dm_submit_system(p["plan"], p["A"], p["B"], p["C"], p["b"], x)
         except dm.DMError:
@@ -758,6 +776,8 @@ def run_serve(args):
         sub_t.append(times[0])
         done_t.append(times[2])
     span = max(done_t) - min(sub_t)
+    stats1 = dm.dm_serve_stats()
+    dm.dm_serve_budget(0.0)
     for p in pool:
         dm.dm_destroy(p["plan"])
     line = {"metric": "solved systems/s", "workload": "serve", "value": len(tickets) / span, "unit": "requests/s",
@@ -765,8 +785,11 @@ def run_serve(args):
             "offered_rps": len(arrivals) / args.seconds, "completed": len(tickets), "refused": refused,
             "failed": bad, "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                                           "p99": 1e3 * float(np.percentile(lat, 99))},
+            "budget_ms": 1e3 * args.budget,
+            "merged": stats1["merged"] - stats0["merged"], "worker_runs": stats1["runs"] - stats0["runs"],
             "config": {"workload": "Poisson 2000 req/s; pool of 48 systems of the batch mix + 2 of N=8192 m=256; "
-                                   "5 % large, 30 % repeat right-hand side; bf16x3 + fp64 refinement",
+                                   "5 % large, 30 % repeat single right-hand-side columns; bf16x3 + fp64 "
+                                   "refinement; admission by latency budget",
                        "seconds": args.seconds, "slots": 8}}
     print(json.dumps(line), flush=True)
 

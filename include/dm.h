@@ -245,6 +245,35 @@ int dm_poll_times(uint64_t ticket, int* status, double* relres_out, double* time
 /* Number of serving worker streams (1..64); only before the first submit. */
 int dm_serve_slots(int slots);
 
+/* A narrow request: b and x hold ncols right-hand-side columns
+ * ([N][m][ncols], 1 <= ncols <= the plan's nrhs), solved on the plan's
+ * resident factors.  Narrow requests queued on one plan are merged: a worker
+ * packs the columns of consecutive queued narrow requests (in submission
+ * order, while they fit in nrhs) into one solve of the plan's nrhs columns,
+ * unused columns zero, and unpacks each request's columns into its x; each
+ * request's relres is the worst of its own columns.  The columns pass through
+ * the plan's residual buffer and a gather kernel, so b and x may be host or
+ * device memory as for dm_solve.  Real single-system plans only (DM_EINVAL
+ * otherwise); other errors as dm_submit. */
+int dm_submit_cols(dm_plan_t plan, const double* b, double* x, int ncols, uint64_t* ticket);
+
+/* Latency budget for admission (seconds; 0, the default, admits everything
+ * the queue holds).  The server keeps per plan a moving average of the
+ * measured service time of factor + solve and of solve requests (a narrow
+ * request is charged its columns' share of a solve).  A submit whose
+ * predicted latency -- the queued and remaining running work divided by the
+ * slots, but at least the work queued or running on its own plan, plus its
+ * own service time -- exceeds the budget is refused with DM_EAGAIN and
+ * nothing is queued.  Plans not yet measured predict zero.  May be changed at
+ * any time.  DM_EINVAL for a negative, NaN or absurd (> 1e6 s) budget. */
+int dm_serve_budget(double seconds);
+
+/* Serving counters since the process started: out[0] requests admitted,
+ * out[1] refused (budget or full queue), out[2] worker runs (a run serves one
+ * request or one merged group), out[3] requests served in merged groups of
+ * two or more. */
+int dm_serve_stats(long long* out);
+
 /* The application case of the paper's Section 7: the right-hand side is zero
  * except its last block row b_N ([m][nrhs]) and only x_N ([m][nrhs]) is
  * wanted.  Every subsystem's z vanishes except the last one's, whose forward

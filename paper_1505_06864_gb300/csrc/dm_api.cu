@@ -40,14 +40,6 @@ int set_error(int code, const char* fmt, ...) {
   return code;
 }
 
-#define DM_CUDA(call)                                                                          \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess)                                                                     \
-      return set_error(DM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
-                       __FILE__, __LINE__);                                                    \
-  } while (0)
-
 // ---------------------------------------------------------------------------
 // Level construction
 int Level::build(const std::vector<SysSpec>& specs, bool fp32_factors, int tensor_mode) {
@@ -1256,6 +1248,15 @@ static double col_ratio(const std::vector<double>& h, int s, int r, int num, int
     const double b = h[(size_t)s * 4 * kMaxR + den * kMaxR + c];
     const double q = b > 0 ? std::sqrt(a / b) : std::sqrt(a);
     worst = std::max(worst, q);
+  }
+  return worst;
+}
+
+double Plan::column_relres(int c0, int nc) const {
+  double worst = 0.0;
+  for (int c = c0; c < c0 + nc && c < kMaxR; ++c) {
+    const double a = h_nrm[c], b = h_nrm[kMaxR + c];
+    worst = std::max(worst, b > 0 ? std::sqrt(a / b) : std::sqrt(a));
   }
   return worst;
 }

@@ -69,12 +69,6 @@ int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152
 
 using namespace dm;
 
-#define DM_CUDA_C(call)                                                                                   \
-  do {                                                                                                    \
-    cudaError_t e_ = (call);                                                                              \
-    if (e_ != cudaSuccess) return set_error(DM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
-  } while (0)
-
 extern "C" {
 
 int dm_plan_complex(dm_plan_t* out, int N, int m, int nrhs, int P, int levels, int precision) {
@@ -132,7 +126,7 @@ int dm_factor_complex(dm_plan_t plan, const double* A, const double* B, const do
       s = pl.cstage;
     }
     k_embed_blocks<<<grid_for(N * m * m), 256, 0, pl.stream>>>(reinterpret_cast<const double2*>(s), dst[k], N, m);
-    DM_CUDA_C(cudaGetLastError());
+    DM_CUDA(cudaGetLastError());
   }
   return pl.factor(pl.embA, pl.embB, pl.embC);
 }
@@ -153,18 +147,18 @@ int dm_solve_complex(dm_plan_t plan, const double* b, double* x, double* relres_
     s = pl.cstage;
   }
   k_embed_vec<<<grid_for(N * m * r), 256, 0, pl.stream>>>(reinterpret_cast<const double2*>(s), pl.bR, N, m, r);
-  DM_CUDA_C(cudaGetLastError());
+  DM_CUDA(cudaGetLastError());
   int rc = pl.solve(pl.bR, pl.xR, relres_out);
   if (rc != DM_OK && rc != DM_ENOTCONV) return rc;
   const bool dev = is_device_ptr(x);
   double2* d = reinterpret_cast<double2*>(dev ? x : pl.cstage);
   k_extract_vec<<<grid_for(N * m * r), 256, 0, pl.stream>>>(pl.xR, d, N, m, r);
-  DM_CUDA_C(cudaGetLastError());
+  DM_CUDA(cudaGetLastError());
   if (!dev) {
     int rc2 = copy_out(x, pl.cstage, bytes, pl.stream);
     if (rc2) return rc2;
   }
-  DM_CUDA_C(cudaStreamSynchronize(pl.stream));
+  DM_CUDA(cudaStreamSynchronize(pl.stream));
   return rc;
 }
 

@@ -231,11 +231,22 @@ struct Plan {
   int factor(const double* A, const double* B, const double* C);
   int solve(const double* b, double* x, double* relres_out);
   int solve_device(const double* b_dev, double* x_dev);
+  // max ||b - T x|| / ||b|| over columns [c0, c0 + nc) of system 0's last solve
+  double column_relres(int c0, int nc) const;
   ~Plan();
 };
 
 int set_error(int code, const char* fmt, ...);
 extern thread_local std::string g_last_error;  // text of the calling thread's last failure
+
+// Return DM_ECUDA with the failing call's text from an int-returning function.
+#define DM_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::dm::set_error(DM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                             __FILE__, __LINE__);                                              \
+  } while (0)
 void partition_plan(int N, int P, std::vector<int>& starts, std::vector<int>& lens, std::vector<int>& seps);
 void partition_lengths(int N, int P, int m, int r, int flags, std::vector<int>& lens);
 void nested_lengths(int N, int M, int J, std::vector<int>& lens);

@@ -89,6 +89,9 @@ def lib():
             "dm_solve_noalloc": (I, [I, I, I, I, P, P, P, P, P, P]),
             "dm_submit": (I, [P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
             "dm_submit_system": (I, [P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
+            "dm_submit_cols": (I, [P, P, P, I, ctypes.POINTER(ctypes.c_uint64)]),
+            "dm_serve_budget": (I, [D]),
+            "dm_serve_stats": (I, [ctypes.POINTER(ctypes.c_longlong)]),
             "dm_poll": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_poll_times": (I, [ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
             "dm_serve_slots": (I, [I]),
@@ -370,6 +373,26 @@ def dm_poll_times(ticket):
 
 def dm_serve_slots(slots):
     return _check(lib().dm_serve_slots(int(slots)))
+
+
+def dm_submit_cols(plan, b, x, ncols):
+    """Queue a solve of ncols columns ([N][m][ncols]) on the plan's resident
+    factors; narrow requests queued on one plan share one solve."""
+    t = ctypes.c_uint64(0)
+    _check(lib().dm_submit_cols(plan, _ptr(b), _ptr(x, True), int(ncols), ctypes.byref(t)))
+    return t.value
+
+
+def dm_serve_budget(seconds):
+    """Latency budget for admission (0: none); refused submits raise DMError(DM_EAGAIN)."""
+    return _check(lib().dm_serve_budget(float(seconds)))
+
+
+def dm_serve_stats():
+    """dict(admitted, refused, runs, merged) since the process started."""
+    out = (ctypes.c_longlong * 4)()
+    _check(lib().dm_serve_stats(out))
+    return dict(admitted=out[0], refused=out[1], runs=out[2], merged=out[3])
 
 
 DM_PROBE_FP64, DM_PROBE_FP32, DM_PROBE_TF32, DM_PROBE_BF16 = 0, 1, 2, 3

@@ -6,6 +6,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1505_06864_gb300 import build as B
@@ -100,6 +101,21 @@ def test_plan_flags_checked_without_gpu(dm):
     with pytest.raises(dm.DMError) as e:
         dm.dm_autotune_ex(100, 8, 1, 9)
     assert e.value.code == dm.DM_EINVAL
+
+
+def test_serving_arguments_checked_without_gpu(dm):
+    """Budget and narrow-request arguments are checked before any device work
+    (the server starts no worker for them)."""
+    for bad in (-1.0, float("nan"), 1e9):
+        with pytest.raises(dm.DMError) as e:
+            dm.dm_serve_budget(bad)
+        assert e.value.code == dm.DM_EINVAL
+    dm.dm_serve_budget(0.0)
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_submit_cols(None, np.zeros(4), np.zeros(4), 1)
+    assert e.value.code == dm.DM_EINVAL
+    st = dm.dm_serve_stats()
+    assert set(st) == {"admitted", "refused", "runs", "merged"} and all(v >= 0 for v in st.values())
 
 
 def test_noalloc_refuses_host_arrays_before_the_call(dm):
