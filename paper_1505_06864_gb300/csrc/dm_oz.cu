@@ -702,15 +702,17 @@ __device__ __forceinline__ bool gj_unusable(double v) {
   return b < 0x0010000000000000ull || b >= 0x7ff0000000000000ull;
 }
 
-// The CTA's best of every lane's (key, idx): a warp butterfly, then the best
-// of the warps' bests after a CTA barrier (the same result in every thread).
+// The CTA's best of every lane's (key, idx): the warp's largest key (its high
+// word, then its low word among the lanes with that high word) and the lowest
+// row holding it, by three warp reductions; then the best of the warps' bests
+// after a CTA barrier (the same result in every thread).
 __device__ __forceinline__ GjKey gj_cta_best(unsigned long long key, int idx, GjKey* wbest, int warp, int lane) {
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
-    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-    if (gj_before(ok, oi, key, idx)) key = ok, idx = oi;
-  }
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+  const unsigned mi = __reduce_min_sync(0xffffffffu, hi == mh && lo == ml ? (unsigned)idx : 0xffffffffu);
+  key = ((unsigned long long)mh << 32) | ml;
+  idx = (int)mi;
   if (lane == 0) wbest[warp] = GjKey{key, idx, 0};
   __syncthreads();
   GjKey best = wbest[0];
@@ -814,6 +816,16 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     if (tid == 0) piv_s[0] = r;
     __syncwarp();
   }
+  // the cluster's published candidates and rows, mapped once (buffer b at + b)
+  const GjCand* rcand[kGjCS];
+  const double* rcrow[kGjCS];
+#pragma unroll
+  for (int s = 0; s < kGjCS; ++s) {
+    rcand[s] = cl.map_shared_rank(&cand[0], s);
+    rcrow[s] = cl.map_shared_rank(&crow[0][0], s);
+  }
+  // the CTA holding row k + 1 and that row's place in it, advanced per pivot
+  int ko = (k0 + 1) / R, kro = (k0 + 1) - ko * R;
 #pragma unroll 1
   for (int kk = 0; kk < 32; ++kk) {
     if (kk >= kw) {  // padding columns of a narrow last panel: rotate only
@@ -827,7 +839,11 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     const bool la = kk + 1 < kw, swap = i == r && i != k;  // row r takes the old row k
     if (swap)
 #pragma unroll
-      for (int c = 0; c < 16; ++c) reg[c] = xr[16 * h + c];
+      for (int c = 0; c < 16; c += 2) {
+        const double2 v2 = *reinterpret_cast<const double2*>(&xr[16 * h + c]);
+        reg[c] = v2.x;
+        reg[c + 1] = v2.y;
+      }
     const double other = __shfl_xor_sync(0xffffffffu, reg[0], 16);  // the other half's first column
     const double f = h == 0 ? reg[0] : other;  // the row's multiplier (column kk)
     if (la) {
@@ -857,30 +873,38 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
     }
     // pivot kk's update of this thread's row, rotated by one column
     if (valid) {
+      double s16[16];  // this half's 16 values of the scaled pivot row
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        const double2 v2 = *reinterpret_cast<const double2*>(&sp[16 * h + c]);
+        s16[c] = v2.x;
+        s16[c + 1] = v2.y;
+      }
+      const double snext = sp[h == 0 ? 16 : 0];  // the next half's first value
       if (i == k) {
 #pragma unroll
-        for (int c = 0; c < 15; ++c) reg[c] = sp[16 * h + c + 1];
-        reg[15] = h == 0 ? sp[16] : sp[0];
+        for (int c = 0; c < 15; ++c) reg[c] = s16[c + 1];
+        reg[15] = snext;
       } else {
 #pragma unroll
-        for (int c = 0; c < 15; ++c) reg[c] = fma(-f, sp[16 * h + c + 1], reg[c + 1]);
-        reg[15] = h == 0 ? fma(-f, sp[16], other) : -f * sp[0];
+        for (int c = 0; c < 15; ++c) reg[c] = fma(-f, s16[c + 1], reg[c + 1]);
+        reg[15] = h == 0 ? fma(-f, snext, other) : -f * snext;
       }
     }
     if (la) {
       cluster_wait();
       const int buf = (kk + 1) & 1, src = (lane + 1) & 31;
-      GjCand w = gj_read_cand(cl.map_shared_rank(&cand[buf], 0));
-      double pre = cl.map_shared_rank(&crow[buf][0], 0)[src];
+      GjCand w = gj_read_cand(rcand[0] + buf);
+      double pre = rcrow[0][32 * buf + src];
 #pragma unroll
       for (int s = 1; s < kGjCS; ++s) {
-        const GjCand o = gj_read_cand(cl.map_shared_rank(&cand[buf], s));
-        const double v = cl.map_shared_rank(&crow[buf][0], s)[src];
+        const GjCand o = gj_read_cand(rcand[s] + buf);
+        const double v = rcrow[s][32 * buf + src];
         if (gj_before(o.key, o.idx, w.key, w.idx)) w = o, pre = v;
       }
-      const int ko = (k + 1) / R;
       const double kpre = cl.map_shared_rank(&krow[buf][0], ko)[src];
       const double kfk = *cl.map_shared_rank(&kf[buf], ko);
+      if (++kro == R) kro = 0, ++ko;
       // pivot kk's update of element `lane` of the winner and of row k + 1
       const double spc = sp[src];
       const double u = src == 0 ? -w.f * spc : fma(-w.f, spc, pre);
