@@ -696,10 +696,25 @@ __device__ __forceinline__ unsigned long long gj_key(double v) {
   return b > 0x7ff0000000000000ull ? 1ull : b + 2ull;
 }
 
-// zero, below 2^-1022 (whose reciprocal overflows) or not finite
+// zero, below 2^-1022 (whose reciprocal overflows), at or above 2^1022
+// (whose reciprocal is not a normal number) or not finite
 __device__ __forceinline__ bool gj_unusable(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-  return b < 0x0010000000000000ull || b >= 0x7ff0000000000000ull;
+  return b < 0x0010000000000000ull || b >= 0x7fd0000000000000ull;
+}
+
+// 1/x for a usable pivot x (2^-1022 <= |x| < 2^1022): the PTX reciprocal
+// approximation rcp.approx.ftz.f64 refined by two Newton-Raphson steps for
+// f(y) = 1/y - x, y <- y + y (1 - x y), each of which squares the relative
+// error (within about one unit in the last place of 1/x).  It has no
+// branch, so the compiler can interleave it with the pivot search.
+__device__ __forceinline__ double gj_recip(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
 }
 
 // The CTA's best of every lane's (key, idx): the warp's largest key (its high
@@ -787,7 +802,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       for (int c = 0; c < 16; c += 2)
         *reinterpret_cast<double2*>(&crow[0][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
       if (h == 0) {
-        cand[0].inv = gj_unusable(reg[0]) ? 0.0 : 1.0 / reg[0];
+        cand[0].inv = gj_unusable(reg[0]) ? 0.0 : gj_recip(reg[0]);
         cand[0].f = 0.0;
       }
     }
@@ -852,13 +867,14 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       const int buf = (kk + 1) & 1;
       const double new1 = i == k ? sp[1] : fma(-f, sp[1], reg[1]);
       const bool elig = h == 0 && valid && i > k;
+      const double rinv = gj_recip(new1);  // every row's, overlapping the search
       const GjKey best = gj_cta_best(elig ? gj_key(new1) : 0ull, elig ? i : noidx, wbest, warp, lane);
       if (valid && i == best.idx) {
 #pragma unroll
         for (int c = 0; c < 16; c += 2)
           *reinterpret_cast<double2*>(&crow[buf][16 * h + c]) = make_double2(reg[c], reg[c + 1]);
         if (h == 0) {
-          cand[buf].inv = gj_unusable(new1) ? 0.0 : 1.0 / new1;
+          cand[buf].inv = gj_unusable(new1) ? 0.0 : rinv;
           cand[buf].f = f;
         }
       }
