@@ -925,9 +925,10 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const PartDesc* __restr
       const double spc = sp[src];
       const double u = src == 0 ? -w.f * spc : fma(-w.f, spc, pre);
       const double x = src == 0 ? -kfk * spc : fma(-kfk, spc, kpre);
-      const double p0 = __shfl_sync(0xffffffffu, u, 0);
+      // u at lane 0 is the winner's updated pivot, the same multiply-add of the
+      // same operands its owner made: the owner's inv is 0 exactly when it is unusable
       double inv = w.inv;
-      if (gj_unusable(p0)) inv = 0.0, bad = true;
+      if (inv == 0.0) bad = true;
       r = w.idx;
       if (r <= k || r >= m) r = k + 1, inv = 0.0, bad = true;  // never: the winner is an eligible row
       __syncwarp();
