@@ -456,7 +456,7 @@ int Level::allocate() {
       DM_ALLOC(Z.eV, np * ex);
       DM_ALLOC(Z.piv, np * ex);
       ok = oz_make_map(Z.U, np, m, oz_box_rows_left(), Z.gj_maps[0], 32) &&
-           oz_make_map(Z.V, np, m, oz_box_rows_right(), Z.gj_maps[1], 32);
+           oz_make_map(Z.V, np, m, oz_box_rows_gj(), Z.gj_maps[1], 32);
       if (!ok) return set_error(DM_ECUDA, "tensor map creation for the blocked inversion failed (m = %d)", m);
       Z.gj = true;
     }

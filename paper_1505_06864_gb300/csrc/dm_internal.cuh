@@ -159,6 +159,7 @@ int oz_slice_blocks_bytes(int m);
 bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* out, int kdim = 0);
 int oz_box_rows_left();
 int oz_box_rows_right();
+int oz_box_rows_gj();  // rows of the right operand's box in the inverse's trailing updates
 // The supplementary blocks of a sliced level (Eq. e2311) as digit-sliced
 // products: C_q row slices and the four boundary spike blocks' column slices
 // per separator, then HB = B_q - A_q ZR - C_q ZL, HA = -A_q ZL, HC = -C_q ZR.

@@ -53,13 +53,14 @@ constexpr int kEpiWarps = 8;                 // epilogue warps 2 .. 9
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0: TMA producer, warp 1: MMA issuer
 constexpr int MT = 128;          // rows per tile
 constexpr int NT = 48;           // columns per tile
+constexpr int NT3 = 32;          // columns per tile of the inverse's trailing updates (KIND 3)
 constexpr int KS = 32;           // K elements per stage (64-byte rows, 64-byte swizzle)
 constexpr int kStages = 2;
 constexpr int S = kRsSlices;     // 9 slices
 constexpr int NACC = 10;         // accumulators d = 2 .. 11
 constexpr int ROWB = KS * 2;     // 64 bytes
 constexpr int LSL = MT * ROWB;   // one left slice in a stage: 8 KB
-constexpr int RSL = NT * ROWB;   // one right slice: 3 KB
+constexpr int RSL = NT * ROWB;   // one right slice: 3 KB (2 KB for KIND 3, packed the same way)
 constexpr int LBYTES = S * LSL;  // 72 KB
 constexpr int RBYTES = (S + 1) * RSL;  // 30 KB with the zero slice
 constexpr int STAGE = LBYTES + RBYTES;
@@ -134,6 +135,11 @@ struct OzTile {
 };
 
 template <int KIND>
+constexpr int nt_of() {
+  return KIND == 3 ? NT3 : NT;
+}
+
+template <int KIND>
 __device__ __forceinline__ OzTile oz_tile(int tile, const PartDesc* __restrict__ parts, const OzOut& out, int step,
                                           int aux, int m, int ntm, int ntn) {
   OzTile w{};
@@ -142,6 +148,9 @@ __device__ __forceinline__ OzTile oz_tile(int tile, const PartDesc* __restrict__
   w.unit = tile / per;
   const int rest = tile - w.unit * per;
   w.tn = rest % ntn;
+  // KIND 3: the 32-column tile equal to panel `step` produces nothing and is
+  // not enumerated (ntn counts the others)
+  if (KIND == 3 && w.tn >= step) ++w.tn;
   const int r2 = rest / ntn;
   w.j = nj == 1 ? 0 : (r2 & 1);
   w.tm = nj == 1 ? r2 : (r2 >> 1);
@@ -172,7 +181,7 @@ __device__ __forceinline__ OzTile oz_tile(int tile, const PartDesc* __restrict__
   // products with a banded operand run in the banded kernels instead
   const bool banded = out.band && *out.band <= kBandMax;
   if (banded && ((KIND == 0 && j == 0) || KIND == 1 || KIND >= 4)) act = false;
-  w.act = act && w.tm * MT < m && w.tn * NT < m;
+  w.act = act && w.tm * MT < m && w.tn * nt_of<KIND>() < m;
   const long long mm = (long long)m * m;
   const int b0 = (int)(p.blk / mm), t = w.t;
   if (KIND == 4) {
@@ -210,6 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_oz_step(const PartDesc* __restrict__ parts, int step, int aux, int m, int ntm, int ntn, int ntiles, OzOut out,
               const int* __restrict__ lexp, const int* __restrict__ rexp0, const int* __restrict__ rexp1,
               int* __restrict__ errflag, const __grid_constant__ OzMaps maps) {
+  constexpr int NTK = nt_of<KIND>();   // columns per tile
+  constexpr int RSLK = NTK * ROWB;      // one right slice in a stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t full[kStages], empty[kStages], tfull, tempty, mdone;
   __shared__ uint32_t tmem_slot;
@@ -220,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* verr = &err;
   // the zero right slice of both stages (never written by the copies)
   for (int st = 0; st < kStages; ++st)
-    for (int i = threadIdx.x; i < RSL / 16; i += kThreads)
-      reinterpret_cast<uint4*>(base + st * STAGE + LBYTES + S * RSL)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < RSLK / 16; i += kThreads)
+      reinterpret_cast<uint4*>(base + st * STAGE + LBYTES + S * RSLK)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_async_shared();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_slot;
   const long long mm = (long long)m * m;
   const int nslab = KIND == 3 ? 1 : (m + KS - 1) / KS;
-  constexpr uint32_t tx = (uint32_t)(S * (MT + NT) * ROWB);
+  constexpr uint32_t tx = (uint32_t)(S * (MT + NTK) * ROWB);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sb = smem_u32(base + st * STAGE);
           mbar_expect_tx(&full[st], tx);
           tma_load_4d(sb, &maps.L, s * KS, w.tm * MT, 0, w.zl, &full[st]);
-          tma_load_4d(sb + LBYTES, mr, s * KS, w.tn * NT, 0, w.zr, &full[st]);
+          tma_load_4d(sb + LBYTES, mr, s * KS, w.tn * NTK, 0, w.zr, &full[st]);
         }
         if (!ok) {
           *verr = 1;
@@ -303,10 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int ta = 1; ta <= T; ta += 5) {
                 const int cnt = min(5, T - ta + 1);
-                const uint64_t bd = kmajor_desc(ra + (ta - 1) * RSL + off, kSbo, kLayout);
-                const uint32_t dcol = (uint32_t)((sl + ta - 2) * NT);
+                const uint64_t bd = kmajor_desc(ra + (ta - 1) * RSLK + off, kSbo, kLayout);
+                const uint32_t dcol = (uint32_t)((sl + ta - 2) * NTK);
                 const uint32_t acc = (s == 0 && k == 0 && sl == 1) ? 0u : 1u;
-                mma<1>(tmem + dcol, ad, bd, make_idesc(1u, MT, NT * cnt), acc);
+                mma<1>(tmem + dcol, ad, bd, make_idesc(1u, MT, NTK * cnt), acc);
               }
             }
           }
@@ -346,8 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int er = row < m ? lexp[(long long)w.zl * m + row] : 0;
       int fexp = 0;
       {
-        const int n = w.tn * NT + half * (NT / 2) + lane;
-        if (lane < NT / 2 && n < m) fexp = rexp[(long long)w.zr * m + n];
+        const int n = w.tn * NTK + half * (NTK / 2) + lane;
+        if (lane < NTK / 2 && n < m) fexp = rexp[(long long)w.zr * m + n];
       }
       const bool rmw = KIND == 2 && j == 0, dnext = KIND == 1 && j == 0, gj = KIND == 3, hb = KIND >= 4 && j == 0;
       const bool upd = rmw || dnext || gj || hb;
@@ -358,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  : out.B + o + mm;
       // the values chunk ci's stores update, loaded one chunk ahead
       auto load_in = [&](int ci, double (&in)[8]) {
-        const int n = w.tn * NT + half * (NT / 2) + 8 * ci + cl;
+        const int n = w.tn * NTK + half * (NTK / 2) + 8 * ci + cl;
         const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -391,15 +402,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       // conversion is exact): K = 32, or K = m <= 112 (acc_d <= 9 K 63^2)
       const bool small = KIND == 3 || m <= 112;
 #pragma unroll
-      for (int ci = 0; ci < NT / 16; ++ci) {
-        const int ch = half * (NT / 2) + 8 * ci;
+      for (int ci = 0; ci < NTK / 16; ++ci) {
+        const int ch = half * (NTK / 2) + 8 * ci;
         // chunks past the block's last column, and (KIND 3) inside the
         // panel's columns, produce nothing: only the release of the
         // accumulators after the last chunk remains
-        const int c0n = w.tn * NT + ch;
+        const int c0n = w.tn * NTK + ch;
         const bool dead = c0n >= m || (KIND == 3 && c0n >= k0 && c0n < k0 + 32);
         if (dead) {
-          if (ci == NT / 16 - 1) {
+          if (ci == NTK / 16 - 1) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty);
@@ -412,11 +423,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         uint32_t r[NACC][8];
 #pragma unroll
-        for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NT + ch), r[dd]);
+        for (int dd = 0; dd < NACC; ++dd) tmem_ld8_nowait(tl + (uint32_t)(dd * NTK + ch), r[dd]);
         tmem_wait_ld();
 #pragma unroll
         for (int dd = 0; dd < NACC; ++dd) tmem_regs_after_wait(r[dd]);
-        if (ci == NT / 16 - 1) {  // the last accumulator read of this tile: the MMAs may go on
+        if (ci == NTK / 16 - 1) {  // the last accumulator read of this tile: the MMAs may go on
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty);
@@ -425,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int n = w.tn * NT + ch + c;
+          const int n = w.tn * NTK + ch + c;
           const int k = er + __shfl_sync(0xffffffffu, fexp, 8 * ci + c);
           int a[NACC];
 #pragma unroll
@@ -451,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
         // row-major float64 results: lane = (row quarter, column), 8 row quads
-        const int n = w.tn * NT + ch + cl;
+        const int n = w.tn * NTK + ch + cl;
         const bool outside = KIND != 3 || n < k0 || n >= k0 + 32;
         if (n < m && outside) {
 #pragma unroll
@@ -1346,6 +1357,7 @@ bool oz_make_map(const void* base, long long blocks, int m, int box_rows, void* 
 
 int oz_box_rows_left() { return oz::MT; }
 int oz_box_rows_right() { return oz::NT; }
+int oz_box_rows_gj() { return oz::NT3; }
 
 void launch_band_detect(const double* A, const double* C, long long n, int m, int* band, cudaStream_t st) {
   if (n <= 0 || !band) return;
@@ -1436,8 +1448,11 @@ void launch_oz_step(int kind, const PartDesc* parts, int nparts, int step, int m
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
   }
-  const int ntm = (m + oz::MT - 1) / oz::MT, ntn = (m + oz::NT - 1) / oz::NT;
+  // KIND 3: 32-column tiles without the one that is the panel itself
+  const int ntm = (m + oz::MT - 1) / oz::MT,
+            ntn = kind == 3 ? (m + oz::NT3 - 1) / oz::NT3 - 1 : (m + oz::NT - 1) / oz::NT;
   const int ntiles = nparts * (kind == 3 ? 1 : 2) * ntm * ntn;
+  if (ntiles <= 0) return;
   const int grid = std::min(ntiles, nsm);
 #define DM_OZ(KIND_)                                                                                              \
   do {                                                                                                           \
