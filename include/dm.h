@@ -43,7 +43,8 @@ extern "C" {
 #define DM_PENDING 1      /* dm_poll: the request has not finished */
 #define DM_EINVAL (-1)    /* invalid argument (sizes, P, levels, precision, NULL pointer) */
 #define DM_ENOMEM (-2)    /* device memory could not be allocated / admission refused */
-#define DM_ESINGULAR (-3) /* a pivot of some block LU was zero or not finite */
+#define DM_ESINGULAR (-3) /* a pivot of some block inverse was zero, not finite, or (float64
+                             blocked inverse) of magnitude below 2^-1022 or at least 2^1022 */
 #define DM_ENOTCONV (-4)  /* iterative refinement did not reach its tolerance */
 #define DM_EAGAIN (-5)    /* no serving slot free right now; try again */
 #define DM_ECUDA (-6)     /* a CUDA runtime call failed */
@@ -182,7 +183,8 @@ int dm_plan_batch(dm_plan_t* out, int count, const int* N, const int* m, const i
  * (Eq. e231, the W_R right-hand sides), assembly of the supplementary matrix
  * (Eq. e2311) and its float64 factorisation (Eq. e232).  The factors stay on
  * the device until dm_destroy; dm_factor may be called again with new blocks.
- * Returns DM_ESINGULAR if a pivot vanished (dm_last_error names the block row),
+ * Returns DM_ESINGULAR if a pivot vanished or its reciprocal is not a normal
+ * float64 number (dm_last_error names the block row),
  * DM_ENOMEM if the first call cannot allocate the plan's input copies. */
 int dm_factor(dm_plan_t plan, const double* A, const double* B, const double* C);
 
