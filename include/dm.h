@@ -217,6 +217,12 @@ int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* levels, doub
  * applies.  flags may be NULL. */
 int dm_autotune_ex(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags, double* ms_out);
 
+/* The measured choice stored for this shape and precision (by dm_autotune /
+ * dm_autotune_ex in this process, or read from the DM_TUNE_CACHE file at the
+ * first lookup), which dm_plan with P = 0 and levels = 0 applies.  Host only:
+ * no GPU work.  DM_EINVAL if there is none.  flags may be NULL. */
+int dm_tuned(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags);
+
 /* Continuous batching.  dm_submit queues a solve of b on the plan's resident
  * factors; dm_submit_system queues a factor (of A, B, C) followed by a solve.
  * Both return at once with a ticket.  A process-wide server runs the queued

@@ -24,6 +24,7 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -90,12 +91,20 @@ void load_cache_locked() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   char line[256];
+  const std::string keep = g_last_error;  // validation below must not replace the caller's error text
   while (std::fgets(line, sizeof line, f)) {
     int N, m, r, prec, P, lv, fl = 0;
     double ms;
     const int k = std::sscanf(line, "%d %d %d %d %d %d %lf %d", &N, &m, &r, &prec, &P, &lv, &ms, &fl);
-    if (k >= 7) g_cache[Key(N, m, r, prec)] = Choice{P, lv, ms, k == 8 ? fl : 0, k == 8};
+    // lines written before the flags column have seven fields; lines that do
+    // not describe a valid plan (sizes, P, depth, precision, flags) are skipped
+    SysSpec spec;
+    if (k < 7 || prec < DM_FP64 || prec > DM_BF16X3 || P < 1 || lv < 1 || !(ms >= 0) ||
+        (fl & ~(DM_PLAN_FP64_FMA | DM_PLAN_FP64_INV_COLUMN)) || make_spec(N, m, r, P, lv, &spec) != DM_OK)
+      continue;
+    g_cache[Key(N, m, r, prec)] = Choice{P, lv, ms, k == 8 ? fl : 0, k == 8};
   }
+  g_last_error = keep;
   std::fclose(f);
 }
 
@@ -228,6 +237,16 @@ extern "C" int dm_autotune(int N, int m, int nrhs, int precision, int* P, int* l
   if (!P || !levels) return dm::set_error(DM_EINVAL, "NULL argument to dm_autotune");
   if (precision < DM_FP64 || precision > DM_BF16X3) return dm::set_error(DM_EINVAL, "unknown precision");
   return dm::autotune(N, m, nrhs, precision, P, levels, ms_out, nullptr, false);
+}
+
+extern "C" int dm_tuned(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags) {
+  if (!P || !levels) return dm::set_error(DM_EINVAL, "NULL argument to dm_tuned");
+  int fl = 0;
+  if (!dm::tuned_lookup(N, m, nrhs, precision, P, levels, &fl))
+    return dm::set_error(DM_EINVAL, "no measured choice for N = %d, m = %d, nrhs = %d, precision %d", N, m, nrhs,
+                         precision);
+  if (flags) *flags = fl;
+  return DM_OK;
 }
 
 extern "C" int dm_autotune_ex(int N, int m, int nrhs, int precision, int* P, int* levels, int* flags, double* ms_out) {

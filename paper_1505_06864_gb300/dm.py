@@ -74,6 +74,7 @@ def lib():
             "dm_autotune": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "dm_autotune_ex": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                    ctypes.POINTER(D)]),
+            "dm_tuned": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "dm_factor": (I, [P, P, P, P]),
             "dm_solve": (I, [P, P, P, ctypes.POINTER(D)]),
             "dm_solve_last": (I, [P, P, P]),
@@ -246,6 +247,16 @@ def dm_autotune_ex(N, m, nrhs, precision=DM_FP64):
     _check(lib().dm_autotune_ex(int(N), int(m), int(nrhs), int(precision), ctypes.byref(p), ctypes.byref(lv),
                                 ctypes.byref(fl), ctypes.byref(ms)))
     return p.value, lv.value, fl.value, ms.value
+
+
+def dm_tuned(N, m, nrhs, precision=DM_FP64):
+    """(P, levels, flags) stored by the tuner for this shape; raises DMError if none."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p, lv, fl = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().dm_tuned(int(N), int(m), int(nrhs), int(precision), ctypes.byref(p), ctypes.byref(lv),
+                          ctypes.byref(fl)))
+    return p.value, lv.value, fl.value
 
 
 def dm_factor(plan, A, B, C):

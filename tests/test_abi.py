@@ -103,6 +103,39 @@ def test_plan_flags_checked_without_gpu(dm):
     assert e.value.code == dm.DM_EINVAL
 
 
+def test_tuner_cache_file_read_without_gpu(dm, tmp_path):
+    """The tuner's cache file: seven-field lines (no flags column) and
+    eight-field lines load; lines that do not describe a valid plan are
+    skipped; dm_tuned reports the stored choice with no device work.  A fresh
+    process, since the file is read once per process at the first lookup."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    cache.write_text("300 32 2 0 7 2 12.5\n"            # seven fields: flags 0
+                     "2048 256 1 0 64 3 80.1 4\n"       # the column-by-column inverse
+                     "1000 64 4 3 40 2 9.0 2\n"         # bf16x3, FP64-pipe products
+                     "100 8 1 0 80 1 3.0 0\n"           # P too large for N: skipped
+                     "100 8 2 9 5 1 3.0 0\n"            # unknown precision: skipped
+                     "100 8 3 0 5 1 3.0 64\n"           # unknown flag: skipped
+                     "100 600 1 0 5 1 3.0 0\n"          # m above the limit: skipped
+                     "not a line\n")
+    code = (
+        "from paper_1505_06864_gb300 import dm\n"
+        "assert dm.dm_tuned(300, 32, 2, 'fp64') == (7, 2, 0)\n"
+        "assert dm.dm_tuned(2048, 256, 1, 'fp64') == (64, 3, dm.DM_PLAN_FP64_INV_COLUMN)\n"
+        "assert dm.dm_tuned(1000, 64, 4, 'bf16x3') == (40, 2, dm.DM_PLAN_FP64_FMA)\n"
+        "for args in [(100, 8, 1, 'fp64'), (100, 8, 3, 'fp64'), (100, 600, 1, 'fp64'), (300, 32, 2, 'fp32')]:\n"
+        "    try:\n"
+        "        dm.dm_tuned(*args)\n"
+        "        raise SystemExit('stored: %r' % (args,))\n"
+        "    except dm.DMError as e:\n"
+        "        assert e.code == dm.DM_EINVAL and 'no measured choice' in dm.dm_last_error()\n"
+        "print('ok')\n")
+    env = dict(os.environ, DM_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
 def test_serving_arguments_checked_without_gpu(dm):
     """Budget and narrow-request arguments are checked before any device work
     (the server starts no worker for them)."""
